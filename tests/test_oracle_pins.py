@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, invariants, special cases, brute force on tiny meshes).
+
+A mistake anywhere in the oracle (a dropped term, a wrong sign, a transposed
+operand, a wrong index) should fail at least one of these.
+"""
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.linalg as sla
+
+import oracle
+import workloads
+from oracle import dense, geometry as geo
+from oracle.richardson import Coarse, richardson
+
+
+# ------------------------------------------------------------ geometry
+def test_mesh_areas_and_sphere_measure():
+    nodes, cells = geo.square_mesh(5)
+    P = nodes[cells]
+    e1, e2 = P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]
+    area = 0.5 * (e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    assert np.all(area > 0)                      # counter-clockwise cells
+    assert abs(area.sum() - 1.0) < 1e-14         # |R| = 1
+    for lv in range(4):
+        reps = geo.sphere_reps(lv)
+        assert reps.shape[0] == 4 * 4 ** lv      # n_S^+ = T / 2
+        # the representatives and their antipodes tile S^2: area 4 pi
+        assert abs(2 * geo.spherical_area(reps).sum() - 4 * np.pi) < 1e-12
+        cen = reps.mean(axis=1)
+        assert np.all(cen[:, 2] > 0)             # one per antipodal pair
+    pts, w = geo.quad_rule(geo.sphere_reps(1), 3)
+    assert np.allclose(w.sum(1), geo.spherical_area(geo.sphere_reps(1)),
+                       rtol=1e-13)
+    assert np.allclose(np.linalg.norm(pts, axis=-1), 1.0)
+
+
+def test_octant_triangle_area_closed_form():
+    # one octahedron face is an octant of the sphere: area 4 pi / 8
+    assert abs(geo.spherical_area(geo.UPPER_FACES[:1])[0] - np.pi / 2) < 1e-14
+
+
+def test_hg_normalisation_closed_form():
+    # int_S k(s.s') ds' = 2 pi int_{-1}^{1} k(mu) dmu = 1  (Section 1)
+    for g in (0.0, 0.3, 0.9):
+        val, _ = si.quad(lambda mu: oracle.hg_kernel(mu, g), -1, 1,
+                         epsabs=1e-13, points=[1.0])
+        assert abs(2 * np.pi * val - 1.0) < 1e-9
+    # first Legendre moment of HG is g (mean cosine), so S maps linear
+    # functions to g times themselves (eq. eigS, l = 1)
+    g = 0.6
+    val, _ = si.quad(lambda mu: mu * oracle.hg_kernel(mu, g), -1, 1,
+                     epsabs=1e-13)
+    assert abs(2 * np.pi * val - g) < 1e-9
+
+
+# ------------------------------------------------------------ spatial
+def test_spatial_matrices_exact_integrals():
+    m = 4
+    st = np.linspace(1, 2, 2 * m * m)
+    smat = oracle.assemble.spatial_matrices(m, st, 0.5 * st)
+    nodes = smat['nodes']
+    one = np.ones(nodes.shape[0])
+    # derivative of a constant vanishes, of x (resp. y) is the cell area
+    assert np.abs(smat['D1'] @ one).max() < 1e-15
+    assert np.abs(smat['D2'] @ one).max() < 1e-15
+    assert np.allclose(smat['D1'] @ nodes[:, 0], smat['area'], atol=1e-15)
+    assert np.allclose(smat['D2'] @ nodes[:, 1], smat['area'], atol=1e-15)
+    assert np.abs(smat['D1'] @ nodes[:, 1]).max() < 1e-15
+    # int_R sigma_t = 1^T M_t 1 ; int_R 1 = 1 ; int_R x = 1/2
+    assert abs(one @ smat['Mt_plus'] @ one - (st * smat['area']).sum()) < 1e-13
+    assert abs(one @ smat['M_plus_unit'] @ one - 1.0) < 1e-14
+    assert abs(nodes[:, 0] @ smat['M_plus_unit'] @ one - 0.5) < 1e-14
+    # int_R x^2 = 1/3 exactly for the P1 mass with the interpolant of x^2?
+    # no: x^T M x = int (I_h x)^2 = int x^2 = 1/3 since x is P1
+    assert abs(nodes[:, 0] @ smat['M_plus_unit'] @ nodes[:, 0] - 1 / 3) < 1e-14
+    # boundary masses: the x-faces and y-faces each have length 2;
+    # int_{x-faces} y^2 = 2/3
+    assert abs(one @ smat['Bx'] @ one - 2.0) < 1e-14
+    assert abs(one @ smat['By'] @ one - 2.0) < 1e-14
+    assert abs(nodes[:, 1] @ smat['Bx'] @ nodes[:, 1] - 2 / 3) < 1e-14
+    assert abs(nodes[:, 0] @ smat['Bx'] @ nodes[:, 0] - 1.0) < 1e-14
+    assert np.allclose(smat['Mt_minus'], st * smat['area'])
+
+
+# ------------------------------------------------------------ angular
+@pytest.fixture(scope="module")
+def ang():
+    return oracle.assemble.angular_matrices(2, 0.6)
+
+
+def test_angular_moments(ang):
+    # sum_k omega^x_k = int_S |s_x| ds = 2 pi ; sum_k a_k^{11} = int s_x^2 = 4pi/3
+    assert abs(ang['omx'].sum() - 2 * np.pi) < 2e-3
+    assert abs(ang['omy'].sum() - 2 * np.pi) < 2e-3
+    Minv = np.linalg.inv(ang['MSm'])
+    a11 = np.einsum('ki,kij,kj->k', ang['A1'], Minv, ang['A1'])
+    a12 = np.einsum('ki,kij,kj->k', ang['A1'], Minv, ang['A2'])
+    assert abs(a11.sum() - 4 * np.pi / 3) < 2e-3
+    assert abs(a12.sum()) < 1e-12
+    # s_n mu_k lies in the odd space: A_n(k) = M_k^- (row n of V_k)^T
+    V = ang['reps'].transpose(0, 2, 1)
+    assert np.allclose(ang['A1'], np.einsum('kij,kj->ki', ang['MSm'], V[:, 0, :]),
+                       atol=1e-14)
+    assert np.allclose(ang['A2'], np.einsum('kij,kj->ki', ang['MSm'], V[:, 1, :]),
+                       atol=1e-14)
+    # nodal odd basis: psi_{k,i}(v_j) = delta_ij
+    assert np.allclose(np.einsum('kij,kjl->kil', ang['Vinv'], V),
+                       np.eye(3)[None], atol=1e-13)
+
+
+def test_scattering_symmetry_and_normalisation(ang):
+    Sp, Sm, m = ang['Splus'], ang['Sminus'], ang['m']
+    assert np.abs(Sp - Sp.T).max() == 0.0
+    assert np.abs(Sm - Sm.T).max() == 0.0
+    assert np.all(Sp > 0)
+    # S^+ 1 = M_S^+ 1 up to quadrature: int k = 1; the rule under-integrates
+    rows = Sp.sum(1) / m
+    assert np.all(rows < 1.0) and np.all(rows > 1 - 3e-3)
+    # constants are (close to) the top eigenvector, eigenvalue g^0 = 1
+    lam = sla.eigh(Sp, np.diag(m), eigvals_only=True)[::-1]
+    assert abs(lam[0] - 1.0) < 3e-3
+    # global linear functions a.s: coefficient vector x_{(k,i)} = a . v_{k,i}
+    V = ang['reps']                               # (k, vertex, xyz)
+    MSm = oracle.assemble.block_diag3(ang['MSm'])
+    for a in np.eye(3):
+        x = (V @ a).ravel()
+        ratio = (x @ Sm @ x) / (x @ MSm @ x)
+        assert abs(ratio - 0.6) < 0.03           # eq. eigS with l = 1
+
+
+def test_scattering_isotropic_closed_form():
+    # g = 0: k = 1/(4 pi), S^+ = m m^T / (4 pi) and S^- = 0 exactly
+    an = oracle.assemble.angular_matrices(1, 0.0)
+    m = an['m']
+    assert np.allclose(an['Splus'], np.outer(m, m) / (4 * np.pi), rtol=1e-13,
+                       atol=0)
+    assert np.abs(an['Sminus']).max() < 1e-17
+
+
+def test_scattering_spectrum_clusters():
+    # eigenvalues of (S^+, M_S^+) cluster near g^l with multiplicity 2l+1 for
+    # even l; for odd l in (S^-, M_S^-) (eq. eigS, eq. lowrankscatteringmatrix)
+    g = 0.5
+    an = oracle.assemble.angular_matrices(2, g)
+    lp = sla.eigh(an['Splus'], np.diag(an['m']), eigvals_only=True)[::-1]
+    lm = sla.eigh(an['Sminus'], oracle.assemble.block_diag3(an['MSm']),
+                  eigvals_only=True)[::-1]
+    for lam, sizes, degs in ((lp, (1, 5, 9), (0, 2, 4)),
+                             (lm, (3, 7, 11), (1, 3, 5))):
+        start = 0
+        for size, l in zip(sizes, degs):
+            cl = lam[start:start + size]
+            assert np.all(np.abs(cl - g ** l) < 0.35 * g ** l + 0.01), (l, cl)
+            # a gap separates each cluster from the next
+            assert lam[start + size] < cl.min() - 0.05 * g ** l
+            start += size
+    # 0 <= lambda <= g (Section 5.1); the quadrature leaves the tail of
+    # the spectrum (g^l ~ 0) a little below zero
+    assert lm.max() <= g + 1e-3 and lm.min() > -1e-3
+
+
+# ------------------------------------------------------------ operators
+def test_apply_matches_dense_kron_and_mixed_system(tiny):
+    p, disc, ops = tiny
+    q = disc.source(p.q_nodal[0])
+    EK, E, f = dense.schur_matrix(disc)
+    rng = np.random.default_rng(1)
+    U = rng.standard_normal(q.shape)
+    ref = EK @ U.ravel()
+    assert np.abs(ops.apply_EK(U).ravel() - ref).max() < 1e-13 * np.abs(ref).max()
+    # E - K^+ is symmetric positive definite (Schur complement, Section 2.6)
+    assert np.abs(EK - EK.T).max() < 1e-13 * np.abs(EK).max()
+    sla.cholesky(EK)
+    up, _ = dense.mixed_solve(disc, q)
+    us = dense.schur_solve(disc, q)
+    assert np.abs(up - us).max() < 1e-12 * np.abs(us).max()
+
+
+def test_infinite_medium_limit():
+    # optically thick, homogeneous: away from the boundary u = q / sigma_a
+    # (int k = 1 means scattering only redistributes), so the even
+    # coefficient of mu_k is q / (sigma_t - sigma_s) at interior nodes.
+    # sigma_t = 40 on a 16x16 mesh: the centre lies 20 mean free paths from
+    # the vacuum boundary and the boundary layer is resolved (h sigma_t = 2.5)
+    for st, ss in ((40.0, 0.0), (40.0, 20.0)):
+        p = workloads.constant(16, 1, 0.5, st, ss, 1.0)
+        disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+        ops = oracle.Operators(disc, n_plus=2, n_minus=1)
+        q = disc.source(p.q_nodal[0])
+        u, info = richardson(ops, q, tol=1e-11, N=2)
+        x, y = workloads.node_xy(16)
+        centre = np.nonzero((np.abs(x - 0.5) < 1e-9) & (np.abs(y - 0.5) < 1e-9))[0][0]
+        # the discrete statement of the same limit: per node,
+        # (sigma_t M_S^+ - sigma_s S^+) u = q m, whose solution is 1/sigma_a
+        # up to the quadrature's row-sum defect of S^+
+        an = disc.an
+        ang = np.linalg.solve(st * np.diag(an['m']) - ss * an['Splus'], an['m'])
+        assert np.allclose(ang, 1.0 / (st - ss), rtol=5e-3)
+        assert np.allclose(u[centre], ang, rtol=1e-3), (u[centre], ang)
+
+
+def test_spectral_equivalence_E_E0(tiny):
+    # (1 - cg) E_0 <= E <= E_0 (eq. equivalence_bE_bE0)
+    p, disc, ops = tiny
+    n = disc.nRp * disc.nSp
+    I = np.eye(n)
+    E = np.stack([ops.apply_E(I[:, i].reshape(disc.nRp, -1)).ravel()
+                  for i in range(n)], 1)
+    E0 = np.stack([ops.apply_E0(I[:, i].reshape(disc.nRp, -1)).ravel()
+                   for i in range(n)], 1)
+    lam = sla.eigh(0.5 * (E + E.T), 0.5 * (E0 + E0.T), eigvals_only=True)
+    assert lam.min() >= (1 - disc.c * disc.g) - 1e-10
+    assert lam.max() <= 1 + 1e-10
+    # the direction blocks of E_0 reproduce its definition
+    e0 = ops.e0_blocks()
+    U = np.random.default_rng(2).standard_normal((disc.nRp, disc.nSp))
+    blk = np.stack([e0['blocks'][k] @ U[:, k] for k in range(disc.nSp)], 1)
+    assert np.abs(blk - ops.apply_E0(U)).max() < 1e-12 * np.abs(blk).max()
+    # E_0^{-1} inverts E_0
+    assert np.abs(ops.apply_E0(ops.solve_E0(U)) - U).max() < 1e-11
+
+
+def test_lemma_preconditioner_is_exact_inverse(tiny):
+    # Lemma apply_high_order_pre against a dense inverse of M^- - K^-_N
+    p, disc, ops = tiny
+    f = dense.full_matrices(disc)
+    lam, W = ops.eig_minus()
+    for N in (1, 3):
+        dN = oracle.d_of(N)
+        SN = disc.MSm @ W[:, :dN] @ np.diag(lam[:dN]) @ W[:, :dN].T @ disc.MSm
+        KN = np.kron(np.diag(disc.sp['Ms_minus']), SN)
+        B = np.random.default_rng(3).standard_normal((disc.nRm, disc.nSm))
+        ref = np.linalg.solve(f['Mm'] - KN, B.ravel())
+        got = ops.precond_MKN(B, N).ravel()
+        assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+    # with N covering every eigenvalue, the preconditioner is (M - K)^{-1}
+    Z = ops.apply_A(np.random.default_rng(4).standard_normal((disc.nRp, disc.nSp)))
+    x, it = ops.pcg_MKminus(Z, tol=1e-13)
+    assert np.abs(x - ops.solve_MKminus(Z)).max() < 1e-12 * np.abs(x).max()
+
+
+def test_isotropic_pcg_one_iteration():
+    # Table 1, column g = 0: K^- = K^-_N = 0, PCG converges in one iteration
+    p = workloads.constant(3, 1, 0.0, 1.0, 0.9, 1.0)
+    disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+    ops = oracle.Operators(disc, n_minus=5)
+    Z = ops.apply_A(np.random.default_rng(5).standard_normal((disc.nRp, disc.nSp)))
+    _, it = ops.pcg_MKminus(Z, tol=1e-13)
+    assert it == 1
+    # and E = E_0 (Remark after Remark ep_choices)
+    U = np.random.default_rng(6).standard_normal((disc.nRp, disc.nSp))
+    assert np.abs(ops.apply_E(U) - ops.apply_E0(U)).max() < 1e-12 * np.abs(ops.apply_E(U)).max()
+
+
+def test_no_scattering_one_iteration():
+    # sigma_s = 0: K = 0, c = 0, E_0 = E, so P_1 = E^{-1} and one Richardson
+    # step reaches the solution
+    p = workloads.constant(3, 1, 0.5, 2.0, 0.0, 1.0)
+    disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+    ops = oracle.Operators(disc, n_plus=2)
+    q = disc.source(p.q_nodal[0])
+    u, info = richardson(ops, q, tol=1e-11, N=2, l=1)
+    assert info['iterations'] == 1
+
+
+def _dense_ops(disc, ops, l, N):
+    n = disc.nRp * disc.nSp
+    I = np.eye(n)
+    cols = lambda fn: np.stack([fn(I[:, i].reshape(disc.nRp, -1)).ravel()
+                                for i in range(n)], 1)
+    EK = cols(ops.apply_EK)
+    P1 = cols(lambda x: ops.apply_P1(x, l))
+    co = Coarse(ops, N)
+    Wd = np.kron(np.eye(disc.nRp), co.W)      # row-major W_N (x) I
+    return EK, P1, co, Wd
+
+
+def test_preconditioner_identities_and_contraction(tiny):
+    p, disc, ops = tiny
+    l, N = 3, 2
+    EK, P1, co, Wd = _dense_ops(disc, ops, l, N)
+    n = EK.shape[0]
+    I = np.eye(n)
+    # P_1^l symmetric positive definite with E_0^{-1} <= P_1^l <= E^{-1}
+    # (Lemma preconditioner_pl)
+    assert np.abs(P1 - P1.T).max() < 1e-11 * np.abs(P1).max()
+    E = np.stack([ops.apply_E(I[:, i].reshape(disc.nRp, -1)).ravel()
+                  for i in range(n)], 1)
+    E0inv = np.stack([ops.solve_E0(I[:, i].reshape(disc.nRp, -1)).ravel()
+                      for i in range(n)], 1)
+    assert np.linalg.eigvalsh(0.5 * (P1 + P1.T) - E0inv).min() > -1e-10
+    assert np.linalg.eigvalsh(np.linalg.inv(E) - P1).min() > -1e-10
+    # E_c = W^T (E - K^+) W (brute force against the structured assembly)
+    Ec = Wd.T @ EK @ Wd
+    assert np.abs(co.Ec.toarray() - Ec).max() < 1e-11 * np.abs(Ec).max()
+    # factorisation I - P2 P1 (E-K) = (I - P_G)(I - P1 (E-K)) (Section 5)
+    PG = Wd @ np.linalg.solve(Ec, Wd.T @ EK)
+    P2P1 = P1 + Wd @ np.linalg.solve(Ec, Wd.T @ (I - EK @ P1))   # eq. product_pre
+    assert np.abs((I - P2P1 @ EK) - (I - PG) @ (I - P1 @ EK)).max() < 1e-10
+    # projection identity (I - P_G)^T (E-K) (I - P_G) = (E-K)(I - P_G)
+    lhs = (I - PG).T @ EK @ (I - PG)
+    assert np.abs(lhs - EK @ (I - PG)).max() < 1e-10 * np.abs(EK).max()
+    # eta <= c (eq. def_eta): eta^2 = largest eigenvalue of
+    # (E-K)^{1/2} T (E-K)^{-1} T^T (E-K)^{1/2} with T the iteration matrix
+    T = (I - PG) @ (I - P1 @ EK)
+    L = np.linalg.cholesky(0.5 * (EK + EK.T))
+    Tn = L.T @ T @ np.linalg.inv(L.T)
+    eta = np.linalg.norm(Tn, 2)
+    assert eta <= disc.c + 1e-10
+    # one oracle Richardson step equals the dense iteration matrix
+    q = disc.source(p.q_nodal[0])
+    u0 = np.random.default_rng(7).standard_normal(q.shape)
+    u1, _ = richardson(ops, q, maxit=1, tol=0.0, l=l, N=N, u0=u0, coarse=co)
+    dense_u1 = u0.ravel() - P2P1 @ (EK @ u0.ravel() - q.ravel())
+    assert np.abs(u1.ravel() - dense_u1).max() < 1e-11 * np.abs(dense_u1).max()
+    # errors contract by at least eta per step in the E-K norm
+    ustar = np.linalg.solve(EK, q.ravel())
+    err = lambda u: np.sqrt((u.ravel() - ustar) @ EK @ (u.ravel() - ustar))
+    u, e_prev = u0, err(u0)
+    for _ in range(4):
+        u, _ = richardson(ops, q, maxit=1, tol=0.0, l=l, N=N, u0=u, coarse=co)
+        e = err(u)
+        assert e <= eta * e_prev * (1 + 1e-8) + 1e-13
+        e_prev = e
+
+
+def test_fixed_point_and_cluster_rotation(tiny):
+    p, disc, ops = tiny
+    q = disc.source(p.q_nodal[0])
+    ustar = dense.schur_solve(disc, q).reshape(q.shape)
+    co = Coarse(ops, 2)
+    u1, info = richardson(ops, q, maxit=1, tol=0.0, N=2, u0=ustar, coarse=co)
+    assert np.abs(u1 - ustar).max() < 1e-12 * np.abs(ustar).max()
+    # P_G depends on span(W_N) only: rotate within the degree-2 cluster
+    rng = np.random.default_rng(8)
+    Q, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+    W2 = co.W.copy()
+    W2[:, 1:6] = co.W[:, 1:6] @ Q
+    EK, _, _ = dense.schur_matrix(disc)
+    Wd2 = np.kron(np.eye(disc.nRp), W2)
+    Wd = np.kron(np.eye(disc.nRp), co.W)
+    v = rng.standard_normal(EK.shape[0])
+    PG = Wd @ np.linalg.solve(Wd.T @ EK @ Wd, Wd.T @ EK @ v)
+    PG2 = Wd2 @ np.linalg.solve(Wd2.T @ EK @ Wd2, Wd2.T @ EK @ v)
+    assert np.abs(PG - PG2).max() < 1e-10 * np.abs(PG).max()
+
+
+def test_richardson_matches_direct_solve(tiny):
+    p, disc, ops = tiny
+    q = disc.source(p.q_nodal[0])
+    us = dense.schur_solve(disc, q)
+    u, info = richardson(ops, q, tol=1e-12, N=2)
+    assert np.abs(u.ravel() - us).max() < 1e-10 * np.abs(us).max()
+    assert info['iterations'] < 30
+    # residuals decrease monotonically in practice here
+    r = np.array(info['residuals'])
+    assert np.all(r[1:] < r[:-1])
