@@ -37,13 +37,15 @@ class Coarse:
     """The Galerkin subspace W^+ = W_N^+ (x) I and its matrix
     E_c = W^T (E - K^+) W (Section 5.4)."""
 
-    def __init__(self, ops, N=4):
+    def __init__(self, ops, N=4, W=None):
+        """W: optional basis of the angular subspace (n_S^+ x d_N); by
+        default the eigenvectors of the d_N largest eigenvalues of
+        (S^+, M_S^+) (Section 5.4)."""
         self.ops = ops
-        disc = ops.d
         self.N = N
         self.dN = d_of(N)
-        lam, W = ops.eig_plus()
-        self.W = W[:, :self.dN].copy()
+        lam, Wfull = ops.eig_plus()
+        self.W = Wfull[:, :self.dN].copy() if W is None else np.array(W)
         self.lam = lam[:self.dN].copy()
         self.Ec = self.assemble()
         self._lu = None
@@ -52,10 +54,11 @@ class Coarse:
         ops, disc = self.ops, self.ops.d
         smat, an = disc.sp, disc.an
         W, dN = self.W, self.dN
-        I = np.eye(dN)
-        # W^T M^+ W = I (x) M_t^+ ;  W^T K^+ W = Lambda_N (x) M_s^+
-        Ec = sp.kron(smat['Mt_plus'], I) - sp.kron(smat['Ms_plus'],
-                                                  np.diag(self.lam))
+        # W^T M^+ W = (W^T M_S^+ W) (x) M_t^+ and W^T K^+ W = (W^T S^+ W) (x)
+        # M_s^+; for M_S^+-orthonormal eigenvectors these are I and Lambda_N
+        # (Section 5.4), the general form serves any basis of the span.
+        Ec = (sp.kron(smat['Mt_plus'], W.T @ (ops.m[:, None] * W))
+              - sp.kron(smat['Ms_plus'], W.T @ ops.Sp @ W))
         # W^T R W: block (a,b) = sum_k R_k W(k,a) W(k,b)
         Ec = Ec + sp.kron(smat['Bx'], W.T @ (an['omx'][:, None] * W))
         Ec = Ec + sp.kron(smat['By'], W.T @ (an['omy'][:, None] * W))
