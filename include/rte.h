@@ -1,0 +1,200 @@
+/*
+ * rte.h - C ABI of the GB300 library for the preconditioned Richardson
+ * iteration of Dölz, Palii and Schlottbom (arXiv 2102.09038) for the
+ * even-parity anisotropic radiative transfer equation.
+ *
+ * Discretisation (Section 4): continuous P1 elements on a uniform
+ * "/"-triangulation of the unit square (n_R^+ = (m+1)^2 nodes,
+ * n_R^- = 2 m^2 cells) times piecewise-constant even (n_S^+) and piecewise-
+ * linear odd (n_S^- = 3 n_S^+) functions on a sphere mesh made by refining the
+ * octahedron ``sphere_levels`` times (8 * 4^levels triangles, one even
+ * function per antipodal pair).
+ *
+ * Vector layout.  Every even vector is nrhs consecutive matrices
+ * U^+ (n_R^+ x n_S^+) stored row-major: element (r, i, k) at
+ * ((r * n_R^+) + i) * n_S^+ + k, node i, direction k.  Odd vectors use
+ * n_R^- x n_S^- the same way (odd index 3k + c).  Coarse vectors use
+ * n_R^+ x d^+ (mode index fastest).
+ *
+ * Ownership.  The caller owns every vector pointer (device memory unless a
+ * name says host).  The handle owns the assembled matrices and a workspace
+ * sized for opts->max_rhs right-hand sides; it is freed by rte_destroy.
+ * All work is queued on the stream given to rte_setup; functions that
+ * return statistics synchronise that stream.
+ *
+ * Errors.  Every function returns RTE_OK (0) or one of the RTE_ERR_* codes
+ * and never aborts.  rte_last_error() gives a message for the calling
+ * thread's last failure.
+ */
+#ifndef RTE_H
+#define RTE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTE_OK 0
+#define RTE_ERR_ARG 1       /* invalid argument or size                      */
+#define RTE_ERR_NOMEM 2     /* device or host allocation failed              */
+#define RTE_ERR_DIVERGED 3  /* residual grew or became NaN/Inf               */
+#define RTE_ERR_MAXITER 4   /* iteration cap reached before the tolerance   */
+#define RTE_ERR_TIMEOUT 5   /* a bounded device-side wait gave up            */
+#define RTE_ERR_CUDA 6      /* a CUDA runtime or library call failed         */
+
+/* Arithmetic of the inner operators (the outer residual is always FP64). */
+#define RTE_FP64 0          /* every step in FP64                            */
+#define RTE_MIXED_FP32 1    /* inner applies in FP32 (TF32 tensor GEMMs)     */
+#define RTE_MIXED_BF16 2    /* inner applies in FP32, scattering GEMMs BF16  */
+
+/* How (M^- - K^-)^{-1} is applied inside Apply-E (Algorithm 1, line 2). */
+#define RTE_MK_EIGEN 0      /* exact, in the full eigenbasis of (S^-, M_S^-) */
+#define RTE_MK_PCG 1        /* PCG with the Lemma apply_high_order_pre prec. */
+
+typedef struct rte_handle rte_handle;
+
+/* The problem of Section 1, eq. (rte1)-(rte2), with vacuum inflow:
+ * sigma_t, sigma_s piecewise constant per cell (host arrays of length
+ * 2*mesh_m^2, 0 <= sigma_s < sigma_t), Henyey-Greenstein parameter
+ * 0 <= g < 1 (eq. HG-kernel1). */
+typedef struct {
+    int mesh_m;             /* m >= 1: m x m squares                         */
+    int sphere_levels;      /* 0..5: 8*4^levels sphere triangles            */
+    const double* sigma_t;  /* host, per cell                                */
+    const double* sigma_s;  /* host, per cell                                */
+    double g;
+} rte_problem;
+
+/* Method parameters.  Defaults (rte_default_options) follow Section 6:
+ * l = 4 inner steps for P_1^l, N^+ = 4 (d^+ = 15) for the subspace
+ * correction, N^- = 5 (d^- = 21) for the preconditioner of (M^- - K^-). */
+typedef struct {
+    int l;                  /* steps of P_1^l, eq. (applyP1)                 */
+    int n_plus;             /* even degree N^+ (0, 2, 4, ...); -1: no P_2    */
+    int n_minus;            /* odd degree N^- (1, 3, 5, ...)                 */
+    int precision;          /* RTE_FP64 | RTE_MIXED_FP32 | RTE_MIXED_BF16    */
+    int mk_route;           /* RTE_MK_EIGEN | RTE_MK_PCG                     */
+    double mk_tol;          /* relative residual of the (M^- - K^-) PCG      */
+    int mk_maxit;
+    double e0_tol;          /* relative residual per column of E_0 CG        */
+    int e0_maxit;
+    double coarse_tol;      /* relative residual of the E_c CG               */
+    int coarse_maxit;
+    int max_iter;           /* outer Richardson iterations                   */
+    int max_rhs;            /* workspace is sized for this many RHS          */
+} rte_options;
+
+typedef struct {
+    int iterations;             /* outer iterations taken                    */
+    double rel_residual;        /* max over RHS of ||r||_2 / ||q||_2 (FP64)  */
+    double energy_update;       /* max over RHS of ||u_n - u_{n-1}||_{E-K}   */
+    int e0_iters_last;          /* CG iterations of the last E_0^{-1}        */
+    int coarse_iters_last;      /* CG iterations of the last coarse solve    */
+    int mk_iters_last;          /* PCG iterations of the last (M-K)^{-1}     */
+    double* history;            /* optional host array: rel. residual per it */
+    int history_cap;            /* its capacity                              */
+    double seconds;             /* wall time of the solve                    */
+} rte_stats;
+
+/* Fills *opts with the defaults above (FP64, eigen route, tolerances
+ * 1e-12, 200 outer iterations, max_rhs 1). */
+int rte_default_options(rte_options* opts);
+
+/* Assembles the discrete system of Section 4 (eq. bKebKo, bMebMo, AR),
+ * the generalised eigenpairs of (S^+, M_S^+) and (S^-, M_S^-) (Section 5.1
+ * and 5.4), the direction blocks of E_0 (eq. equivalence_bE_bE0) and the
+ * coarse matrix E_c = W^T (E - K^+) W (Section 5.4, Algorithm 3 lines 1-4)
+ * and uploads them to the current device.  stream: a cudaStream_t (NULL
+ * for the legacy default stream).  On success *out owns all of it. */
+int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
+              rte_handle** out);
+
+/* Sizes of the discrete spaces: n_R^+, n_R^-, n_S^+, n_S^-, d^+, d^-. */
+int rte_sizes(const rte_handle* h, int* n_nodes, int* n_cells, int* n_dirs,
+              int* n_odd, int* d_plus, int* d_minus);
+
+/* q = l^+ for an isotropic source with nodal values q_nodal (device,
+ * nrhs x n_R^+) and vacuum inflow: q_{i,k} = (M q_h)_i * |K_k u -K_k|
+ * (Section 2.4, l^+(w) = (q, w)); l^- = 0 because the odd functions
+ * integrate to zero against an isotropic q. */
+int rte_rhs(rte_handle* h, const double* q_nodal, double* q, int nrhs);
+
+/* y = (E - K^+) x (eq. ep_discrete; Algorithm 1 for E), device vectors. */
+int rte_apply(rte_handle* h, const double* x, double* y, int nrhs);
+
+/* s = P_2 P_1^l r: P_1^l of eq. (applyP1) and, when with_p2 != 0, the
+ * subspace correction of eq. (product_pre):
+ * s = P_1 r + W E_c^{-1} W^T (r - (E - K^+) P_1 r). */
+int rte_precond(rte_handle* h, const double* r, double* s, int nrhs,
+                int with_p2);
+
+/* Algorithm 3: preconditioned Richardson iteration for (E - K^+) u = q,
+ * eq. (Richardson_discrete), from the initial guess held in u on entry,
+ * until ||r_n||_2 <= tol ||q||_2 for every RHS (r_n in FP64).  stats may be
+ * NULL.  Returns RTE_ERR_MAXITER if opts.max_iter is reached and
+ * RTE_ERR_DIVERGED on a NaN/Inf residual. */
+int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
+              rte_stats* stats);
+
+/* Individual steps of the iteration, for testing and profiling (device
+ * vectors, sizes as in the header comment):
+ *  RTE_OP_A          odd  <- even : A x = sum_n A_n (x) D_n     (eq. AR)
+ *  RTE_OP_AT         even <- odd  : A^T z
+ *  RTE_OP_KPLUS      even <- even : K^+ x = (S^+ (x) M_s^+) x (eq. bKebKo)
+ *  RTE_OP_MK         odd  <- odd  : (M^- - K^-) z
+ *  RTE_OP_MK_INV     odd  <- odd  : (M^- - K^-)^{-1} z by mk_route
+ *  RTE_OP_MK_PREC    odd  <- odd  : (M^- - K^-_N)^{-1} z, eq. (MmKprecond)
+ *  RTE_OP_E          even <- even : E x (Algorithm 1)
+ *  RTE_OP_E0_INV     even <- even : E_0^{-1} x by per-direction CG
+ *  RTE_OP_P1         even <- even : P_1^l x (Algorithm 2, eq. applyP1)
+ *  RTE_OP_RESTRICT   coarse <- even: W^T x = X W_N^+
+ *  RTE_OP_PROLONG    even <- coarse: W u_c = U_c (W_N^+)^T
+ *  RTE_OP_EC         coarse <- coarse: E_c u_c
+ *  RTE_OP_EC_INV     coarse <- coarse: E_c^{-1} u_c by CG            */
+#define RTE_OP_A 1
+#define RTE_OP_AT 2
+#define RTE_OP_KPLUS 3
+#define RTE_OP_MK 4
+#define RTE_OP_MK_INV 5
+#define RTE_OP_MK_PREC 6
+#define RTE_OP_E 7
+#define RTE_OP_E0_INV 8
+#define RTE_OP_P1 9
+#define RTE_OP_RESTRICT 10
+#define RTE_OP_PROLONG 11
+#define RTE_OP_EC 12
+#define RTE_OP_EC_INV 13
+int rte_operator(rte_handle* h, int op, const double* in, double* out,
+                 int nrhs);
+
+/* Copies an assembled matrix to host memory (for checks against an
+ * independent assembly).  what: 0 S^+ (n_S^+^2), 1 S^- (n_S^-^2),
+ * 2 M_S^+ diagonal (n_S^+), 3 M_S^- blocks (n_S^+ x 9), 4 A_1 (n_S^+ x 3),
+ * 5 A_2 (n_S^+ x 3), 6 omega^x (n_S^+), 7 omega^y (n_S^+), 8 Lambda^+
+ * (n_S^+, non-increasing), 9 Lambda^- (n_S^-), 10 W_N^+ (n_S^+ x d^+),
+ * 11 E_c nonzero blocks (count x d^+ x d^+, CSR order of the node stencil).
+ * n: capacity of host_out in doubles; returns RTE_ERR_ARG if too small. */
+int rte_export(const rte_handle* h, int what, double* host_out, size_t n);
+
+/* Per-kernel device time (milliseconds) accumulated since the last reset,
+ * measured with CUDA events on the handle's stream when timing is enabled:
+ * names[i] and ms[i] for i < *count (capacity cap). */
+int rte_timing_enable(rte_handle* h, int on);
+int rte_timing_read(rte_handle* h, const char** names, double* ms,
+                    long long* launches, int cap, int* count);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles, all threads), for counting launches inside a timed region. */
+long long rte_kernel_launches(void);
+
+void rte_destroy(rte_handle* h);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* rte_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTE_H */

@@ -1,0 +1,274 @@
+"""Python binding of librte, the GB300 library for the preconditioned
+Richardson iteration of Dölz, Palii and Schlottbom (arXiv 2102.09038) for the
+even-parity anisotropic radiative transfer equation.
+
+The binding only marshals arguments: every step of the iteration runs in the
+library's CUDA kernels (include/rte.h).  Device vectors are torch CUDA
+tensors (float64, contiguous) passed by pointer; torch provides memory and
+streams only.  There is no CPU fallback: constructing a ``Solver`` without
+the built library or without a CUDA device raises.
+"""
+import ctypes
+import os
+
+__all__ = ['Solver', 'RteError', 'load', 'OPS', 'FP64', 'MIXED_FP32',
+           'MIXED_BF16', 'MK_EIGEN', 'MK_PCG']
+
+FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
+MK_EIGEN, MK_PCG = 0, 1
+OPS = dict(A=1, AT=2, KPLUS=3, MK=4, MK_INV=5, MK_PREC=6, E=7, E0_INV=8,
+           P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13)
+EXPORTS = dict(Splus=0, Sminus=1, m=2, MSm=3, A1=4, A2=5, omx=6, omy=7,
+               lamP=8, lamM=9, WpN=10, Ec=11)
+ERRORS = {1: 'RTE_ERR_ARG', 2: 'RTE_ERR_NOMEM', 3: 'RTE_ERR_DIVERGED',
+          4: 'RTE_ERR_MAXITER', 5: 'RTE_ERR_TIMEOUT', 6: 'RTE_ERR_CUDA'}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, '_build', 'librte.so')
+
+
+class RteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__('%s: %s' % (ERRORS.get(code, code), msg))
+        self.code = code
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [('mesh_m', ctypes.c_int), ('sphere_levels', ctypes.c_int),
+                ('sigma_t', ctypes.POINTER(ctypes.c_double)),
+                ('sigma_s', ctypes.POINTER(ctypes.c_double)),
+                ('g', ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [('l', ctypes.c_int), ('n_plus', ctypes.c_int),
+                ('n_minus', ctypes.c_int), ('precision', ctypes.c_int),
+                ('mk_route', ctypes.c_int), ('mk_tol', ctypes.c_double),
+                ('mk_maxit', ctypes.c_int), ('e0_tol', ctypes.c_double),
+                ('e0_maxit', ctypes.c_int), ('coarse_tol', ctypes.c_double),
+                ('coarse_maxit', ctypes.c_int), ('max_iter', ctypes.c_int),
+                ('max_rhs', ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [('iterations', ctypes.c_int), ('rel_residual', ctypes.c_double),
+                ('energy_update', ctypes.c_double),
+                ('e0_iters_last', ctypes.c_int),
+                ('coarse_iters_last', ctypes.c_int),
+                ('mk_iters_last', ctypes.c_int),
+                ('history', ctypes.POINTER(ctypes.c_double)),
+                ('history_cap', ctypes.c_int), ('seconds', ctypes.c_double)]
+
+
+_lib = None
+EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs',
+            'rte_apply', 'rte_precond', 'rte_solve', 'rte_operator',
+            'rte_export', 'rte_timing_enable', 'rte_timing_read',
+            'rte_kernel_launches', 'rte_destroy', 'rte_last_error']
+
+
+def load(path=LIB_PATH):
+    """Load librte.so and declare its signatures (no GPU needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError('librte.so not built: run __graft_entry__.build() '
+                          '(expected at %s)' % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    lib.rte_default_options.argtypes = [ctypes.POINTER(_Options)]
+    lib.rte_setup.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Options),
+                              P, ctypes.POINTER(P)]
+    lib.rte_sizes.argtypes = [P] + [ctypes.POINTER(I)] * 6
+    lib.rte_rhs.argtypes = [P, P, P, I]
+    lib.rte_apply.argtypes = [P, P, P, I]
+    lib.rte_precond.argtypes = [P, P, P, I, I]
+    lib.rte_solve.argtypes = [P, P, P, I, D, ctypes.POINTER(_Stats)]
+    lib.rte_operator.argtypes = [P, I, P, P, I]
+    lib.rte_export.argtypes = [P, I, ctypes.POINTER(D), ctypes.c_size_t]
+    lib.rte_timing_enable.argtypes = [P, I]
+    lib.rte_timing_read.argtypes = [P, ctypes.POINTER(ctypes.c_char_p),
+                                    ctypes.POINTER(D),
+                                    ctypes.POINTER(ctypes.c_longlong), I,
+                                    ctypes.POINTER(I)]
+    lib.rte_kernel_launches.argtypes = []
+    lib.rte_kernel_launches.restype = ctypes.c_longlong
+    lib.rte_destroy.argtypes = [P]
+    lib.rte_destroy.restype = V
+    lib.rte_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ('rte_destroy', 'rte_last_error', 'rte_kernel_launches'):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def kernel_launches():
+    """Kernels launched by librte in this process so far."""
+    return int(load().rte_kernel_launches())
+
+
+def _check(rc):
+    if rc != 0:
+        raise RteError(rc, _lib.rte_last_error().decode())
+
+
+def default_options(**kw):
+    lib = load()
+    o = _Options()
+    _check(lib.rte_default_options(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One assembled problem on the current CUDA device.
+
+    problem: an object with m, levels, g, sigma_t, sigma_s (e.g.
+    ``workloads.Problem``); options: keyword overrides of rte_options.
+    """
+
+    def __init__(self, problem, stream=None, **options):
+        import numpy as np
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError('librte needs a CUDA device; there is no CPU path')
+        lib = load()
+        self.torch = torch
+        self._st = np.ascontiguousarray(problem.sigma_t, dtype=np.float64)
+        self._ss = np.ascontiguousarray(problem.sigma_s, dtype=np.float64)
+        pr = _Problem(int(problem.m), int(problem.levels),
+                      self._st.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      self._ss.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      float(problem.g))
+        self.options = default_options(**options)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.rte_setup(ctypes.byref(pr), ctypes.byref(self.options),
+                             ctypes.c_void_p(self.stream.cuda_stream),
+                             ctypes.byref(h)))
+        self._h = h
+        vals = [ctypes.c_int() for _ in range(6)]
+        _check(lib.rte_sizes(h, *[ctypes.byref(v) for v in vals]))
+        (self.n_nodes, self.n_cells, self.n_dirs, self.n_odd, self.d_plus,
+         self.d_minus) = [v.value for v in vals]
+
+    # ------------------------------------------------------------ shapes
+    def even(self, nrhs=1):
+        return self.torch.zeros((nrhs, self.n_nodes, self.n_dirs),
+                                dtype=self.torch.float64, device='cuda')
+
+    def odd(self, nrhs=1):
+        return self.torch.zeros((nrhs, self.n_cells, self.n_odd),
+                                dtype=self.torch.float64, device='cuda')
+
+    def coarse(self, nrhs=1):
+        return self.torch.zeros((nrhs, self.n_nodes, self.d_plus),
+                                dtype=self.torch.float64, device='cuda')
+
+    def _vec(self, t):
+        if not (t.is_cuda and t.dtype == self.torch.float64 and t.is_contiguous()):
+            raise ValueError('expected a contiguous float64 CUDA tensor')
+        return _ptr(t)
+
+    # --------------------------------------------------------------- ABI
+    def rhs(self, q_nodal, out=None):
+        q_nodal = q_nodal.reshape(-1, self.n_nodes)
+        nrhs = q_nodal.shape[0]
+        out = self.even(nrhs) if out is None else out
+        _check(_lib.rte_rhs(self._h, self._vec(q_nodal), self._vec(out), nrhs))
+        return out
+
+    def apply(self, x, out=None):
+        out = self.torch.empty_like(x) if out is None else out
+        _check(_lib.rte_apply(self._h, self._vec(x), self._vec(out), x.shape[0]))
+        return out
+
+    def precond(self, r, with_p2=True, out=None):
+        out = self.torch.empty_like(r) if out is None else out
+        _check(_lib.rte_precond(self._h, self._vec(r), self._vec(out),
+                                r.shape[0], int(with_p2)))
+        return out
+
+    def solve(self, q, u=None, tol=1e-8, history=256):
+        u = self.torch.zeros_like(q) if u is None else u
+        hist = (ctypes.c_double * history)()
+        st = _Stats()
+        st.history = ctypes.cast(hist, ctypes.POINTER(ctypes.c_double))
+        st.history_cap = history
+        rc = _lib.rte_solve(self._h, self._vec(q), self._vec(u), q.shape[0],
+                            float(tol), ctypes.byref(st))
+        info = dict(iterations=st.iterations, rel_residual=st.rel_residual,
+                    energy_update=st.energy_update,
+                    e0_iters=st.e0_iters_last,
+                    coarse_iters=st.coarse_iters_last,
+                    mk_iters=st.mk_iters_last, seconds=st.seconds,
+                    history=list(hist[:min(history, st.iterations + 1)]),
+                    status=rc)
+        if rc not in (0, 4):
+            _check(rc)
+        return u, info
+
+    def operator(self, name, x, out):
+        _check(_lib.rte_operator(self._h, OPS[name], self._vec(x),
+                                 self._vec(out), x.shape[0]))
+        return out
+
+    def export(self, name):
+        """Host copy of an assembled matrix (see rte_export in rte.h)."""
+        import numpy as np
+        n, nm, dp = self.n_dirs, self.n_odd, self.d_plus
+        size = dict(Splus=n * n, Sminus=nm * nm, m=n, MSm=9 * n, A1=3 * n,
+                    A2=3 * n, omx=n, omy=n, lamP=n, lamM=nm, WpN=n * max(dp, 1))
+        if name == 'Ec':
+            count = 1
+            while True:   # E_c block count is the stencil size: grow to fit
+                buf = np.zeros(count * dp * dp, dtype=np.float64)
+                rc = _lib.rte_export(self._h, EXPORTS[name],
+                                     buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     buf.size)
+                if rc == 0:
+                    return buf[:self._ec_blocks() * dp * dp]
+                count *= 2
+        buf = np.zeros(size[name], dtype=np.float64)
+        _check(_lib.rte_export(self._h, EXPORTS[name],
+                               buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               buf.size))
+        return buf
+
+    def _ec_blocks(self):
+        m = int(round(self.n_nodes ** 0.5)) - 1
+        # 7-point stencil of the "/"-triangulation: (m+1)^2 diagonal entries,
+        # 3 m (m+1) horizontal/vertical edge pairs and m^2 diagonal edges
+        return (m + 1) ** 2 + 2 * (2 * m * (m + 1) + m * m)
+
+    def timing(self, on=True):
+        _check(_lib.rte_timing_enable(self._h, int(on)))
+
+    def timing_read(self, cap=64):
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        cnt = (ctypes.c_longlong * cap)()
+        n = ctypes.c_int()
+        _check(_lib.rte_timing_read(self._h, names, ms, cnt, cap,
+                                    ctypes.byref(n)))
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n.value, cap))}
+
+    def close(self):
+        if getattr(self, '_h', None):
+            _lib.rte_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

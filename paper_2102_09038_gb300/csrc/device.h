@@ -1,0 +1,134 @@
+// Device-resident data of one assembled problem and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace rte {
+
+// Raw device pointers of an assembled system (owned by rte_handle).
+struct DevSystem {
+    int nRp, nRm, nSp, nSm, dP, dM, nnz;
+    double g, c, gamma;
+    // spatial
+    const int* cell_nodes;     // [nRm][3]
+    const double* cell_D;      // [nRm][6]  D1[a], D2[a]
+    const double* cell_at;     // [nRm]     |T| sigma_t
+    const double* cell_as;     // [nRm]     |T| sigma_s
+    const int* adj_ptr;        // [nRp+1]   node -> incident cells
+    const int* adj_cell;
+    const int* adj_loc;
+    const int* st_ptr;         // [nRp+1]   7-point stencil
+    const int* st_col;         // [nnz]
+    const int* st_diag;        // [nRp]
+    const double* sval;        // [kSlots][nnz]
+    const float* sval_f;       // [kSlots][nnz] (FP32 copy)
+    // angular
+    const double* ang_m;       // [nSp]
+    const double* ang_omx;     // [nSp]
+    const double* ang_omy;     // [nSp]
+    const double* ang_A1;      // [nSp][3]
+    const double* ang_A2;      // [nSp][3]
+    const double* ang_MSm;     // [nSp][9]
+    const double* ang_MSm_inv; // [nSp][9]
+    const double* e0s;         // [nSp][6]  gamma a11, gamma a12, gamma a22, omx, omy, m
+    const double* Sp;          // [nSp][nSp]
+    const double* Sm;          // [nSm][nSm]
+    const double* Vm;          // [nSm][nSm]  eigenvectors of (S^-, M_S^-) as columns
+    const double* VmT;         // [nSm][nSm]
+    const double* lamM;        // [nSm]       non-increasing
+    const double* WmN;         // [nSm][dM]
+    const double* WmNT;        // [dM][nSm]
+    const double* WpN;         // [nSp][dP]
+    const double* WpNT;        // [dP][nSp]
+    const double* lamP;        // [nSp]
+    // coarse matrix E_c: blocks [nnz][dP][dP] and inverse diagonal blocks
+    const double* ec_val;
+    const double* ec_dinv;     // [nRp][dP][dP]
+};
+
+// Status words written by persistent kernels (bounded waits, iteration counts).
+struct SolveStatus {
+    int iterations;
+    int timed_out;
+    int converged;
+    int pad;
+};
+
+// ------------------------------------------------------------- launchers
+// C = alpha * op(A B) + beta * C for row-major A (M x K), B (K x N),
+// C (M x N); epi selects a per-element factor applied to A B:
+//   0: none
+//   1: 1 / (at[r % rows] - lam[c] * as[r % rows])           eigenbasis of M-K
+//   2: 1 / (at - lam as) - 1 / at                            Lemma precond.
+void gemm_f64(cudaStream_t s, int M, int N, int K, const double* A, int lda,
+              const double* B, int ldb, double* C, int ldc, double alpha,
+              double beta, int epi, const double* at, const double* as,
+              const double* lam, int rows);
+
+// Z = A U (eq. AR): even (nrhs x nRp x nSp) -> odd (nrhs x nRm x nSm)
+void apply_A(cudaStream_t s, const DevSystem& d, const double* U, double* Z,
+             int nrhs);
+
+// Y = [A^T Zp] + [M^+ X + R X] - [M_s^+ V] (terms selected by flags):
+// flags bit0: A^T Zp, bit1: M^+ X + R X, bit2: - M_s^+ V (V = X S^+).
+void apply_even(cudaStream_t s, const DevSystem& d, const double* Zp,
+                const double* X, const double* V, double* Y, int nrhs,
+                int flags);
+
+// Y = M_t^- Z M_S^- - G with G already = M_s^- Z S^- scaled: here
+// Y = at_j (Z_j M_S^-) - as_j G_j  (G = Z S^-).
+void mk_combine(cudaStream_t s, const DevSystem& d, const double* Z,
+                const double* G, double* Y, int nrhs);
+
+// Y = (B M_S^{-1}) / at  (high-order part of eq. MmKprecond).
+void mk_minv_scale(cudaStream_t s, const DevSystem& d, const double* B,
+                   double* Y, int nrhs);
+
+// q_{r,i,k} = (M q_nodal_r)_i m_k
+void rhs_source(cudaStream_t s, const DevSystem& d, const double* qn,
+                double* q, int nrhs);
+
+// per-RHS reductions over blocks of length len: out[r] = sum x*y
+// (deterministic two-pass; partial must hold nrhs * 1024 doubles)
+void dot_per_rhs(cudaStream_t s, const double* x, const double* y, size_t len,
+                 int nrhs, double* partial, double* out);
+
+// y = a[r] * x + b[r] * y per RHS block (a, b device arrays or nullptr for
+// the constants ca, cb).
+void axpby_per_rhs(cudaStream_t s, const double* x, double* y, size_t len,
+                   int nrhs, const double* a, double ca, const double* b,
+                   double cb);
+
+// E_0^{-1} B by one persistent CG over all (rhs, direction) columns.
+int e0_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,
+          int nrhs, double tol, int maxit, void* work, size_t work_bytes,
+          SolveStatus* status_dev);
+size_t e0_cg_work_bytes(const DevSystem& d, int nrhs);
+
+// E_c^{-1} B by one persistent block-Jacobi CG per RHS.
+int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,
+              int nrhs, double tol, int maxit, void* work, size_t work_bytes,
+              SolveStatus* status_dev);
+size_t coarse_cg_work_bytes(const DevSystem& d, int nrhs);
+
+// y = E_c x
+void coarse_apply(cudaStream_t s, const DevSystem& d, const double* X,
+                  double* Y, int nrhs);
+
+// Assembly of S^+ and S^- by the quadrature rule (setup).
+struct QuadDev {
+    const double *near_pts, *near_w, *near_psi, *far_pts, *far_w, *far_psi;
+    const int *near_ptr, *near_idx;
+    int qn, qf;
+};
+void assemble_scattering(cudaStream_t s, int n, double g, const QuadDev& q,
+                         double* Sp, double* Sm);
+
+int device_sm_count();
+
+// Count of kernel launches issued by the library (host-side counter).
+void count_launches(long long n);
+long long launches_total();
+
+}  // namespace rte

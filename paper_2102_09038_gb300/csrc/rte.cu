@@ -1,0 +1,1009 @@
+// C ABI of the library: setup (Section 4 assembly, Section 5.1/5.4 eigenpairs
+// and coarse matrix), the operator applies of Algorithm 1, the preconditioner
+// of Algorithm 2 / eq. (product_pre) and the Richardson loop of Algorithm 3.
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "rte_internal.h"
+
+namespace rte {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct TimerRec {
+    int name;
+    cudaEvent_t a, b;
+};
+
+struct rte_handle {
+    rte_options opt;
+    cudaStream_t stream = nullptr;
+    DevSystem d{};
+    std::vector<void*> allocs;
+    // host copies kept for rte_export
+    std::vector<double> h_Sp, h_Sm, h_m, h_MSm, h_A1, h_A2, h_omx, h_omy, h_lamP,
+        h_lamM, h_WpN, h_ec;
+    // workspace
+    int cap_rhs = 0;
+    double *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr;   // odd
+    double *z5 = nullptr, *z6 = nullptr, *z7 = nullptr, *zsk = nullptr;  // PCG route
+    double *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr, *e5 = nullptr,
+           *e6 = nullptr, *e7 = nullptr, *e8 = nullptr;                     // even
+    double *c1 = nullptr, *c2 = nullptr;                                    // coarse
+    double *partial = nullptr, *sc = nullptr;                               // reductions
+    void* e0work = nullptr;
+    size_t e0bytes = 0;
+    void* cowork = nullptr;
+    size_t cobytes = 0;
+    SolveStatus* status = nullptr;
+    // statistics of the last inner solves
+    int e0_iters = 0, co_iters = 0, mk_iters = 0;
+    // timing
+    bool timing = false;
+    std::vector<std::string> tnames;
+    std::vector<TimerRec> trecs;
+    std::vector<double> tms;
+    std::vector<long long> tcount;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(rte_handle* h, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(RTE_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->allocs.push_back((void*)*p);
+    return RTE_OK;
+}
+
+template <typename T>
+int upload(rte_handle* h, const T** dst, const std::vector<T>& src) {
+    T* p = nullptr;
+    RTE_TRY(dalloc(h, &p, src.size()));
+    if (!src.empty())
+        RTE_CUDA_TRY(cudaMemcpyAsync(p, src.data(), src.size() * sizeof(T),
+                                     cudaMemcpyHostToDevice, h->stream));
+    *dst = p;
+    return RTE_OK;
+}
+
+// ------------------------------------------------------------- timing
+struct Scope {
+    rte_handle* h;
+    int idx = -1;
+    cudaEvent_t b{};
+    Scope(rte_handle* hh, const char* name) : h(hh) {
+        if (!h->timing) return;
+        for (size_t i = 0; i < h->tnames.size(); ++i)
+            if (h->tnames[i] == name) idx = (int)i;
+        if (idx < 0) {
+            idx = (int)h->tnames.size();
+            h->tnames.push_back(name);
+            h->tms.push_back(0.0);
+            h->tcount.push_back(0);
+        }
+        cudaEvent_t a;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, h->stream);
+        h->trecs.push_back({idx, a, b});
+    }
+    ~Scope() {
+        if (idx >= 0) cudaEventRecord(b, h->stream);
+    }
+};
+
+void flush_timers(rte_handle* h) {
+    if (h->trecs.empty()) return;
+    cudaStreamSynchronize(h->stream);
+    for (auto& t : h->trecs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+            h->tms[t.name] += ms;
+            h->tcount[t.name] += 1;
+        }
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    h->trecs.clear();
+}
+
+// ---------------------------------------------------------- eigenpairs
+// Symmetric eigen-decomposition of an n x n matrix on the device
+// (cusolverDnDsyevd, setup only).  On return C holds the eigenvectors as
+// rows (row-major view of the column-major output) and w the ascending
+// eigenvalues.
+int sym_eig(rte_handle* h, std::vector<double>& C, std::vector<double>& w, int n) {
+    cusolverDnHandle_t cs = nullptr;
+    if (cusolverDnCreate(&cs) != CUSOLVER_STATUS_SUCCESS)
+        return fail(RTE_ERR_CUDA, "cusolverDnCreate failed");
+    cusolverDnSetStream(cs, h->stream);
+    double *dA = nullptr, *dW = nullptr, *dWork = nullptr;
+    int* dInfo = nullptr;
+    int rc = RTE_OK;
+    int lwork = 0;
+    if (cudaMalloc(&dA, sizeof(double) * (size_t)n * n) != cudaSuccess ||
+        cudaMalloc(&dW, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&dInfo, sizeof(int)) != cudaSuccess) {
+        rc = fail(RTE_ERR_NOMEM, "eigensolver allocation failed");
+    }
+    if (rc == RTE_OK) {
+        cudaMemcpyAsync(dA, C.data(), sizeof(double) * (size_t)n * n,
+                        cudaMemcpyHostToDevice, h->stream);
+        if (cusolverDnDsyevd_bufferSize(cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                        n, dA, n, dW, &lwork) != CUSOLVER_STATUS_SUCCESS)
+            rc = fail(RTE_ERR_CUDA, "syevd_bufferSize failed");
+    }
+    if (rc == RTE_OK && cudaMalloc(&dWork, sizeof(double) * (size_t)std::max(lwork, 1)) != cudaSuccess)
+        rc = fail(RTE_ERR_NOMEM, "eigensolver workspace allocation failed");
+    if (rc == RTE_OK &&
+        cusolverDnDsyevd(cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dW,
+                         dWork, lwork, dInfo) != CUSOLVER_STATUS_SUCCESS)
+        rc = fail(RTE_ERR_CUDA, "syevd failed");
+    if (rc == RTE_OK) {
+        int info = 0;
+        w.resize(n);
+        cudaMemcpyAsync(C.data(), dA, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToHost,
+                        h->stream);
+        cudaMemcpyAsync(w.data(), dW, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+        cudaMemcpyAsync(&info, dInfo, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+            rc = fail(RTE_ERR_CUDA, "eigensolver synchronisation failed");
+        else if (info != 0)
+            rc = fail(RTE_ERR_CUDA, "syevd did not converge");
+    }
+    cudaFree(dA);
+    cudaFree(dW);
+    cudaFree(dWork);
+    cudaFree(dInfo);
+    cusolverDnDestroy(cs);
+    return rc;
+}
+
+bool chol_inv_sym(int d, const double* A, double* Ainv) {
+    // Gauss-Jordan inverse with partial pivoting of a small d x d matrix
+    std::vector<double> M(A, A + d * d), I(d * d, 0.0);
+    for (int i = 0; i < d; ++i) I[i * d + i] = 1.0;
+    for (int c = 0; c < d; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < d; ++r)
+            if (std::fabs(M[r * d + c]) > std::fabs(M[piv * d + c])) piv = r;
+        if (!(std::fabs(M[piv * d + c]) > 0)) return false;
+        if (piv != c)
+            for (int k = 0; k < d; ++k) {
+                std::swap(M[c * d + k], M[piv * d + k]);
+                std::swap(I[c * d + k], I[piv * d + k]);
+            }
+        const double inv = 1.0 / M[c * d + c];
+        for (int k = 0; k < d; ++k) {
+            M[c * d + k] *= inv;
+            I[c * d + k] *= inv;
+        }
+        for (int r = 0; r < d; ++r) {
+            if (r == c) continue;
+            const double f = M[r * d + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < d; ++k) {
+                M[r * d + k] -= f * M[c * d + k];
+                I[r * d + k] -= f * I[c * d + k];
+            }
+        }
+    }
+    std::memcpy(Ainv, I.data(), sizeof(double) * d * d);
+    return true;
+}
+
+// 3x3 lower Cholesky factor
+bool chol3(const double* A, double* L) {
+    for (int i = 0; i < 9; ++i) L[i] = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[3 * i + j];
+            for (int k = 0; k < j; ++k) s -= L[3 * i + k] * L[3 * j + k];
+            if (i == j) {
+                if (!(s > 0)) return false;
+                L[3 * i + i] = std::sqrt(s);
+            } else {
+                L[3 * i + j] = s / L[3 * j + j];
+            }
+        }
+    return true;
+}
+
+void inv_lower3(const double* L, double* Li) {
+    for (int i = 0; i < 9; ++i) Li[i] = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        for (int i = 0; i < 3; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) s -= L[3 * i + k] * Li[3 * k + c];
+            Li[3 * i + c] = s / L[3 * i + i];
+        }
+    }
+}
+
+// ------------------------------------------------------------ workspace
+int ensure_workspace(rte_handle* h, int nrhs) {
+    if (nrhs <= h->cap_rhs) return RTE_OK;
+    return fail(RTE_ERR_ARG, "nrhs exceeds opts.max_rhs given to rte_setup");
+}
+
+int alloc_workspace(rte_handle* h, int nrhs) {
+    const DevSystem& d = h->d;
+    const size_t ne = (size_t)nrhs * d.nRp * d.nSp;
+    const size_t no = (size_t)nrhs * d.nRm * d.nSm;
+    const size_t nc = (size_t)nrhs * d.nRp * std::max(d.dP, 1);
+    RTE_TRY(dalloc(h, &h->z1, no));
+    RTE_TRY(dalloc(h, &h->z2, no));
+    RTE_TRY(dalloc(h, &h->z3, no));
+    RTE_TRY(dalloc(h, &h->z4, no));
+    if (h->opt.mk_route == RTE_MK_PCG) {
+        RTE_TRY(dalloc(h, &h->z5, no));
+        RTE_TRY(dalloc(h, &h->z6, no));
+        RTE_TRY(dalloc(h, &h->z7, no));
+    }
+    RTE_TRY(dalloc(h, &h->zsk, (size_t)nrhs * d.nRm * d.dM));
+    double** ev[] = {&h->e1, &h->e2, &h->e3, &h->e4, &h->e5, &h->e6, &h->e7, &h->e8};
+    for (auto p : ev) RTE_TRY(dalloc(h, p, ne));
+    RTE_TRY(dalloc(h, &h->c1, nc));
+    RTE_TRY(dalloc(h, &h->c2, nc));
+    RTE_TRY(dalloc(h, &h->partial, (size_t)nrhs * 1024));
+    RTE_TRY(dalloc(h, &h->sc, (size_t)nrhs * 16));
+    h->e0bytes = e0_cg_work_bytes(d, nrhs);
+    char* w = nullptr;
+    RTE_TRY(dalloc(h, &w, h->e0bytes));
+    h->e0work = w;
+    h->cobytes = coarse_cg_work_bytes(d, nrhs);
+    RTE_TRY(dalloc(h, &w, h->cobytes));
+    h->cowork = w;
+    RTE_TRY(dalloc(h, &h->status, 1));
+    h->cap_rhs = nrhs;
+    return RTE_OK;
+}
+
+// --------------------------------------------------------- operators
+// Z2 = (M^- - K^-)^{-1} Z1 in the full eigenbasis of (S^-, M_S^-):
+// per cell j, (|T_j| (sigma_t M_S^- - sigma_s S^-))^{-1} = V diag(1/(at - lam as)) V^T
+int mk_inv_eigen(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
+    const DevSystem& d = h->d;
+    const int rows = nrhs * d.nRm;
+    {
+        Scope sc(h, "gemm_mk_eig1");
+        gemm_f64(h->stream, rows, d.nSm, d.nSm, Z1, d.nSm, d.Vm, d.nSm, h->z4, d.nSm, 1.0,
+                 0.0, 1, d.cell_at, d.cell_as, d.lamM, d.nRm);
+    }
+    {
+        Scope sc(h, "gemm_mk_eig2");
+        gemm_f64(h->stream, rows, d.nSm, d.nSm, h->z4, d.nSm, d.VmT, d.nSm, Z2, d.nSm, 1.0,
+                 0.0, 0, nullptr, nullptr, nullptr, 1);
+    }
+    return RTE_OK;
+}
+
+// x = (M^- - K^-_N)^{-1} b by eq. (MmKprecond):
+// x = ((b W_N) .* (F - 1/at)) W_N^T + (b M_S^{-1}) / at
+int mk_prec(rte_handle* h, const double* B, double* X, double* tmp, int nrhs) {
+    const DevSystem& d = h->d;
+    const int rows = nrhs * d.nRm;
+    Scope sc(h, "mk_prec");
+    gemm_f64(h->stream, rows, d.dM, d.nSm, B, d.nSm, d.WmN, d.dM, tmp, d.dM, 1.0, 0.0, 2,
+             d.cell_at, d.cell_as, d.lamM, d.nRm);
+    mk_minv_scale(h->stream, d, B, X, nrhs);
+    gemm_f64(h->stream, rows, d.nSm, d.dM, tmp, d.dM, d.WmNT, d.nSm, X, d.nSm, 1.0, 1.0, 0,
+             nullptr, nullptr, nullptr, 1);
+    return RTE_OK;
+}
+
+// Y = (M^- - K^-) Z
+int mk_apply(rte_handle* h, const double* Z, double* Y, double* G, int nrhs) {
+    const DevSystem& d = h->d;
+    Scope sc(h, "mk_apply");
+    gemm_f64(h->stream, nrhs * d.nRm, d.nSm, d.nSm, Z, d.nSm, d.Sm, d.nSm, G, d.nSm, 1.0, 0.0,
+             0, nullptr, nullptr, nullptr, 1);
+    mk_combine(h->stream, d, Z, G, Y, nrhs);
+    return RTE_OK;
+}
+
+__global__ void k_ratio(const double* num, const double* den, double* out, int n,
+                        double sign) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = den[i] != 0.0 ? sign * num[i] / den[i] : 0.0;
+}
+
+// Algorithm 1 line 2: (M^- - K^-) X = B by PCG preconditioned with
+// eq. (MmKprecond); B = z1 and X = z2 inside Apply-E.  Per-RHS scalars stay
+// on the device; the host reads ||r||^2 once per iteration to stop.
+int mk_inv_pcg(rte_handle* h, const double* B, double* X, int nrhs) {
+    const DevSystem& d = h->d;
+    if (!h->z5) return fail(RTE_ERR_ARG, "PCG route needs mk_route = RTE_MK_PCG at setup");
+    const size_t len = (size_t)d.nRm * d.nSm;
+    double *R = h->z3, *P = h->z4, *AP = h->z5, *Zb = h->z6, *G = h->z7, *tmp = h->zsk;
+    const int n = nrhs;
+    // sc: [0,n) rz, [n,2n) scratch, [2n,3n) alpha, [3n,4n) rr, [4n,5n) bb, [5n,6n) beta
+    double* sc = h->sc;
+    cudaStream_t s = h->stream;
+    RTE_CUDA_TRY(cudaMemcpyAsync(R, B, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
+    RTE_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * n * len, s));
+    dot_per_rhs(s, B, B, len, n, h->partial, sc + 4 * n);
+    RTE_TRY(mk_prec(h, R, Zb, tmp, n));
+    RTE_CUDA_TRY(cudaMemcpyAsync(P, Zb, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
+    dot_per_rhs(s, R, Zb, len, n, h->partial, sc);
+    std::vector<double> hb(n), hr(n);
+    RTE_CUDA_TRY(cudaMemcpyAsync(hb.data(), sc + 4 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    RTE_CUDA_TRY(cudaStreamSynchronize(s));
+    bool allzero = true;
+    for (double v : hb) allzero = allzero && v == 0.0;
+    int it = 0;
+    if (!allzero) {
+        for (it = 1; it <= h->opt.mk_maxit; ++it) {
+            RTE_TRY(mk_apply(h, P, AP, G, n));
+            dot_per_rhs(s, P, AP, len, n, h->partial, sc + n);
+            k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc, sc + n, sc + 2 * n, n, 1.0);
+            axpby_per_rhs(s, P, X, len, n, sc + 2 * n, 0.0, nullptr, 1.0);
+            k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc, sc + n, sc + 2 * n, n, -1.0);
+            count_launches(2);
+            axpby_per_rhs(s, AP, R, len, n, sc + 2 * n, 0.0, nullptr, 1.0);
+            dot_per_rhs(s, R, R, len, n, h->partial, sc + 3 * n);
+            RTE_CUDA_TRY(cudaMemcpyAsync(hr.data(), sc + 3 * n, sizeof(double) * n,
+                                         cudaMemcpyDeviceToHost, s));
+            RTE_CUDA_TRY(cudaStreamSynchronize(s));
+            bool done = true;
+            for (int r = 0; r < n; ++r) {
+                if (!std::isfinite(hr[r])) return fail(RTE_ERR_DIVERGED, "PCG residual is NaN");
+                done = done && hr[r] <= h->opt.mk_tol * h->opt.mk_tol * hb[r];
+            }
+            if (done) break;
+            RTE_TRY(mk_prec(h, R, Zb, tmp, n));
+            dot_per_rhs(s, R, Zb, len, n, h->partial, sc + n);       // rz_new
+            k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc + n, sc, sc + 5 * n, n, 1.0);
+            count_launches(1);
+            RTE_CUDA_TRY(cudaMemcpyAsync(sc, sc + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            axpby_per_rhs(s, Zb, P, len, n, nullptr, 1.0, sc + 5 * n, 0.0);   // p = z + beta p
+        }
+        if (it > h->opt.mk_maxit) it = h->opt.mk_maxit;
+    }
+    h->mk_iters = it;
+    return RTE_OK;
+}
+
+int mk_inv(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
+    if (h->opt.mk_route == RTE_MK_PCG) return mk_inv_pcg(h, Z1, Z2, nrhs);
+    return mk_inv_eigen(h, Z1, Z2, nrhs);
+}
+
+// y = E x (with_k: y = (E - K^+) x).  Uses z1, z2 (and z3, z4 for routes).
+int apply_E(rte_handle* h, const double* x, double* y, int nrhs, bool with_k) {
+    const DevSystem& d = h->d;
+    {
+        Scope sc(h, "transport_A");
+        apply_A(h->stream, d, x, h->z1, nrhs);
+    }
+    RTE_TRY(mk_inv(h, h->z1, h->z2, nrhs));
+    double* V = nullptr;
+    if (with_k) {
+        V = h->e8;
+        Scope sc(h, "gemm_kplus");
+        gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.nSp, x, d.nSp, d.Sp, d.nSp, V, d.nSp, 1.0,
+                 0.0, 0, nullptr, nullptr, nullptr, 1);
+    }
+    Scope sc(h, "apply_even");
+    apply_even(h->stream, d, h->z2, x, V, y, nrhs, with_k ? 7 : 3);
+    return RTE_OK;
+}
+
+int read_status(rte_handle* h, SolveStatus& st) {
+    RTE_CUDA_TRY(cudaMemcpyAsync(&st, h->status, sizeof(SolveStatus), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (st.timed_out) return fail(RTE_ERR_TIMEOUT, "a bounded grid barrier timed out");
+    return RTE_OK;
+}
+
+int e0_inv(rte_handle* h, const double* b, double* x, int nrhs) {
+    {
+        Scope sc(h, "e0_cg");
+        RTE_TRY(e0_cg(h->stream, h->d, b, x, nrhs, h->opt.e0_tol, h->opt.e0_maxit, h->e0work,
+                      h->e0bytes, h->status));
+    }
+    SolveStatus st;
+    RTE_TRY(read_status(h, st));
+    h->e0_iters = st.iterations;
+    return RTE_OK;
+}
+
+int coarse_inv(rte_handle* h, const double* b, double* x, int nrhs) {
+    {
+        Scope sc(h, "coarse_cg");
+        RTE_TRY(coarse_cg(h->stream, h->d, b, x, nrhs, h->opt.coarse_tol, h->opt.coarse_maxit,
+                          h->cowork, h->cobytes, h->status));
+    }
+    SolveStatus st;
+    RTE_TRY(read_status(h, st));
+    h->co_iters = st.iterations;
+    return RTE_OK;
+}
+
+// z = P_1^l b (eq. applyP1).  Uses e5, e6 (and apply_E's buffers).
+int apply_P1(rte_handle* h, const double* b, double* z, int nrhs) {
+    const DevSystem& d = h->d;
+    const size_t len = (size_t)d.nRp * d.nSp;
+    RTE_TRY(e0_inv(h, b, z, nrhs));   // z_1 = E_0^{-1} b
+    for (int k = 1; k < h->opt.l; ++k) {
+        RTE_TRY(apply_E(h, z, h->e5, nrhs, false));
+        {
+            Scope sc(h, "axpy");
+            axpby_per_rhs(h->stream, b, h->e5, len, nrhs, nullptr, -1.0, nullptr, 1.0);
+        }
+        RTE_TRY(e0_inv(h, h->e5, h->e6, nrhs));
+        Scope sc(h, "axpy");
+        axpby_per_rhs(h->stream, h->e6, z, len, nrhs, nullptr, -1.0, nullptr, 1.0);
+    }
+    return RTE_OK;
+}
+
+int restrict_(rte_handle* h, const double* x, double* qc, int nrhs) {
+    const DevSystem& d = h->d;
+    Scope sc(h, "restrict");
+    gemm_f64(h->stream, nrhs * d.nRp, d.dP, d.nSp, x, d.nSp, d.WpN, d.dP, qc, d.dP, 1.0, 0.0,
+             0, nullptr, nullptr, nullptr, 1);
+    return RTE_OK;
+}
+
+int prolong_add(rte_handle* h, const double* uc, double* x, int nrhs, double beta) {
+    const DevSystem& d = h->d;
+    Scope sc(h, "prolong");
+    gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.dP, uc, d.dP, d.WpNT, d.nSp, x, d.nSp, 1.0, beta,
+             0, nullptr, nullptr, nullptr, 1);
+    return RTE_OK;
+}
+
+// s = P_2 P_1 r = P_1 r + W E_c^{-1} W^T (r - (E - K^+) P_1 r)   (eq. product_pre)
+int precond(rte_handle* h, const double* r, double* s, int nrhs, bool p2) {
+    const DevSystem& d = h->d;
+    const size_t len = (size_t)d.nRp * d.nSp;
+    RTE_TRY(apply_P1(h, r, s, nrhs));
+    if (!p2 || d.dP == 0) return RTE_OK;
+    RTE_TRY(apply_E(h, s, h->e7, nrhs, true));
+    {
+        Scope sc(h, "axpy");   // e7 = r - (E - K^+) s
+        axpby_per_rhs(h->stream, r, h->e7, len, nrhs, nullptr, 1.0, nullptr, -1.0);
+    }
+    RTE_TRY(restrict_(h, h->e7, h->c1, nrhs));   // -q_c = W^T (r - (E-K) s)
+    RTE_TRY(coarse_inv(h, h->c1, h->c2, nrhs));  // -u_c
+    // s <- s - W u_c, so that u_{n+1} = u_n - s = u_{n+1/2} + W u_c
+    RTE_TRY(prolong_add(h, h->c2, s, nrhs, 1.0));
+    return RTE_OK;
+}
+
+__global__ void k_neg(double* c, size_t n) {
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i < n) c[i] = -c[i];
+}
+
+bool bad(double v) { return !std::isfinite(v); }
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+const char* rte_last_error(void) { return rte::g_last_error.c_str(); }
+
+int rte_default_options(rte_options* o) {
+    if (!o) return fail(RTE_ERR_ARG, "opts is NULL");
+    o->l = 4;
+    o->n_plus = 4;
+    o->n_minus = 5;
+    o->precision = RTE_FP64;
+    o->mk_route = RTE_MK_EIGEN;
+    o->mk_tol = 1e-12;
+    o->mk_maxit = 500;
+    o->e0_tol = 1e-12;
+    o->e0_maxit = 20000;
+    o->coarse_tol = 1e-12;
+    o->coarse_maxit = 20000;
+    o->max_iter = 200;
+    o->max_rhs = 1;
+    return RTE_OK;
+}
+
+int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
+              rte_handle** out) {
+    if (!prob || !out) return fail(RTE_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    rte_options o;
+    if (opts) o = *opts; else rte_default_options(&o);
+    if (o.l < 1 || o.n_minus < 1 || (o.n_minus % 2) == 0 || (o.n_plus >= 0 && o.n_plus % 2) ||
+        o.max_rhs < 1 || o.mk_maxit < 1 || o.e0_maxit < 1 || o.coarse_maxit < 1)
+        return fail(RTE_ERR_ARG, "invalid options (l >= 1, odd N^- >= 1, even N^+ or -1)");
+    if (o.precision != RTE_FP64)
+        return fail(RTE_ERR_ARG, "only RTE_FP64 is available in this build");
+    HostSystem hs;
+    RTE_TRY(build_host_system(*prob, o, hs));
+    rte_handle* h = new rte_handle();
+    h->opt = o;
+    h->stream = (cudaStream_t)stream;
+    auto bail = [&](int rc) {
+        rte_destroy(h);
+        return rc;
+    };
+    DevSystem& d = h->d;
+    d.nRp = hs.nRp; d.nRm = hs.nRm; d.nSp = hs.nSp; d.nSm = hs.nSm;
+    d.dP = hs.dP; d.dM = hs.dM; d.nnz = (int)hs.st.col.size();
+    d.g = hs.g; d.c = hs.c; d.gamma = hs.gamma;
+    int rc = RTE_OK;
+#define UP(dst, src) do { rc = upload(h, &d.dst, src); if (rc) return bail(rc); } while (0)
+    UP(cell_nodes, hs.mesh.cell_nodes);
+    UP(cell_D, hs.cell_D);
+    UP(cell_at, hs.cell_at);
+    UP(cell_as, hs.cell_as);
+    UP(adj_ptr, hs.adj_ptr);
+    UP(adj_cell, hs.adj_cell);
+    UP(adj_loc, hs.adj_loc);
+    UP(st_ptr, hs.st.ptr);
+    UP(st_col, hs.st.col);
+    UP(st_diag, hs.st.diag);
+    UP(sval, hs.sval);
+    UP(ang_m, hs.m_);
+    UP(ang_omx, hs.omx);
+    UP(ang_omy, hs.omy);
+    UP(ang_A1, hs.A1);
+    UP(ang_A2, hs.A2);
+    UP(ang_MSm, hs.MSm);
+    UP(ang_MSm_inv, hs.MSm_inv);
+    UP(e0s, hs.e0s);
+    // ------------------------------------------------ S^+ and S^- (device)
+    const int n = hs.nSp, nm = hs.nSm;
+    QuadDev q{};
+    {
+        double *sp = nullptr, *sm = nullptr;
+        rc = dalloc(h, &sp, (size_t)n * n); if (rc) return bail(rc);
+        rc = dalloc(h, &sm, (size_t)nm * nm); if (rc) return bail(rc);
+        d.Sp = sp;
+        d.Sm = sm;
+    }
+    {
+        const double *a, *b, *c, *e, *f, *g2;
+        const int *pi, *ii;
+        rc = upload(h, &a, hs.quad_near_pts); if (rc) return bail(rc);
+        rc = upload(h, &b, hs.quad_near_w); if (rc) return bail(rc);
+        rc = upload(h, &c, hs.quad_near_psi); if (rc) return bail(rc);
+        rc = upload(h, &e, hs.quad_far_pts); if (rc) return bail(rc);
+        rc = upload(h, &f, hs.quad_far_w); if (rc) return bail(rc);
+        rc = upload(h, &g2, hs.quad_far_psi); if (rc) return bail(rc);
+        rc = upload(h, &pi, hs.near_ptr); if (rc) return bail(rc);
+        rc = upload(h, &ii, hs.near_idx); if (rc) return bail(rc);
+        q = QuadDev{a, b, c, e, f, g2, pi, ii, 1 << (2 * kRNear), 1 << (2 * kRFar)};
+    }
+    assemble_scattering(h->stream, n, hs.g, q, const_cast<double*>(d.Sp),
+                        const_cast<double*>(d.Sm));
+    h->h_Sp.resize((size_t)n * n);
+    h->h_Sm.resize((size_t)nm * nm);
+    if (cudaMemcpyAsync(h->h_Sp.data(), d.Sp, sizeof(double) * n * n, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->h_Sm.data(), d.Sm, sizeof(double) * (size_t)nm * nm, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return bail(fail(RTE_ERR_CUDA, "scattering assembly failed"));
+    h->h_m = hs.m_; h->h_MSm = hs.MSm; h->h_A1 = hs.A1; h->h_A2 = hs.A2;
+    h->h_omx = hs.omx; h->h_omy = hs.omy;
+
+    // --------------------------------------- eigenpairs of (S^+, M_S^+)
+    std::vector<double> C((size_t)n * n), w;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            C[(size_t)i * n + j] = h->h_Sp[(size_t)i * n + j] / std::sqrt(hs.m_[i] * hs.m_[j]);
+    rc = sym_eig(h, C, w, n);
+    if (rc) return bail(rc);
+    // eigenvector t (ascending) is row t of C; reorder non-increasing
+    h->h_lamP.resize(n);
+    std::vector<double> WpFull((size_t)n * n);
+    for (int t = 0; t < n; ++t) {
+        const int src = n - 1 - t;
+        h->h_lamP[t] = w[src];
+        for (int k = 0; k < n; ++k)
+            WpFull[(size_t)k * n + t] = C[(size_t)src * n + k] / std::sqrt(hs.m_[k]);
+    }
+    const int dP = hs.dP;
+    h->h_WpN.assign((size_t)n * std::max(dP, 1), 0.0);
+    std::vector<double> WpNT((size_t)std::max(dP, 1) * n, 0.0);
+    for (int k = 0; k < n; ++k)
+        for (int a = 0; a < dP; ++a) {
+            h->h_WpN[(size_t)k * dP + a] = WpFull[(size_t)k * n + a];
+            WpNT[(size_t)a * n + k] = WpFull[(size_t)k * n + a];
+        }
+    UP(WpN, h->h_WpN);
+    UP(WpNT, WpNT);
+    UP(lamP, h->h_lamP);
+
+    // --------------------------------------- eigenpairs of (S^-, M_S^-)
+    // M_S^- = L L^T blockwise; C = L^{-1} S^- L^{-T}; W = L^{-T} Q
+    std::vector<double> Linv((size_t)9 * n);
+    for (int k = 0; k < n; ++k) {
+        double L[9];
+        if (!chol3(&hs.MSm[9 * k], L)) return bail(fail(RTE_ERR_ARG, "odd mass not SPD"));
+        inv_lower3(L, &Linv[9 * k]);
+    }
+    std::vector<double> Cm((size_t)nm * nm);
+    for (int K1 = 0; K1 < n; ++K1)
+        for (int K2 = 0; K2 < n; ++K2) {
+            const double* Li = &Linv[9 * K1];
+            const double* Lj = &Linv[9 * K2];
+            double T[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double s = 0.0;
+                    for (int k = 0; k < 3; ++k)
+                        s += Li[3 * i + k] * h->h_Sm[(size_t)(3 * K1 + k) * nm + 3 * K2 + j];
+                    T[3 * i + j] = s;
+                }
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double s = 0.0;
+                    for (int k = 0; k < 3; ++k) s += T[3 * i + k] * Lj[3 * j + k];
+                    Cm[(size_t)(3 * K1 + i) * nm + 3 * K2 + j] = s;
+                }
+        }
+    std::vector<double> wm;
+    rc = sym_eig(h, Cm, wm, nm);
+    if (rc) return bail(rc);
+    h->h_lamM.resize(nm);
+    std::vector<double> Vm((size_t)nm * nm), VmT((size_t)nm * nm);
+    for (int t = 0; t < nm; ++t) {
+        const int src = nm - 1 - t;
+        h->h_lamM[t] = wm[src];
+        const double* qv = &Cm[(size_t)src * nm];
+        for (int K1 = 0; K1 < n; ++K1) {
+            const double* Li = &Linv[9 * K1];
+            for (int i = 0; i < 3; ++i) {
+                // (L^{-T} q)_i = sum_k Linv[k][i] q_k
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += Li[3 * k + i] * qv[3 * K1 + k];
+                Vm[(size_t)(3 * K1 + i) * nm + t] = s;
+                VmT[(size_t)t * nm + 3 * K1 + i] = s;
+            }
+        }
+    }
+    const int dM = hs.dM;
+    std::vector<double> WmN((size_t)nm * dM), WmNT((size_t)dM * nm);
+    for (int r = 0; r < nm; ++r)
+        for (int a = 0; a < dM; ++a) {
+            WmN[(size_t)r * dM + a] = Vm[(size_t)r * nm + a];
+            WmNT[(size_t)a * nm + r] = Vm[(size_t)r * nm + a];
+        }
+    UP(Vm, Vm);
+    UP(VmT, VmT);
+    UP(lamM, h->h_lamM);
+    UP(WmN, WmN);
+    UP(WmNT, WmNT);
+
+    // ------------------------------- coarse matrix E_c = W^T (E - K^+) W
+    if (dP > 0) {
+        const int nnz = d.nnz;
+        const int dd = dP * dP;
+        h->h_ec.assign((size_t)nnz * dd, 0.0);
+        const double* Mt = &hs.sval[(size_t)kMt * nnz];
+        const double* Ms = &hs.sval[(size_t)kMs * nnz];
+        const double* Bx = &hs.sval[(size_t)kBx * nnz];
+        const double* By = &hs.sval[(size_t)kBy * nnz];
+        std::vector<double> Ox(dd, 0.0), Oy(dd, 0.0);
+        for (int a = 0; a < dP; ++a)
+            for (int b = 0; b < dP; ++b)
+                for (int k = 0; k < n; ++k) {
+                    const double ww = h->h_WpN[(size_t)k * dP + a] * h->h_WpN[(size_t)k * dP + b];
+                    Ox[a * dP + b] += hs.omx[k] * ww;
+                    Oy[a * dP + b] += hs.omy[k] * ww;
+                }
+        for (int p = 0; p < nnz; ++p) {
+            double* blk = &h->h_ec[(size_t)p * dd];
+            for (int a = 0; a < dP; ++a) {
+                blk[a * dP + a] += Mt[p] - h->h_lamP[a] * Ms[p];
+                for (int b = 0; b < dP; ++b)
+                    blk[a * dP + b] += Bx[p] * Ox[a * dP + b] + By[p] * Oy[a * dP + b];
+            }
+        }
+        // transport block: G_n = V^T (A_n W_N)  (n_S^- x dP) for n = 1, 2
+        std::vector<double> G((size_t)2 * nm * dP, 0.0);
+        for (int nn = 0; nn < 2; ++nn) {
+            const std::vector<double>& An = nn == 0 ? hs.A1 : hs.A2;
+            for (int lam = 0; lam < nm; ++lam) {
+                double* g = &G[((size_t)nn * nm + lam) * dP];
+                for (int K1 = 0; K1 < n; ++K1)
+                    for (int c = 0; c < 3; ++c) {
+                        const double v = Vm[(size_t)(3 * K1 + c) * nm + lam] * An[3 * K1 + c];
+                        if (v == 0.0) continue;
+                        const double* wrow = &h->h_WpN[(size_t)K1 * dP];
+                        for (int a = 0; a < dP; ++a) g[a] += v * wrow[a];
+                    }
+            }
+        }
+        // H(sigma_t, sigma_s) per class of cells, (2 dP)^2 entries
+        std::map<std::pair<double, double>, std::vector<double>> Hc;
+        const int d2 = 2 * dP;
+        for (int j = 0; j < hs.nRm; ++j) {
+            const double st = prob->sigma_t[j], ss = prob->sigma_s[j];
+            auto key = std::make_pair(st, ss);
+            if (Hc.count(key)) continue;
+            std::vector<double> H((size_t)d2 * d2, 0.0);
+            for (int lam = 0; lam < nm; ++lam) {
+                const double f = 1.0 / (st - h->h_lamM[lam] * ss);
+                for (int x = 0; x < d2; ++x) {
+                    const double gx = G[((size_t)(x / dP) * nm + lam) * dP + x % dP] * f;
+                    if (gx == 0.0) continue;
+                    for (int y = 0; y < d2; ++y)
+                        H[(size_t)x * d2 + y] += gx * G[((size_t)(y / dP) * nm + lam) * dP + y % dP];
+                }
+            }
+            Hc[key] = std::move(H);
+        }
+        for (int j = 0; j < hs.nRm; ++j) {
+            const std::vector<double>& H = Hc[std::make_pair(prob->sigma_t[j], prob->sigma_s[j])];
+            const double A = hs.mesh.area[j];
+            const int* nd = &hs.mesh.cell_nodes[3 * j];
+            for (int al = 0; al < 3; ++al)
+                for (int be = 0; be < 3; ++be) {
+                    const int row = nd[al], col = nd[be];
+                    const int* bgn = hs.st.col.data() + hs.st.ptr[row];
+                    const int* end = hs.st.col.data() + hs.st.ptr[row + 1];
+                    const int pos = (int)(std::lower_bound(bgn, end, col) - hs.st.col.data());
+                    double* blk = &h->h_ec[(size_t)pos * dd];
+                    const double D[2][2] = {{hs.cell_D[6 * j + al], hs.cell_D[6 * j + 3 + al]},
+                                            {hs.cell_D[6 * j + be], hs.cell_D[6 * j + 3 + be]}};
+                    for (int nn = 0; nn < 2; ++nn)
+                        for (int mm = 0; mm < 2; ++mm) {
+                            const double fac = D[0][nn] * D[1][mm] / A;
+                            for (int a = 0; a < dP; ++a)
+                                for (int b = 0; b < dP; ++b)
+                                    blk[a * dP + b] += fac * H[(size_t)(nn * dP + a) * d2 + mm * dP + b];
+                        }
+                }
+        }
+        std::vector<double> dinv((size_t)hs.nRp * dd);
+        for (int i = 0; i < hs.nRp; ++i)
+            if (!chol_inv_sym(dP, &h->h_ec[(size_t)hs.st.diag[i] * dd], &dinv[(size_t)i * dd]))
+                return bail(fail(RTE_ERR_ARG, "singular coarse diagonal block"));
+        UP(ec_val, h->h_ec);
+        UP(ec_dinv, dinv);
+    }
+#undef UP
+    rc = alloc_workspace(h, o.max_rhs);
+    if (rc) return bail(rc);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return bail(fail(RTE_ERR_CUDA, "setup synchronisation failed"));
+    *out = h;
+    return RTE_OK;
+}
+
+int rte_sizes(const rte_handle* h, int* n_nodes, int* n_cells, int* n_dirs, int* n_odd,
+              int* d_plus, int* d_minus) {
+    if (!h) return fail(RTE_ERR_ARG, "NULL handle");
+    if (n_nodes) *n_nodes = h->d.nRp;
+    if (n_cells) *n_cells = h->d.nRm;
+    if (n_dirs) *n_dirs = h->d.nSp;
+    if (n_odd) *n_odd = h->d.nSm;
+    if (d_plus) *d_plus = h->d.dP;
+    if (d_minus) *d_minus = h->d.dM;
+    return RTE_OK;
+}
+
+int rte_rhs(rte_handle* h, const double* q_nodal, double* q, int nrhs) {
+    if (!h || !q_nodal || !q || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
+    Scope sc(h, "rhs");
+    rhs_source(h->stream, h->d, q_nodal, q, nrhs);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int rte_apply(rte_handle* h, const double* x, double* y, int nrhs) {
+    if (!h || !x || !y || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
+    RTE_TRY(ensure_workspace(h, nrhs));
+    RTE_TRY(apply_E(h, x, y, nrhs, true));
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int rte_precond(rte_handle* h, const double* r, double* s, int nrhs, int with_p2) {
+    if (!h || !r || !s || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
+    RTE_TRY(ensure_workspace(h, nrhs));
+    RTE_TRY(precond(h, r, s, nrhs, with_p2 != 0));
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int rte_operator(rte_handle* h, int op, const double* in, double* out, int nrhs) {
+    if (!h || !in || !out || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
+    RTE_TRY(ensure_workspace(h, nrhs));
+    const DevSystem& d = h->d;
+    cudaStream_t s = h->stream;
+    const size_t no = (size_t)nrhs * d.nRm * d.nSm;
+    switch (op) {
+        case RTE_OP_A: apply_A(s, d, in, out, nrhs); break;
+        case RTE_OP_AT: apply_even(s, d, in, nullptr, nullptr, out, nrhs, 1); break;
+        case RTE_OP_KPLUS:
+            gemm_f64(s, nrhs * d.nRp, d.nSp, d.nSp, in, d.nSp, d.Sp, d.nSp, h->e8, d.nSp, 1.0,
+                     0.0, 0, nullptr, nullptr, nullptr, 1);
+            apply_even(s, d, nullptr, h->e8, h->e8, out, nrhs, 4);
+            k_neg<<<(unsigned)((nrhs * (size_t)d.nRp * d.nSp + 255) / 256), 256, 0, s>>>(
+                out, (size_t)nrhs * d.nRp * d.nSp);
+            count_launches(1);
+            break;
+        case RTE_OP_MK: RTE_TRY(mk_apply(h, in, out, h->z4, nrhs)); break;
+        case RTE_OP_MK_INV:
+            RTE_CUDA_TRY(cudaMemcpyAsync(h->z1, in, no * 8, cudaMemcpyDeviceToDevice, s));
+            RTE_TRY(mk_inv(h, h->z1, h->z2, nrhs));
+            RTE_CUDA_TRY(cudaMemcpyAsync(out, h->z2, no * 8, cudaMemcpyDeviceToDevice, s));
+            break;
+        case RTE_OP_MK_PREC: RTE_TRY(mk_prec(h, in, out, h->z4, nrhs)); break;
+        case RTE_OP_E: RTE_TRY(apply_E(h, in, out, nrhs, false)); break;
+        case RTE_OP_E0_INV: RTE_TRY(e0_inv(h, in, out, nrhs)); break;
+        case RTE_OP_P1: RTE_TRY(apply_P1(h, in, out, nrhs)); break;
+        case RTE_OP_RESTRICT: RTE_TRY(restrict_(h, in, out, nrhs)); break;
+        case RTE_OP_PROLONG: RTE_TRY(prolong_add(h, in, out, nrhs, 0.0)); break;
+        case RTE_OP_EC: coarse_apply(s, d, in, out, nrhs); break;
+        case RTE_OP_EC_INV: RTE_TRY(coarse_inv(h, in, out, nrhs)); break;
+        default: return fail(RTE_ERR_ARG, "unknown operator id");
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
+int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
+              rte_stats* stats) {
+    if (!h || !q || !u || nrhs < 1 || !(tol >= 0)) return fail(RTE_ERR_ARG, "bad argument");
+    RTE_TRY(ensure_workspace(h, nrhs));
+    const auto t0 = std::chrono::steady_clock::now();
+    const DevSystem& d = h->d;
+    cudaStream_t s = h->stream;
+    const size_t len = (size_t)d.nRp * d.nSp;
+    double* r = h->e1;       // residual r_n
+    double* sv = h->e2;      // s = P_2 P_1 r
+    double* rprev = h->e3;
+    double* delta = h->e4;   // u_n - u_{n-1}
+    std::vector<double> hq(nrhs), hr(nrhs), hd1(nrhs), hd2(nrhs);
+    double* sc = h->sc;
+    dot_per_rhs(s, q, q, len, nrhs, h->partial, sc);
+    RTE_CUDA_TRY(cudaMemcpyAsync(hq.data(), sc, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    RTE_CUDA_TRY(cudaStreamSynchronize(s));
+    int it = 0, rc = RTE_OK;
+    double worst = 0.0, energy = 0.0;
+    for (it = 0;; ++it) {
+        // r = (E - K^+) u - q   (Algorithm 3: residual)
+        RTE_TRY(apply_E(h, u, r, nrhs, true));
+        {
+            Scope scp(h, "axpy");
+            axpby_per_rhs(s, q, r, len, nrhs, nullptr, -1.0, nullptr, 1.0);
+        }
+        dot_per_rhs(s, r, r, len, nrhs, h->partial, sc);
+        if (it > 0) {
+            // ||u_n - u_{n-1}||^2_{E-K} = delta^T (r_n - r_{n-1})
+            dot_per_rhs(s, delta, r, len, nrhs, h->partial, sc + nrhs);
+            dot_per_rhs(s, delta, rprev, len, nrhs, h->partial, sc + 2 * nrhs);
+        }
+        RTE_CUDA_TRY(cudaMemcpyAsync(hr.data(), sc, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        if (it > 0) {
+            RTE_CUDA_TRY(cudaMemcpyAsync(hd1.data(), sc + nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+            RTE_CUDA_TRY(cudaMemcpyAsync(hd2.data(), sc + 2 * nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+        }
+        RTE_CUDA_TRY(cudaStreamSynchronize(s));
+        worst = 0.0;
+        energy = 0.0;
+        bool nan = false;
+        for (int k = 0; k < nrhs; ++k) {
+            const double rel = hq[k] > 0 ? std::sqrt(hr[k] / hq[k]) : std::sqrt(hr[k]);
+            if (bad(rel)) nan = true;
+            worst = std::max(worst, rel);
+            if (it > 0) energy = std::max(energy, std::sqrt(std::max(0.0, hd1[k] - hd2[k])));
+        }
+        if (stats && stats->history && it < stats->history_cap) stats->history[it] = worst;
+        if (nan) { rc = fail(RTE_ERR_DIVERGED, "residual is NaN or Inf"); break; }
+        if (worst <= tol) break;
+        if (it >= h->opt.max_iter) { rc = fail(RTE_ERR_MAXITER, "outer iteration cap reached"); break; }
+        // s = P_2 P_1 r ; u_{n+1} = u_n - s   (half step plus subspace correction)
+        RTE_TRY(precond(h, r, sv, nrhs, true));
+        RTE_CUDA_TRY(cudaMemcpyAsync(rprev, r, sizeof(double) * nrhs * len, cudaMemcpyDeviceToDevice, s));
+        RTE_CUDA_TRY(cudaMemcpyAsync(delta, sv, sizeof(double) * nrhs * len, cudaMemcpyDeviceToDevice, s));
+        {
+            Scope scp(h, "axpy");
+            k_neg<<<(unsigned)((nrhs * len + 255) / 256), 256, 0, s>>>(delta, nrhs * len);
+            count_launches(1);
+            axpby_per_rhs(s, sv, u, len, nrhs, nullptr, -1.0, nullptr, 1.0);
+        }
+    }
+    RTE_CUDA_TRY(cudaGetLastError());
+    if (stats) {
+        stats->iterations = it;
+        stats->rel_residual = worst;
+        stats->energy_update = energy;
+        stats->e0_iters_last = h->e0_iters;
+        stats->coarse_iters_last = h->co_iters;
+        stats->mk_iters_last = h->mk_iters;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rc;
+}
+
+int rte_export(const rte_handle* h, int what, double* out, size_t n) {
+    if (!h || !out) return fail(RTE_ERR_ARG, "bad argument");
+    const std::vector<double>* src = nullptr;
+    switch (what) {
+        case 0: src = &h->h_Sp; break;
+        case 1: src = &h->h_Sm; break;
+        case 2: src = &h->h_m; break;
+        case 3: src = &h->h_MSm; break;
+        case 4: src = &h->h_A1; break;
+        case 5: src = &h->h_A2; break;
+        case 6: src = &h->h_omx; break;
+        case 7: src = &h->h_omy; break;
+        case 8: src = &h->h_lamP; break;
+        case 9: src = &h->h_lamM; break;
+        case 10: src = &h->h_WpN; break;
+        case 11: src = &h->h_ec; break;
+        default: return fail(RTE_ERR_ARG, "unknown export id");
+    }
+    if (n < src->size()) return fail(RTE_ERR_ARG, "export buffer too small");
+    std::memcpy(out, src->data(), src->size() * sizeof(double));
+    return RTE_OK;
+}
+
+int rte_timing_enable(rte_handle* h, int on) {
+    if (!h) return fail(RTE_ERR_ARG, "NULL handle");
+    flush_timers(h);
+    h->timing = on != 0;
+    for (auto& v : h->tms) v = 0.0;
+    for (auto& v : h->tcount) v = 0;
+    return RTE_OK;
+}
+
+int rte_timing_read(rte_handle* h, const char** names, double* ms, long long* launches,
+                    int cap, int* count) {
+    if (!h || !count) return fail(RTE_ERR_ARG, "bad argument");
+    flush_timers(h);
+    const int nn = (int)h->tnames.size();
+    *count = nn;
+    for (int i = 0; i < nn && i < cap; ++i) {
+        if (names) names[i] = h->tnames[i].c_str();
+        if (ms) ms[i] = h->tms[i];
+        if (launches) launches[i] = h->tcount[i];
+    }
+    return RTE_OK;
+}
+
+long long rte_kernel_launches(void) { return launches_total(); }
+
+void rte_destroy(rte_handle* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (auto& t : h->trecs) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+}
+
+}  // extern "C"

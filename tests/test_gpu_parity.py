@@ -1,0 +1,235 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 oracle.
+
+Every step of the hot path is compared element by element on the same
+seeded inputs; iterative solves are judged on their residual in the
+oracle's exact operator.  FP64 tolerances: direct applies agree to 1e-11
+(relative, max norm; the summation order differs), solves reach the
+requested relative residual.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle.richardson import Coarse, richardson
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip('torch')
+
+
+def relerr(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+CASES = {
+    # 16 directions (< one 32-lane tile), 16 nodes (< one node chunk)
+    'tiny': lambda: workloads.constant(3, 1, 0.5, 1.0, 0.9, 1.0),
+    # ragged node chunks, piecewise-constant coefficients, 64 directions
+    'ragged': lambda: workloads.checkerboard(m=9, levels=2, g=0.7, ratio=0.95,
+                                             blocks=3, nrhs=2),
+    # isotropic scattering: K^- = 0
+    'g0': lambda: workloads.constant(4, 1, 0.0, 2.0, 1.5, 1.0),
+    # no scattering: K = 0, c = 0
+    'nosc': lambda: workloads.constant(4, 1, 0.6, 2.0, 0.0, 1.0),
+}
+
+
+class Pair:
+    def __init__(self, name, n_plus=2, n_minus=3, **opts):
+        import paper_2102_09038_gb300 as rte
+        self.p = CASES[name]()
+        p = self.p
+        self.disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+        self.ops = oracle.Operators(self.disc, n_plus=n_plus, n_minus=n_minus)
+        self.gpu = rte.Solver(p, n_plus=n_plus, n_minus=n_minus,
+                              max_rhs=max(3, p.nrhs), **opts)
+        self.rng = np.random.default_rng(zlib.crc32(name.encode()))
+
+    def even(self, nrhs=1):
+        return self.rng.standard_normal((nrhs, self.disc.nRp, self.disc.nSp))
+
+    def odd(self, nrhs=1):
+        return self.rng.standard_normal((nrhs, self.disc.nRm, self.disc.nSm))
+
+    def run(self, op, x, out_shape):
+        xt = torch.tensor(x, dtype=torch.float64, device='cuda')
+        out = torch.zeros(out_shape, dtype=torch.float64, device='cuda')
+        self.gpu.operator(op, xt, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+
+@pytest.fixture(scope='module', params=list(CASES))
+def pair(request):
+    pr = Pair(request.param)
+    yield pr
+    pr.gpu.close()
+
+
+@pytest.fixture(scope='module')
+def pcg_pair():
+    pr = Pair('ragged', mk_route=1)
+    yield pr
+    pr.gpu.close()
+
+
+def test_assembly_matches_independent_oracle(pair):
+    an = pair.disc.an
+    g = pair.gpu
+    n = pair.disc.nSp
+    assert relerr(g.export('Splus').reshape(n, n), an['Splus']) < 1e-12
+    assert relerr(g.export('Sminus').reshape(3 * n, 3 * n), an['Sminus']) < 1e-12
+    assert relerr(g.export('m'), an['m']) < 1e-14
+    assert relerr(g.export('MSm').reshape(n, 3, 3), an['MSm']) < 1e-13
+    assert relerr(g.export('A1').reshape(n, 3), an['A1']) < 1e-13
+    assert relerr(g.export('A2').reshape(n, 3), an['A2']) < 1e-13
+    assert relerr(g.export('omx'), an['omx']) < 1e-13
+    assert relerr(g.export('omy'), an['omy']) < 1e-13
+    lamP, _ = pair.ops.eig_plus()
+    lamM, _ = pair.ops.eig_minus()
+    assert np.abs(g.export('lamP') - lamP).max() < 1e-12
+    assert np.abs(g.export('lamM') - lamM).max() < 1e-12
+
+
+def test_coarse_matrix_in_library_basis(pair):
+    d = pair.gpu.d_plus
+    W = pair.gpu.export('WpN').reshape(pair.disc.nSp, d)
+    # the library's W is M_S^+-orthonormal
+    assert relerr(W.T @ (pair.disc.an['m'][:, None] * W), np.eye(d)) < 1e-12
+    co = Coarse(pair.ops, 2, W=W)
+    Ec = co.Ec.tocsr()
+    blocks = pair.gpu.export('Ec')
+    nRp = pair.disc.nRp
+    ref = []
+    for i in range(nRp):
+        cols = sorted(set(Ec[i * d:(i + 1) * d].indices // d))
+        for j in cols:
+            ref.append(Ec[i * d:(i + 1) * d, j * d:(j + 1) * d].toarray())
+    ref = np.array(ref)
+    assert relerr(blocks[:ref.size].reshape(ref.shape), ref) < 1e-11
+
+
+def test_transport_pieces(pair):
+    ops, nr = pair.ops, 2
+    x = pair.even(nr)
+    got = pair.run('A', x, (nr, pair.disc.nRm, pair.disc.nSm))
+    assert relerr(got, np.stack([ops.apply_A(v) for v in x])) < 1e-13
+    z = pair.odd(nr)
+    got = pair.run('AT', z, x.shape)
+    assert relerr(got, np.stack([ops.apply_AT(v) for v in z])) < 1e-13
+    got = pair.run('KPLUS', x, x.shape)
+    assert relerr(got, np.stack([ops.apply_Kplus(v) for v in x])) < 1e-12
+    got = pair.run('MK', z, z.shape)
+    assert relerr(got, np.stack([ops.apply_MKminus(v) for v in z])) < 1e-12
+
+
+def test_mk_inverse_and_lemma_preconditioner(pair):
+    ops, nr = pair.ops, 2
+    z = pair.odd(nr)
+    got = pair.run('MK_INV', z, z.shape)
+    assert relerr(got, np.stack([ops.solve_MKminus(v) for v in z])) < 1e-11
+    got = pair.run('MK_PREC', z, z.shape)
+    assert relerr(got, np.stack([ops.precond_MKN(v, 3) for v in z])) < 1e-10
+
+
+def test_mk_inverse_pcg_route(pcg_pair):
+    pr = pcg_pair
+    z = pr.odd(2)
+    got = pr.run('MK_INV', z, z.shape)
+    ref = np.stack([pr.ops.solve_MKminus(v) for v in z])
+    assert relerr(got, ref) < 1e-10
+
+
+def test_apply_E_and_EK(pair):
+    ops, nr = pair.ops, 2
+    x = pair.even(nr)
+    got = pair.run('E', x, x.shape)
+    assert relerr(got, np.stack([ops.apply_E(v) for v in x])) < 1e-11
+    xt = torch.tensor(x, dtype=torch.float64, device='cuda')
+    y = pair.gpu.apply(xt)
+    torch.cuda.synchronize()
+    assert relerr(y.cpu().numpy(), np.stack([ops.apply_EK(v) for v in x])) < 1e-11
+
+
+def test_e0_inverse_per_direction_cg(pair):
+    ops, nr = pair.ops, 2
+    b = pair.even(nr)
+    got = pair.run('E0_INV', b, b.shape)
+    for r in range(nr):
+        res = ops.apply_E0(got[r]) - b[r]
+        # every direction column reaches the 1e-12 relative residual
+        col = np.linalg.norm(res, axis=0) / np.linalg.norm(b[r], axis=0)
+        assert col.max() < 2e-12
+        assert relerr(got[r], ops.solve_E0(b[r])) < 1e-8
+
+
+def test_p1_and_coarse_steps(pair):
+    ops, nr = pair.ops, 2
+    b = pair.even(nr)
+    got = pair.run('P1', b, b.shape)
+    ref = np.stack([ops.apply_P1(v, 4) for v in b])
+    assert relerr(got, ref) < 1e-8
+    d = pair.gpu.d_plus
+    W = pair.gpu.export('WpN').reshape(pair.disc.nSp, d)
+    co = Coarse(ops, 2, W=W)
+    qc = pair.run('RESTRICT', b, (nr, pair.disc.nRp, d))
+    assert relerr(qc, np.stack([co.restrict(v) for v in b])) < 1e-13
+    pro = pair.run('PROLONG', qc, b.shape)
+    assert relerr(pro, np.stack([co.prolong(v) for v in qc])) < 1e-13
+    ec = pair.run('EC', qc, qc.shape)
+    assert relerr(ec, np.stack([(co.Ec @ v.ravel()).reshape(v.shape) for v in qc])) < 1e-12
+    uc = pair.run('EC_INV', qc, qc.shape)
+    for r in range(nr):
+        res = co.Ec @ uc[r].ravel() - qc[r].ravel()
+        assert np.linalg.norm(res) / np.linalg.norm(qc[r]) < 2e-12
+
+
+def test_precond_product_form(pair):
+    # rte_precond = P_1 + W E_c^{-1} W^T (I - (E - K) P_1)  (eq. product_pre)
+    ops, nr = pair.ops, 1
+    r = pair.even(nr)
+    rt = torch.tensor(r, dtype=torch.float64, device='cuda')
+    s = pair.gpu.precond(rt).cpu().numpy()
+    d = pair.gpu.d_plus
+    W = pair.gpu.export('WpN').reshape(pair.disc.nSp, d)
+    co = Coarse(ops, 2, W=W)
+    s1 = ops.apply_P1(r[0], 4)
+    ref = s1 + co.prolong(co.solve(co.restrict(r[0] - ops.apply_EK(s1))))
+    assert relerr(s[0], ref) < 1e-8
+
+
+def test_solve_reaches_oracle_residual(pair):
+    p, ops = pair.p, pair.ops
+    qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
+    q = pair.gpu.rhs(qn)
+    qref = np.stack([pair.disc.source(v) for v in p.q_nodal])
+    assert relerr(q.cpu().numpy(), qref) < 1e-14
+    u, info = pair.gpu.solve(q, tol=1e-11)
+    assert info['status'] == 0, info
+    u = u.cpu().numpy()
+    for r in range(p.nrhs):
+        res = np.linalg.norm(ops.apply_EK(u[r]) - qref[r]) / np.linalg.norm(qref[r])
+        assert res < 1e-10, res
+    # same iterate sequence as the oracle's Algorithm 3 (same l, N)
+    uo, io = richardson(ops, qref[0], tol=1e-11, l=4, N=2)
+    assert abs(info['iterations'] - io['iterations']) <= 1
+    assert relerr(u[0], uo) < 1e-8
+
+
+def test_solve_warm_start_and_multi_rhs(pair):
+    # three right-hand sides at once; u holds the initial guess on entry
+    p, ops = pair.p, pair.ops
+    qref = pair.even(3)
+    q = torch.tensor(qref, dtype=torch.float64, device='cuda')
+    u0 = torch.tensor(pair.even(3) * 1e-3, dtype=torch.float64, device='cuda')
+    u, info = pair.gpu.solve(q, u=u0, tol=1e-10)
+    assert info['status'] == 0
+    u = u.cpu().numpy()
+    for r in range(3):
+        res = np.linalg.norm(ops.apply_EK(u[r]) - qref[r]) / np.linalg.norm(qref[r])
+        assert res < 1e-10

@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/rte.h declares (no GPU needed: no compute calls here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2102_09038_gb300 import build
+    return build.build()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, 'include', 'rte.h')).read()
+    src = re.sub(r'/\*.*?\*/', '', src, flags=re.S)
+    return sorted(set(re.findall(r'\b(rte_[a-z_0-9]+)\s*\(', src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ('rte_setup', 'rte_apply', 'rte_precond', 'rte_solve',
+                 'rte_rhs', 'rte_destroy'):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(['nm', '-D', '--defined-only', lib_path],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r'\sT\s+(rte_\w+)', out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+
+
+def test_binding_loads_without_gpu(lib_path):
+    import paper_2102_09038_gb300 as rte
+    lib = rte.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name)
+    o = rte.default_options()
+    assert (o.l, o.n_plus, o.n_minus) == (4, 4, 5)   # Section 6 defaults
+
+
+def test_solver_refuses_without_cuda(lib_path):
+    import torch
+    import paper_2102_09038_gb300 as rte
+    import workloads
+    if torch.cuda.is_available():
+        pytest.skip('a GPU is present')
+    with pytest.raises(RuntimeError):
+        rte.Solver(workloads.constant(2, 0, 0.5, 1.0, 0.5))
