@@ -151,7 +151,11 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
  *  RTE_OP_RESTRICT   coarse <- even: W^T x = X W_N^+
  *  RTE_OP_PROLONG    even <- coarse: W u_c = U_c (W_N^+)^T
  *  RTE_OP_EC         coarse <- coarse: E_c u_c
- *  RTE_OP_EC_INV     coarse <- coarse: E_c^{-1} u_c by CG            */
+ *  RTE_OP_EC_INV     coarse <- coarse: E_c^{-1} u_c by CG
+ *  RTE_OP_E_LO       even <- even : E x in the handle's mixed precision
+ *  RTE_OP_EK_LO      even <- even : (E - K^+) x in the mixed precision
+ * (the _LO ids need a handle set up with RTE_MIXED_FP32 / RTE_MIXED_BF16;
+ * vectors stay FP64 at the interface)                                      */
 #define RTE_OP_A 1
 #define RTE_OP_AT 2
 #define RTE_OP_KPLUS 3
@@ -165,8 +169,19 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
 #define RTE_OP_PROLONG 11
 #define RTE_OP_EC 12
 #define RTE_OP_EC_INV 13
+#define RTE_OP_E_LO 14
+#define RTE_OP_EK_LO 15
 int rte_operator(rte_handle* h, int op, const double* in, double* out,
                  int nrhs);
+
+/* Tensor-core GEMM used by the mixed-precision paths, exposed for testing
+ * and profiling: C[M x N] = A[M x K] * Bt[N x K]^T with A and Bt row-major
+ * (K contiguous) device arrays of BF16 (bf16 != 0) or FP32 read as TF32,
+ * FP32 accumulation, C written as FP32 (or BF16 if out_bf16 and bf16).
+ * K * element size and the base addresses must be multiples of 16 bytes.
+ * Queued on stream (a cudaStream_t). */
+int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K,
+                  int bf16, int out_bf16, void* stream);
 
 /* Copies an assembled matrix to host memory (for checks against an
  * independent assembly).  what: 0 S^+ (n_S^+^2), 1 S^- (n_S^-^2),

@@ -17,7 +17,7 @@ __all__ = ['Solver', 'RteError', 'load', 'OPS', 'FP64', 'MIXED_FP32',
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 MK_EIGEN, MK_PCG = 0, 1
 OPS = dict(A=1, AT=2, KPLUS=3, MK=4, MK_INV=5, MK_PREC=6, E=7, E0_INV=8,
-           P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13)
+           P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13, E_LO=14, EK_LO=15)
 EXPORTS = dict(Splus=0, Sminus=1, m=2, MSm=3, A1=4, A2=5, omx=6, omy=7,
                lamP=8, lamM=9, WpN=10, Ec=11)
 ERRORS = {1: 'RTE_ERR_ARG', 2: 'RTE_ERR_NOMEM', 3: 'RTE_ERR_DIVERGED',
@@ -64,7 +64,8 @@ _lib = None
 EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs',
             'rte_apply', 'rte_precond', 'rte_solve', 'rte_operator',
             'rte_export', 'rte_timing_enable', 'rte_timing_read',
-            'rte_kernel_launches', 'rte_destroy', 'rte_last_error']
+            'rte_kernel_launches', 'rte_gemm_lowp', 'rte_destroy',
+            'rte_last_error']
 
 
 def load(path=LIB_PATH):
@@ -92,6 +93,7 @@ def load(path=LIB_PATH):
                                     ctypes.POINTER(D),
                                     ctypes.POINTER(ctypes.c_longlong), I,
                                     ctypes.POINTER(I)]
+    lib.rte_gemm_lowp.argtypes = [P, P, P, I, I, I, I, I, P]
     lib.rte_kernel_launches.argtypes = []
     lib.rte_kernel_launches.restype = ctypes.c_longlong
     lib.rte_destroy.argtypes = [P]
@@ -107,6 +109,24 @@ def load(path=LIB_PATH):
 def kernel_launches():
     """Kernels launched by librte in this process so far."""
     return int(load().rte_kernel_launches())
+
+
+def gemm_lowp(A, Bt, out_bf16=False, stream=None):
+    """C = A @ Bt.T on the tensor cores (A: M x K, Bt: N x K, both bfloat16
+    or both float32 read as TF32; FP32 accumulation)."""
+    import torch
+    load()
+    bf16 = A.dtype == torch.bfloat16
+    if Bt.dtype != A.dtype or A.dtype not in (torch.bfloat16, torch.float32):
+        raise ValueError('A and Bt must both be bfloat16 or both float32')
+    M, K = A.shape
+    N = Bt.shape[0]
+    C = torch.empty((M, N), device=A.device,
+                    dtype=torch.bfloat16 if (bf16 and out_bf16) else torch.float32)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.rte_gemm_lowp(_ptr(A.contiguous()), _ptr(Bt.contiguous()), _ptr(C), M, N,
+                              K, int(bf16), int(out_bf16), ctypes.c_void_p(st.cuda_stream)))
+    return C
 
 
 def _check(rc):

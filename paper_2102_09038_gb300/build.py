@@ -12,7 +12,7 @@ SRC = os.path.join(HERE, 'csrc')
 OUT = os.path.join(HERE, '_build')
 LIB = os.path.join(OUT, 'librte.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
-SOURCES = ['setup_host.cpp', 'kernels.cu', 'cg.cu', 'rte.cu']
+SOURCES = ['setup_host.cpp', 'mg_host.cpp', 'kernels.cu', 'mg.cu', 'tc_gemm.cu', 'rte.cu']
 
 
 def nvcc():

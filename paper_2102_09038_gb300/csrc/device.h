@@ -1,10 +1,33 @@
 // Device-resident data of one assembled problem and the kernel launchers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "mg.h"
+
 namespace rte {
+
+// FP32 copies of the operator data used by the mixed-precision paths, and
+// the low-precision GEMM operands (BF16 or FP32 read as TF32), K-major.
+struct DevLow {
+    const float* cell_D;       // [nRm][6]
+    const float* cell_at;      // [nRm]
+    const float* cell_as;      // [nRm]
+    const float* sval;         // [kSlots][nnz]
+    const float* m;            // [nSp]
+    const float* omx;
+    const float* omy;
+    const float* A1;           // [nSp][3]
+    const float* A2;
+    const float* e0s;          // [nSp][6]
+    const float* lamM;         // [nSm]
+    const void* VmT;           // GEMM 1 second operand (N x K = V^T)
+    const void* Vm;            // GEMM 2 second operand (N x K = V)
+    const void* Sp;            // scattering second operand (S^+, symmetric)
+    bool bf16;                 // operand type: BF16, else FP32 (TF32 MMA)
+};
 
 // Raw device pointers of an assembled system (owned by rte_handle).
 struct DevSystem {
@@ -45,6 +68,12 @@ struct DevSystem {
     // coarse matrix E_c: blocks [nnz][dP][dP] and inverse diagonal blocks
     const double* ec_val;
     const double* ec_dinv;     // [nRp][dP][dP]
+    DevLow lo;                 // mixed-precision copies (null in FP64 mode)
+    // E_0 level-0 stencil coefficients per direction, [nnz][nSp]
+    const double* e0coef;
+    const float* e0coef_f;
+    MGDevice e0mg;             // multigrid of the E_0 direction blocks
+    MGDevice ecmg;             // multigrid of E_c
 };
 
 // Status words written by persistent kernels (bounded waits, iteration counts).
@@ -69,6 +98,19 @@ void gemm_f64(cudaStream_t s, int M, int N, int K, const double* A, int lda,
 // Z = A U (eq. AR): even (nrhs x nRp x nSp) -> odd (nrhs x nRm x nSm)
 void apply_A(cudaStream_t s, const DevSystem& d, const double* U, double* Z,
              int nrhs);
+
+void apply_A_lo(cudaStream_t s, const DevSystem& d, const float* U, void* Z, bool bf16,
+                int nrhs);
+void apply_even_lo(cudaStream_t s, const DevSystem& d, const float* Zp, const float* X,
+                   const float* V, float* Y, int nrhs, int flags);
+void dot_per_rhs(cudaStream_t s, const float* x, const float* y, size_t len, int nrhs,
+                 double* partial, double* out);
+void axpby_per_rhs(cudaStream_t s, const float* x, float* y, size_t len, int nrhs,
+                   const double* a, double ca, const double* b, double cb);
+void convert(cudaStream_t s, const double* x, float* y, size_t n);
+void convert(cudaStream_t s, const float* x, double* y, size_t n);
+void convert(cudaStream_t s, const float* x, __nv_bfloat16* y, size_t n);
+void convert(cudaStream_t s, const double* x, __nv_bfloat16* y, size_t n);
 
 // Y = [A^T Zp] + [M^+ X + R X] - [M_s^+ V] (terms selected by flags):
 // flags bit0: A^T Zp, bit1: M^+ X + R X, bit2: - M_s^+ V (V = X S^+).
@@ -105,6 +147,10 @@ int e0_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,
           int nrhs, double tol, int maxit, void* work, size_t work_bytes,
           SolveStatus* status_dev);
 size_t e0_cg_work_bytes(const DevSystem& d, int nrhs);
+// The same in FP32 (vectors and coefficients), FP64 right-hand side and
+// solution at the interface, reductions in FP64.
+int e0_cg_lo(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nrhs,
+             double tol, int maxit, void* work, size_t work_bytes, SolveStatus* status_dev);
 
 // E_c^{-1} B by one persistent block-Jacobi CG per RHS.
 int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,
@@ -115,6 +161,9 @@ size_t coarse_cg_work_bytes(const DevSystem& d, int nrhs);
 // y = E_c x
 void coarse_apply(cudaStream_t s, const DevSystem& d, const double* X,
                   double* Y, int nrhs);
+
+// coef[p][k] = sum_s e0s[k][s] sval[slot_s][p] (E_0 direction-block entries)
+void e0_coefficients(cudaStream_t s, const DevSystem& d, double* coef, float* coef_f);
 
 // Assembly of S^+ and S^- by the quadrature rule (setup).
 struct QuadDev {

@@ -2,6 +2,7 @@
 // mass applies (eq. AR, bMebMo with eq. tpmv), the scattering and eigenbasis
 // contractions (eq. bKebKo, Lemma apply_high_order_pre), the coarse-matrix
 // apply, per-RHS reductions, and the setup-time quadrature of S^+ / S^-.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -93,13 +94,15 @@ k_gemm_f64(int M, int N, int K, const double* __restrict__ A, int lda,
 }
 
 // ----------------------------------------------------- transport A (a1)
-// Z[r, j, 3k+c] = sum_n A_n(k, c) (D_n U_r)[j, k]
+// Z[r, j, 3k+c] = sum_n A_n(k, c) (D_n U_r)[j, k]; computed in TC, read as TIn,
+// written as TOut (FP64, or FP32 in / BF16-or-FP32 out for the mixed paths)
+template <typename TIn, typename TOut, typename TC>
 __global__ void k_apply_A(int nRm, int nRp, int nSp, int nrhs,
                           const int* __restrict__ cell_nodes,
-                          const double* __restrict__ cell_D,
-                          const double* __restrict__ A1,
-                          const double* __restrict__ A2,
-                          const double* __restrict__ U, double* __restrict__ Z) {
+                          const TC* __restrict__ cell_D,
+                          const TC* __restrict__ A1,
+                          const TC* __restrict__ A2,
+                          const TIn* __restrict__ U, TOut* __restrict__ Z) {
     const size_t total = (size_t)nrhs * nRm * nSp;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -107,65 +110,66 @@ __global__ void k_apply_A(int nRm, int nRp, int nSp, int nrhs,
         const size_t rj = e / nSp;
         const int j = (int)(rj % nRm);
         const int r = (int)(rj / nRm);
-        const double* Ur = U + (size_t)r * nRp * nSp;
-        double g1 = 0.0, g2 = 0.0;
+        const TIn* Ur = U + (size_t)r * nRp * nSp;
+        TC g1 = 0, g2 = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double u = Ur[(size_t)cell_nodes[3 * j + a] * nSp + k];
+            const TC u = static_cast<TC>(Ur[(size_t)cell_nodes[3 * j + a] * nSp + k]);
             g1 = fma(cell_D[6 * j + a], u, g1);
             g2 = fma(cell_D[6 * j + 3 + a], u, g2);
         }
-        double* z = Z + rj * (3 * (size_t)nSp) + 3 * k;
+        TOut* z = Z + rj * (3 * (size_t)nSp) + 3 * k;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) z[c] = A1[3 * k + c] * g1 + A2[3 * k + c] * g2;
+        for (int c = 0; c < 3; ++c) z[c] = static_cast<TOut>(A1[3 * k + c] * g1 + A2[3 * k + c] * g2);
     }
 }
 
 // ------------------------------------------ A^T + M^+ + R - K^+ (a2, b2)
+template <typename T>
 __global__ void k_apply_even(int nRm, int nRp, int nSp, int nrhs, int nnz,
                              int flags, const int* __restrict__ adj_ptr,
                              const int* __restrict__ adj_cell,
                              const int* __restrict__ adj_loc,
-                             const double* __restrict__ cell_D,
-                             const double* __restrict__ A1,
-                             const double* __restrict__ A2,
+                             const T* __restrict__ cell_D,
+                             const T* __restrict__ A1,
+                             const T* __restrict__ A2,
                              const int* __restrict__ st_ptr,
                              const int* __restrict__ st_col,
-                             const double* __restrict__ sval,
-                             const double* __restrict__ m,
-                             const double* __restrict__ omx,
-                             const double* __restrict__ omy,
-                             const double* __restrict__ Zp,
-                             const double* __restrict__ X,
-                             const double* __restrict__ V, double* __restrict__ Y) {
+                             const T* __restrict__ sval,
+                             const T* __restrict__ m,
+                             const T* __restrict__ omx,
+                             const T* __restrict__ omy,
+                             const T* __restrict__ Zp,
+                             const T* __restrict__ X,
+                             const T* __restrict__ V, T* __restrict__ Y) {
     const size_t total = (size_t)nrhs * nRp * nSp;
-    const double* Mt = sval + (size_t)kMt * nnz;
-    const double* Ms = sval + (size_t)kMs * nnz;
-    const double* Bx = sval + (size_t)kBx * nnz;
-    const double* By = sval + (size_t)kBy * nnz;
+    const T* Mt = sval + (size_t)kMt * nnz;
+    const T* Ms = sval + (size_t)kMs * nnz;
+    const T* Bx = sval + (size_t)kBx * nnz;
+    const T* By = sval + (size_t)kBy * nnz;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int k = (int)(e % nSp);
         const size_t ri = e / nSp;
         const int i = (int)(ri % nRp);
         const int r = (int)(ri / nRp);
-        double acc = 0.0;
+        T acc = 0;
         if (flags & 1) {
-            const double a1[3] = {A1[3 * k], A1[3 * k + 1], A1[3 * k + 2]};
-            const double a2[3] = {A2[3 * k], A2[3 * k + 1], A2[3 * k + 2]};
-            const double* Zr = Zp + (size_t)r * nRm * 3 * nSp;
+            const T a1[3] = {A1[3 * k], A1[3 * k + 1], A1[3 * k + 2]};
+            const T a2[3] = {A2[3 * k], A2[3 * k + 1], A2[3 * k + 2]};
+            const T* Zr = Zp + (size_t)r * nRm * 3 * nSp;
             for (int p = adj_ptr[i]; p < adj_ptr[i + 1]; ++p) {
                 const int j = adj_cell[p], a = adj_loc[p];
-                const double* z = Zr + (size_t)j * 3 * nSp + 3 * k;
-                const double t1 = a1[0] * z[0] + a1[1] * z[1] + a1[2] * z[2];
-                const double t2 = a2[0] * z[0] + a2[1] * z[1] + a2[2] * z[2];
+                const T* z = Zr + (size_t)j * 3 * nSp + 3 * k;
+                const T t1 = a1[0] * z[0] + a1[1] * z[1] + a1[2] * z[2];
+                const T t2 = a2[0] * z[0] + a2[1] * z[1] + a2[2] * z[2];
                 acc += cell_D[6 * j + a] * t1 + cell_D[6 * j + 3 + a] * t2;
             }
         }
         if (flags & 6) {
-            const double mk = m[k], ox = omx[k], oy = omy[k];
-            const double* Xr = X + (size_t)r * nRp * nSp;
-            const double* Vr = V ? V + (size_t)r * nRp * nSp : nullptr;
+            const T mk = m[k], ox = omx[k], oy = omy[k];
+            const T* Xr = X + (size_t)r * nRp * nSp;
+            const T* Vr = V ? V + (size_t)r * nRp * nSp : nullptr;
             for (int p = st_ptr[i]; p < st_ptr[i + 1]; ++p) {
                 const size_t col = (size_t)st_col[p] * nSp + k;
                 if (flags & 2) acc += (mk * Mt[p] + ox * Bx[p] + oy * By[p]) * Xr[col];
@@ -257,16 +261,17 @@ __device__ double block_sum(double v) {
     return v;  // valid in thread 0
 }
 
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_dot_partial(const double* __restrict__ x, const double* __restrict__ y,
+k_dot_partial(const T* __restrict__ x, const T* __restrict__ y,
               size_t len, double* __restrict__ partial) {
     const int r = blockIdx.y;
-    const double* xr = x + (size_t)r * len;
-    const double* yr = y + (size_t)r * len;
+    const T* xr = x + (size_t)r * len;
+    const T* yr = y + (size_t)r * len;
     double s = 0.0;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < len;
          e += (size_t)gridDim.x * blockDim.x)
-        s = fma(xr[e], yr[e], s);
+        s = fma((double)xr[e], (double)yr[e], s);
     s = block_sum<256>(s);
     if (threadIdx.x == 0) partial[(size_t)r * 1024 + blockIdx.x] = s;
 }
@@ -280,18 +285,26 @@ k_dot_final(const double* __restrict__ partial, int nb, double* __restrict__ out
     if (threadIdx.x == 0) out[r] = s;
 }
 
-__global__ void k_axpby(const double* __restrict__ x, double* __restrict__ y,
+template <typename T>
+__global__ void k_axpby(const T* __restrict__ x, T* __restrict__ y,
                         size_t len, int nrhs, const double* __restrict__ a,
                         double ca, const double* __restrict__ b, double cb) {
     const size_t total = len * nrhs;
     for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
          e += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / len);
-        const double av = a ? a[r] : ca;
-        const double bv = b ? b[r] : cb;
-        const double yv = bv == 0.0 ? 0.0 : bv * y[e];
-        y[e] = (x ? av * x[e] : 0.0) + yv;
+        const T av = static_cast<T>(a ? a[r] : ca);
+        const T bv = static_cast<T>(b ? b[r] : cb);
+        const T yv = bv == T(0) ? T(0) : bv * y[e];
+        y[e] = (x ? av * x[e] : T(0)) + yv;
     }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ x, TO* __restrict__ y, size_t n) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x)
+        y[e] = static_cast<TO>(x[e]);
 }
 
 // --------------------------------------------------------- coarse apply
@@ -414,6 +427,19 @@ __global__ void k_symmetrise(int n, double* __restrict__ S) {
     S[(size_t)j * n + i] = v;
 }
 
+__global__ void k_e0_coef(int nnz, int nSp, const double* __restrict__ sval,
+                          const double* __restrict__ e0s, double* __restrict__ coef,
+                          float* __restrict__ coef_f) {
+    const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (e >= (size_t)nnz * nSp) return;
+    const int p = (int)(e / nSp), k = (int)(e % nSp);
+    const int slots[6] = {kK11, kK12, kK22, kBx, kBy, kMt};
+    double c = 0.0;
+    for (int q = 0; q < 6; ++q) c += e0s[6 * k + q] * sval[(size_t)slots[q] * nnz + p];
+    coef[e] = c;
+    if (coef_f) coef_f[e] = (float)c;
+}
+
 __global__ void k_near_rows(int n, const int* __restrict__ near_ptr, int* __restrict__ row) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -451,18 +477,42 @@ void gemm_f64(cudaStream_t s, int M, int N, int K, const double* A, int lda,
 void apply_A(cudaStream_t s, const DevSystem& d, const double* U, double* Z, int nrhs) {
     const size_t total = (size_t)nrhs * d.nRm * d.nSp;
     count_launches(1);
-    k_apply_A<<<grid_for(total), kThreads, 0, s>>>(d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes,
-                                                   d.cell_D, d.ang_A1, d.ang_A2, U, Z);
+    k_apply_A<double, double, double><<<grid_for(total), kThreads, 0, s>>>(
+        d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes, d.cell_D, d.ang_A1, d.ang_A2, U, Z);
+}
+
+void apply_A_lo(cudaStream_t s, const DevSystem& d, const float* U, void* Z, bool bf16,
+                int nrhs) {
+    const size_t total = (size_t)nrhs * d.nRm * d.nSp;
+    count_launches(1);
+    if (bf16)
+        k_apply_A<float, __nv_bfloat16, float><<<grid_for(total), kThreads, 0, s>>>(
+            d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes, d.lo.cell_D, d.lo.A1, d.lo.A2, U,
+            static_cast<__nv_bfloat16*>(Z));
+    else
+        k_apply_A<float, float, float><<<grid_for(total), kThreads, 0, s>>>(
+            d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes, d.lo.cell_D, d.lo.A1, d.lo.A2, U,
+            static_cast<float*>(Z));
 }
 
 void apply_even(cudaStream_t s, const DevSystem& d, const double* Zp, const double* X,
                 const double* V, double* Y, int nrhs, int flags) {
     const size_t total = (size_t)nrhs * d.nRp * d.nSp;
     count_launches(1);
-    k_apply_even<<<grid_for(total), kThreads, 0, s>>>(
+    k_apply_even<double><<<grid_for(total), kThreads, 0, s>>>(
         d.nRm, d.nRp, d.nSp, nrhs, d.nnz, flags, d.adj_ptr, d.adj_cell, d.adj_loc,
         d.cell_D, d.ang_A1, d.ang_A2, d.st_ptr, d.st_col, d.sval, d.ang_m, d.ang_omx,
         d.ang_omy, Zp, X, V, Y);
+}
+
+void apply_even_lo(cudaStream_t s, const DevSystem& d, const float* Zp, const float* X,
+                   const float* V, float* Y, int nrhs, int flags) {
+    const size_t total = (size_t)nrhs * d.nRp * d.nSp;
+    count_launches(1);
+    k_apply_even<float><<<grid_for(total), kThreads, 0, s>>>(
+        d.nRm, d.nRp, d.nSp, nrhs, d.nnz, flags, d.adj_ptr, d.adj_cell, d.adj_loc,
+        d.lo.cell_D, d.lo.A1, d.lo.A2, d.st_ptr, d.st_col, d.lo.sval, d.lo.m, d.lo.omx,
+        d.lo.omy, Zp, X, V, Y);
 }
 
 void mk_combine(cudaStream_t s, const DevSystem& d, const double* Z, const double* G,
@@ -488,18 +538,55 @@ void rhs_source(cudaStream_t s, const DevSystem& d, const double* qn, double* q,
                                                       d.st_col, d.sval, d.ang_m, qn, q);
 }
 
-void dot_per_rhs(cudaStream_t s, const double* x, const double* y, size_t len, int nrhs,
-                 double* partial, double* out) {
+template <typename T>
+void dot_impl(cudaStream_t s, const T* x, const T* y, size_t len, int nrhs, double* partial,
+              double* out) {
     int nb = (int)std::min<size_t>(1024, std::max<size_t>(1, (len + 2047) / 2048));
     count_launches(2);
-    k_dot_partial<<<dim3(nb, nrhs), 256, 0, s>>>(x, y, len, partial);
+    k_dot_partial<T><<<dim3(nb, nrhs), 256, 0, s>>>(x, y, len, partial);
     k_dot_final<<<nrhs, 256, 0, s>>>(partial, nb, out);
+}
+
+void dot_per_rhs(cudaStream_t s, const double* x, const double* y, size_t len, int nrhs,
+                 double* partial, double* out) {
+    dot_impl(s, x, y, len, nrhs, partial, out);
+}
+
+void dot_per_rhs(cudaStream_t s, const float* x, const float* y, size_t len, int nrhs,
+                 double* partial, double* out) {
+    dot_impl(s, x, y, len, nrhs, partial, out);
 }
 
 void axpby_per_rhs(cudaStream_t s, const double* x, double* y, size_t len, int nrhs,
                    const double* a, double ca, const double* b, double cb) {
     count_launches(1);
-    k_axpby<<<grid_for(len * nrhs), kThreads, 0, s>>>(x, y, len, nrhs, a, ca, b, cb);
+    k_axpby<double><<<grid_for(len * nrhs), kThreads, 0, s>>>(x, y, len, nrhs, a, ca, b, cb);
+}
+
+void axpby_per_rhs(cudaStream_t s, const float* x, float* y, size_t len, int nrhs,
+                   const double* a, double ca, const double* b, double cb) {
+    count_launches(1);
+    k_axpby<float><<<grid_for(len * nrhs), kThreads, 0, s>>>(x, y, len, nrhs, a, ca, b, cb);
+}
+
+void convert(cudaStream_t s, const double* x, float* y, size_t n) {
+    count_launches(1);
+    k_convert<double, float><<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+}
+
+void convert(cudaStream_t s, const float* x, double* y, size_t n) {
+    count_launches(1);
+    k_convert<float, double><<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+}
+
+void convert(cudaStream_t s, const float* x, __nv_bfloat16* y, size_t n) {
+    count_launches(1);
+    k_convert<float, __nv_bfloat16><<<grid_for(n), kThreads, 0, s>>>(x, y, n);
+}
+
+void convert(cudaStream_t s, const double* x, __nv_bfloat16* y, size_t n) {
+    count_launches(1);
+    k_convert<double, __nv_bfloat16><<<grid_for(n), kThreads, 0, s>>>(x, y, n);
 }
 
 void coarse_apply(cudaStream_t s, const DevSystem& d, const double* X, double* Y, int nrhs) {
@@ -507,6 +594,12 @@ void coarse_apply(cudaStream_t s, const DevSystem& d, const double* X, double* Y
     count_launches(1);
     k_coarse_apply<<<grid_for(total), kThreads, 0, s>>>(d.nRp, d.dP, nrhs, d.st_ptr,
                                                         d.st_col, d.ec_val, X, Y);
+}
+
+void e0_coefficients(cudaStream_t s, const DevSystem& d, double* coef, float* coef_f) {
+    const size_t n = (size_t)d.nnz * d.nSp;
+    k_e0_coef<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.nnz, d.nSp, d.sval, d.e0s, coef,
+                                                         coef_f);
 }
 
 void assemble_scattering(cudaStream_t s, int n, double g, const QuadDev& q, double* Sp,

@@ -1,0 +1,64 @@
+// Helpers for persistent cooperative kernels: a grid barrier whose waits are
+// bounded, L2-coherent loads, and workspace carving.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace rte {
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+// Spins of ~128 ns before a barrier gives up (about 2 s).
+constexpr unsigned long long kSpinLimit = 1ull << 24;
+
+// All blocks of the (co-resident) grid meet here.  A wait that runs out sets
+// gb->err, and every later barrier returns false at once, so the kernel can
+// leave cleanly and the host reads RTE_ERR_TIMEOUT.
+__device__ __forceinline__ bool grid_sync(GridBar* gb) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &gb->gen;
+        volatile int* verr = &gb->err;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&gb->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == g) {
+                __nanosleep(128);
+                if (*verr) break;
+                if (++spins > kSpinLimit) {
+                    atomicExch(&gb->err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *((volatile int*)&gb->err) == 0;
+}
+
+// Loads of data written by other blocks of the same kernel: bypass L1.
+__device__ __forceinline__ double ldg2(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldg2(const float* p) { return __ldcg(p); }
+
+template <typename T>
+inline T* carve(char*& p, size_t n) {
+    T* out = reinterpret_cast<T*>(p);
+    p += ((n * sizeof(T) + 255) / 256) * 256;
+    return out;
+}
+
+}  // namespace rte

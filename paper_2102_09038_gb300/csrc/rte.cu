@@ -12,7 +12,9 @@
 #include <vector>
 
 #include "device.h"
+#include "mg_host.h"
 #include "rte_internal.h"
+#include "tc_gemm.h"
 
 namespace rte {
 
@@ -53,6 +55,11 @@ struct rte_handle {
     double *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr, *e5 = nullptr,
            *e6 = nullptr, *e7 = nullptr, *e8 = nullptr;                     // even
     double *c1 = nullptr, *c2 = nullptr;                                    // coarse
+    // mixed precision: FP32 even vectors, low-precision odd GEMM operands
+    bool mixed = false;
+    float *f1 = nullptr, *f2 = nullptr, *f3 = nullptr;
+    void *zl1 = nullptr, *zl2 = nullptr, *xl = nullptr;
+    float* zf = nullptr;
     double *partial = nullptr, *sc = nullptr;                               // reductions
     void* e0work = nullptr;
     size_t e0bytes = 0;
@@ -249,6 +256,97 @@ void inv_lower3(const double* L, double* Li) {
     }
 }
 
+// Uploads a host multigrid hierarchy; work vectors hold cols columns of bs
+// values per node.
+int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv,
+              MGDevice& out) {
+    out.L = (int)mh.levels.size();
+    if (out.L > kMaxMGLevels) return fail(RTE_ERR_ARG, "too many multigrid levels");
+    out.nu = 2;
+    out.cap_cols = cols;
+    out.dense = mh.dense_coarse;
+    for (int l = 0; l < out.L; ++l) {
+        const MGHostLevel& L = mh.levels[l];
+        MGDeviceLevel& D = out.lev[l];
+        D.n = (L.m + 1) * (L.m + 1);
+        D.nnz = (int)L.st.col.size();
+        RTE_TRY(upload(h, &D.ptr, L.st.ptr));
+        RTE_TRY(upload(h, &D.col, L.st.col));
+        RTE_TRY(upload(h, &D.diag, L.st.diag));
+        RTE_TRY(upload(h, &D.val, std::vector<float>(L.vals.begin(), L.vals.end())));
+        if (block_dinv) {
+            std::vector<float> di;
+            RTE_TRY(block_diag_inverse(L, bs, di));
+            RTE_TRY(upload(h, &D.dinv, di));
+        }
+        if (l + 1 < out.L) {
+            RTE_TRY(upload(h, &D.rptr, L.rptr));
+            RTE_TRY(upload(h, &D.ridx, L.ridx));
+            RTE_TRY(upload(h, &D.rw, L.rw));
+            RTE_TRY(upload(h, &D.p0, L.p0));
+            RTE_TRY(upload(h, &D.p1, L.p1));
+            RTE_TRY(upload(h, &D.w0, L.w0));
+            RTE_TRY(upload(h, &D.w1, L.w1));
+        }
+        const size_t nv = (size_t)D.n * cols * bs;
+        RTE_TRY(dalloc(h, &D.X, nv));
+        RTE_TRY(dalloc(h, &D.Xt, nv));
+        RTE_TRY(dalloc(h, &D.B, nv));
+    }
+    return RTE_OK;
+}
+
+// Coarsest-level inverses no larger than this many nodes are formed densely.
+constexpr int kDenseCoarseNodes = 256;
+
+int setup_multigrid(rte_handle* h, const HostSystem& hs) {
+    DevSystem& d = h->d;
+    const int cap = h->opt.max_rhs;
+    // ------------------------------------------------------------ E_0
+    {
+        const int slots[6] = {kK11, kK12, kK22, kBx, kBy, kMt};
+        const size_t nnz = hs.st.col.size();
+        std::vector<double> v((size_t)6 * nnz);
+        for (int q = 0; q < 6; ++q)
+            std::copy(hs.sval.begin() + (size_t)slots[q] * nnz,
+                      hs.sval.begin() + (size_t)(slots[q] + 1) * nnz, v.begin() + q * nnz);
+        MGHost mh;
+        RTE_TRY(build_hierarchy(hs.m, hs.st, v, 6, 1, kDenseCoarseNodes, mh));
+        RTE_TRY(upload_mg(h, mh, cap * hs.nSp, 1, false, d.e0mg));
+        const float* e0f = nullptr;
+        RTE_TRY(upload(h, &e0f, std::vector<float>(hs.e0s.begin(), hs.e0s.end())));
+        d.e0mg.e0s = e0f;
+        if (d.e0mg.dense) {
+            std::vector<float> all, one;
+            for (int k = 0; k < hs.nSp; ++k) {
+                std::vector<double> w(hs.e0s.begin() + 6 * k, hs.e0s.begin() + 6 * k + 6);
+                RTE_TRY(coarse_dense_inverse(mh.levels.back(), w, 6, 1, one));
+                all.insert(all.end(), one.begin(), one.end());
+            }
+            RTE_TRY(upload(h, &d.e0mg.cinv, all));
+        }
+        double* c = nullptr;
+        float* cf = nullptr;
+        RTE_TRY(dalloc(h, &c, nnz * hs.nSp));
+        if (h->mixed) RTE_TRY(dalloc(h, &cf, nnz * hs.nSp));
+        e0_coefficients(h->stream, d, c, cf);
+        d.e0coef = c;
+        d.e0coef_f = cf;
+    }
+    // ------------------------------------------------------------ E_c
+    if (d.dP > 0) {
+        MGHost mh;
+        RTE_TRY(build_hierarchy(hs.m, hs.st, h->h_ec, 1, d.dP, kDenseCoarseNodes, mh));
+        RTE_TRY(upload_mg(h, mh, cap, d.dP, true, d.ecmg));
+        if (d.ecmg.dense) {
+            std::vector<float> inv;
+            RTE_TRY(coarse_dense_inverse(mh.levels.back(), {}, 1, d.dP, inv));
+            RTE_TRY(upload(h, &d.ecmg.cinv, inv));
+        }
+    }
+    return RTE_OK;
+}
+
 // ------------------------------------------------------------ workspace
 int ensure_workspace(rte_handle* h, int nrhs) {
     if (nrhs <= h->cap_rhs) return RTE_OK;
@@ -284,6 +382,20 @@ int alloc_workspace(rte_handle* h, int nrhs) {
     RTE_TRY(dalloc(h, &w, h->cobytes));
     h->cowork = w;
     RTE_TRY(dalloc(h, &h->status, 1));
+    if (h->mixed) {
+        const size_t lo = d.lo.bf16 ? 2 : 4;
+        RTE_TRY(dalloc(h, &h->f1, ne));
+        RTE_TRY(dalloc(h, &h->f2, ne));
+        RTE_TRY(dalloc(h, &h->f3, ne));
+        RTE_TRY(dalloc(h, &h->zf, no));
+        char* p = nullptr;
+        RTE_TRY(dalloc(h, &p, no * lo));
+        h->zl1 = p;
+        RTE_TRY(dalloc(h, &p, no * lo));
+        h->zl2 = p;
+        RTE_TRY(dalloc(h, &p, ne * lo));
+        h->xl = p;
+    }
     h->cap_rhs = nrhs;
     return RTE_OK;
 }
@@ -418,6 +530,53 @@ int apply_E(rte_handle* h, const double* x, double* y, int nrhs, bool with_k) {
     return RTE_OK;
 }
 
+// ---------------------------------------------- mixed-precision operators
+// y = E x (with_k: (E - K^+) x) with FP32 vectors: transport and the fused
+// gather in FP32, the eigenbasis contractions of (M^- - K^-)^{-1} and the
+// scattering product U S^+ on the tensor cores (BF16 or TF32 operands, FP32
+// accumulation).
+int apply_E_lo(rte_handle* h, const float* x, float* y, int nrhs, bool with_k) {
+    const DevSystem& d = h->d;
+    const bool bf = d.lo.bf16;
+    {
+        Scope sc(h, "transport_A_lo");
+        apply_A_lo(h->stream, d, x, h->zl1, bf, nrhs);
+    }
+    TcGemmArgs g{};
+    g.tf32 = !bf;
+    {
+        Scope sc(h, "tc_gemm_mk1");
+        g.A = h->zl1; g.Bt = d.lo.VmT; g.C = h->zl2;
+        g.M = nrhs * d.nRm; g.N = d.nSm; g.K = d.nSm; g.ldc = d.nSm;
+        g.epi = 1; g.at = d.lo.cell_at; g.as = d.lo.cell_as; g.lam = d.lo.lamM; g.rows = d.nRm;
+        g.out_bf16 = bf;
+        RTE_TRY(tc_gemm(h->stream, g));
+    }
+    {
+        Scope sc(h, "tc_gemm_mk2");
+        g.A = h->zl2; g.Bt = d.lo.Vm; g.C = h->zf; g.epi = 0; g.out_bf16 = false;
+        RTE_TRY(tc_gemm(h->stream, g));
+    }
+    float* V = nullptr;
+    if (with_k) {
+        Scope sc(h, "tc_gemm_kplus");
+        const void* xop = x;
+        if (bf) {
+            convert(h->stream, x, static_cast<__nv_bfloat16*>(h->xl),
+                    (size_t)nrhs * d.nRp * d.nSp);
+            xop = h->xl;
+        }
+        V = h->f3;
+        TcGemmArgs k{};
+        k.tf32 = !bf; k.A = xop; k.Bt = d.lo.Sp; k.C = V;
+        k.M = nrhs * d.nRp; k.N = d.nSp; k.K = d.nSp; k.ldc = d.nSp; k.rows = 1;
+        RTE_TRY(tc_gemm(h->stream, k));
+    }
+    Scope sc(h, "apply_even_lo");
+    apply_even_lo(h->stream, d, h->zf, x, V, y, nrhs, with_k ? 7 : 3);
+    return RTE_OK;
+}
+
 int read_status(rte_handle* h, SolveStatus& st) {
     RTE_CUDA_TRY(cudaMemcpyAsync(&st, h->status, sizeof(SolveStatus), cudaMemcpyDeviceToHost,
                                  h->stream));
@@ -426,8 +585,16 @@ int read_status(rte_handle* h, SolveStatus& st) {
     return RTE_OK;
 }
 
+// FP32 CG stalls near its rounding level: mixed modes stop the E_0 solves at
+// a relative residual of at least this (the FP64 outer loop absorbs it).
+constexpr double kLowInnerTol = 1e-5;
+
 int e0_inv(rte_handle* h, const double* b, double* x, int nrhs) {
-    {
+    if (h->mixed) {
+        Scope sc(h, "e0_cg_lo");
+        RTE_TRY(e0_cg_lo(h->stream, h->d, b, x, nrhs, std::max(h->opt.e0_tol, kLowInnerTol),
+                         h->opt.e0_maxit, h->e0work, h->e0bytes, h->status));
+    } else {
         Scope sc(h, "e0_cg");
         RTE_TRY(e0_cg(h->stream, h->d, b, x, nrhs, h->opt.e0_tol, h->opt.e0_maxit, h->e0work,
                       h->e0bytes, h->status));
@@ -451,12 +618,22 @@ int coarse_inv(rte_handle* h, const double* b, double* x, int nrhs) {
 }
 
 // z = P_1^l b (eq. applyP1).  Uses e5, e6 (and apply_E's buffers).
+// E x for the inner steps: FP64, or FP32 with an FP64 interface in mixed modes
+int apply_E_inner(rte_handle* h, const double* x, double* y, int nrhs, bool with_k) {
+    if (!h->mixed) return apply_E(h, x, y, nrhs, with_k);
+    const size_t n = (size_t)nrhs * h->d.nRp * h->d.nSp;
+    convert(h->stream, x, h->f1, n);
+    RTE_TRY(apply_E_lo(h, h->f1, h->f2, nrhs, with_k));
+    convert(h->stream, h->f2, y, n);
+    return RTE_OK;
+}
+
 int apply_P1(rte_handle* h, const double* b, double* z, int nrhs) {
     const DevSystem& d = h->d;
     const size_t len = (size_t)d.nRp * d.nSp;
     RTE_TRY(e0_inv(h, b, z, nrhs));   // z_1 = E_0^{-1} b
     for (int k = 1; k < h->opt.l; ++k) {
-        RTE_TRY(apply_E(h, z, h->e5, nrhs, false));
+        RTE_TRY(apply_E_inner(h, z, h->e5, nrhs, false));
         {
             Scope sc(h, "axpy");
             axpby_per_rhs(h->stream, b, h->e5, len, nrhs, nullptr, -1.0, nullptr, 1.0);
@@ -490,7 +667,7 @@ int precond(rte_handle* h, const double* r, double* s, int nrhs, bool p2) {
     const size_t len = (size_t)d.nRp * d.nSp;
     RTE_TRY(apply_P1(h, r, s, nrhs));
     if (!p2 || d.dP == 0) return RTE_OK;
-    RTE_TRY(apply_E(h, s, h->e7, nrhs, true));
+    RTE_TRY(apply_E_inner(h, s, h->e7, nrhs, true));
     {
         Scope sc(h, "axpy");   // e7 = r - (E - K^+) s
         axpby_per_rhs(h->stream, r, h->e7, len, nrhs, nullptr, 1.0, nullptr, -1.0);
@@ -543,8 +720,11 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     if (o.l < 1 || o.n_minus < 1 || (o.n_minus % 2) == 0 || (o.n_plus >= 0 && o.n_plus % 2) ||
         o.max_rhs < 1 || o.mk_maxit < 1 || o.e0_maxit < 1 || o.coarse_maxit < 1)
         return fail(RTE_ERR_ARG, "invalid options (l >= 1, odd N^- >= 1, even N^+ or -1)");
-    if (o.precision != RTE_FP64)
-        return fail(RTE_ERR_ARG, "only RTE_FP64 is available in this build");
+    if (o.precision != RTE_FP64 && o.precision != RTE_MIXED_FP32 &&
+        o.precision != RTE_MIXED_BF16)
+        return fail(RTE_ERR_ARG, "unknown precision mode");
+    if (o.precision != RTE_FP64 && o.mk_route != RTE_MK_EIGEN)
+        return fail(RTE_ERR_ARG, "mixed precision uses the eigenbasis route for (M-K)^-1");
     HostSystem hs;
     RTE_TRY(build_host_system(*prob, o, hs));
     rte_handle* h = new rte_handle();
@@ -790,7 +970,48 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         UP(ec_val, h->h_ec);
         UP(ec_dinv, dinv);
     }
+    if (o.precision != RTE_FP64) {
+        h->mixed = true;
+        DevLow& lo = d.lo;
+        lo.bf16 = o.precision == RTE_MIXED_BF16;
+        auto tof = [](const std::vector<double>& v) {
+            return std::vector<float>(v.begin(), v.end());
+        };
+#define UPF(dst, src) do { rc = upload(h, &lo.dst, tof(src)); if (rc) return bail(rc); } while (0)
+        UPF(cell_D, hs.cell_D);
+        UPF(cell_at, hs.cell_at);
+        UPF(cell_as, hs.cell_as);
+        UPF(sval, hs.sval);
+        UPF(m, hs.m_);
+        UPF(omx, hs.omx);
+        UPF(omy, hs.omy);
+        UPF(A1, hs.A1);
+        UPF(A2, hs.A2);
+        UPF(e0s, hs.e0s);
+        UPF(lamM, h->h_lamM);
+#undef UPF
+        // GEMM second operands, K-major: GEMM 1 multiplies by V (needs V^T),
+        // GEMM 2 by V^T (needs V), the scattering product by S^+ = (S^+)^T
+        const std::vector<double>* srcs[3] = {&VmT, &Vm, &h->h_Sp};
+        const void** dsts[3] = {&lo.VmT, &lo.Vm, &lo.Sp};
+        for (int t = 0; t < 3; ++t) {
+            const std::vector<double>& v = *srcs[t];
+            if (lo.bf16) {
+                std::vector<__nv_bfloat16> b(v.size());
+                for (size_t i = 0; i < v.size(); ++i) b[i] = __float2bfloat16_rn((float)v[i]);
+                const __nv_bfloat16* p = nullptr;
+                rc = upload(h, &p, b); if (rc) return bail(rc);
+                *dsts[t] = p;
+            } else {
+                const float* p = nullptr;
+                rc = upload(h, &p, tof(v)); if (rc) return bail(rc);
+                *dsts[t] = p;
+            }
+        }
+    }
 #undef UP
+    rc = setup_multigrid(h, hs);
+    if (rc) return bail(rc);
     rc = alloc_workspace(h, o.max_rhs);
     if (rc) return bail(rc);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -866,6 +1087,12 @@ int rte_operator(rte_handle* h, int op, const double* in, double* out, int nrhs)
         case RTE_OP_PROLONG: RTE_TRY(prolong_add(h, in, out, nrhs, 0.0)); break;
         case RTE_OP_EC: coarse_apply(s, d, in, out, nrhs); break;
         case RTE_OP_EC_INV: RTE_TRY(coarse_inv(h, in, out, nrhs)); break;
+        case RTE_OP_E_LO:
+        case RTE_OP_EK_LO:
+            if (!h->mixed) return fail(RTE_ERR_ARG, "handle was set up in FP64 mode");
+            RTE_TRY(apply_E_inner(h, in, out, nrhs, op == RTE_OP_EK_LO));
+            RTE_TRY(tc_gemm_error(s));
+            break;
         default: return fail(RTE_ERR_ARG, "unknown operator id");
     }
     RTE_CUDA_TRY(cudaGetLastError());
@@ -994,6 +1221,16 @@ int rte_timing_read(rte_handle* h, const char** names, double* ms, long long* la
 }
 
 long long rte_kernel_launches(void) { return launches_total(); }
+
+int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K, int bf16,
+                  int out_bf16, void* stream) {
+    if (!A || !Bt || !C || M < 0 || N < 0 || K < 0) return fail(RTE_ERR_ARG, "bad argument");
+    TcGemmArgs g{};
+    g.A = A; g.Bt = Bt; g.C = C; g.M = M; g.N = N; g.K = K; g.ldc = N;
+    g.tf32 = bf16 == 0; g.out_bf16 = bf16 != 0 && out_bf16 != 0; g.rows = 1;
+    RTE_TRY(tc_gemm((cudaStream_t)stream, g));
+    return tc_gemm_error((cudaStream_t)stream);
+}
 
 void rte_destroy(rte_handle* h) {
     if (!h) return;
