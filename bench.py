@@ -42,8 +42,20 @@ def parse():
     ap.add_argument('--steps', type=int, default=3)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--precision', default='fp64',
+    ap.add_argument('--precision', default='mixed_bf16',
                     choices=['fp64', 'mixed_fp32', 'mixed_bf16'])
+    ap.add_argument('--mesh', type=int, default=128,
+                    help='mesh size (profiling of smaller cases only)')
+    ap.add_argument('--levels', type=int, default=3,
+                    help='sphere refinement levels (profiling only)')
+    ap.add_argument('--profile-once', action='store_true',
+                    help='set up, run one solve and exit (for ncu captures)')
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--no-fp64-compare', action='store_true',
+                    help='skip the plain-FP64 comparison solve')
+    ap.add_argument('--no-serving', action='store_true',
+                    help='skip the serving (continuous batching) measurement')
+    ap.add_argument('--serve-requests', type=int, default=48)
     return ap.parse_args()
 
 
@@ -156,20 +168,53 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-def kernel_work(name, d, nrhs):
-    """Algorithmic work per launch of a named kernel group: (amount, unit,
-    bound).  FP64 GEMMs count 2 M N K flops; HBM-bound kernels count the
-    bytes they must read and write once."""
+def kernel_work(name, d, nrhs, info):
+    """Algorithmic work of one launch of a named kernel group: (amount, unit,
+    bound).  Contractions count 2 M N K flops.  Memory-bound kernels count
+    the bytes they must move once per launch:
+      * transport A: read U^+ (FP64), write Z (FP64);
+      * A^T + M^+ + R - K^+ gather: read Z, U^+ and U S^+, write Y;
+      * E_0 PCG (persistent): per CG iteration and (node, column) the level-0
+        CG traffic (7 stencil coefficients, P, AP write, X/R/P/AP updates,
+        z, V-cycle input: 18 words of the CG precision plus 16 B of FP64 X)
+        and the V-cycle's 18 FP32 array passes on every level (4^-l of the
+        level-0 size), times the iterations the launch took;
+      * E_c PCG: per iteration the FP64 level-0 blocks (7 d^2 per node) and
+        ~12 FP64 vector passes, plus the FP32 V-cycle (7 d^2 + 18 d words
+        per node per sweep-equivalent, 4/3 for the coarser levels)."""
     nRp, nRm, nS, nSm = d['nRp'], d['nRm'], d['nSp'], d['nSm']
     if name in ('gemm_mk_eig1', 'gemm_mk_eig2'):
-        return 2.0 * nrhs * nRm * nSm * nSm, 'flop', 'alu'
+        return 2.0 * nrhs * nRm * nSm * nSm, 'flop', 'fp64'
+    if name in ('tc_gemm_mk1', 'tc_gemm_mk2'):
+        return 2.0 * nrhs * nRm * nSm * nSm, 'flop', 'tensor'
     if name == 'gemm_kplus':
-        return 2.0 * nrhs * nRp * nS * nS, 'flop', 'alu'
+        return 2.0 * nrhs * nRp * nS * nS, 'flop', 'fp64'
     if name == 'transport_A':
         return 8.0 * nrhs * (nRp * nS + nRm * nSm), 'byte', 'hbm'
     if name == 'apply_even':
         return 8.0 * nrhs * (nRm * nSm + 3 * nRp * nS), 'byte', 'hbm'
+    if name in ('e0_cg', 'e0_cg_lo'):
+        ts = 8 if name == 'e0_cg' else 4
+        cols = nrhs * nS
+        cg = nRp * cols * (18 * ts + 16)
+        vc = sum(nRp / 4 ** l * cols * 4 * 18 for l in range(d['e0_levels']))
+        return (cg + vc) * max(info.get('e0_iters', 1), 1), 'byte', 'hbm'
+    if name == 'coarse_cg':
+        dp = d['dP']
+        cg = nRp * nrhs * (7 * dp * dp + 12 * dp) * 8
+        vc = nRp * nrhs * (7 * dp * dp + 18 * dp) * 4 * 6 * 4 / 3
+        return (cg + vc) * max(info.get('coarse_iters', 1), 1), 'byte', 'hbm'
     return None
+
+
+def levels_of(m, max_nodes=300):
+    """Multigrid levels the library builds for an m x m mesh (halving while
+    m is even, m >= 4 and the level has more than max_nodes nodes)."""
+    lv = 1
+    while m % 2 == 0 and m >= 4 and (m + 1) ** 2 > max_nodes:
+        m //= 2
+        lv += 1
+    return lv
 
 
 def run_ours(args):
@@ -185,7 +230,8 @@ def run_ours(args):
         dist.init_process_group('nccl')
     prec = dict(fp64=rte.FP64, mixed_fp32=rte.MIXED_FP32,
                 mixed_bf16=rte.MIXED_BF16)[args.precision]
-    p = workloads.checkerboard(m=128, levels=3, g=0.9, ratio=0.99, seed=rank)
+    p = workloads.checkerboard(m=args.mesh, levels=args.levels, g=0.9, ratio=0.99,
+                               seed=rank)
     solver = rte.Solver(p, precision=prec)
     qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
     q = solver.rhs(qn)
@@ -200,6 +246,12 @@ def run_ours(args):
             raise RuntimeError('solve failed: %s' % info)
         return info
 
+    if args.profile_once:
+        info = step()
+        torch.cuda.synchronize()
+        print(json.dumps(dict(profile_once=True, iterations=info['iterations'],
+                              rel_residual=info['rel_residual'])))
+        return
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -224,33 +276,36 @@ def run_ours(args):
 
     # ------------------------------------------------- per-kernel timing
     solver.timing(True)
-    step()
+    last_info = step()
     tim = solver.timing_read()
     solver.timing(False)
     d = dict(nRp=solver.n_nodes, nRm=solver.n_cells, nSp=solver.n_dirs,
              nSm=solver.n_odd)
     top = max(tim.items(), key=lambda kv: kv[1][0])
     peaks, src = load_peaks()
-    roof = None
-    work = kernel_work(top[0], d, p.nrhs)
+    d['e0_levels'] = levels_of(args.mesh)
+    d['dP'] = solver.d_plus
+    work = kernel_work(top[0], d, p.nrhs, last_info)
     avg_ms = top[1][0] / max(top[1][1], 1)
+    roof = dict(kernel=top[0], bound=None, achieved=None, peak=None, unit=None,
+                frac=None, traffic=None, launches=top[1][1], avg_ms=avg_ms)
     if work is not None:
         amount, unit, bound = work
-        if unit == 'flop':
+        if unit == 'flop' and bound == 'fp64':
             peak = fp64_peak_tflops(torch)
             ach = amount / (avg_ms / 1e3) / 1e12
-            roof = dict(kernel=top[0], bound=bound, achieved=ach, peak=peak,
-                        unit='TFLOP/s', frac=ach / peak, traffic=None,
-                        peak_source='measured cuBLAS FP64 GEMM in this run')
+            roof.update(bound='alu', achieved=ach, peak=peak, unit='TFLOP/s',
+                        frac=ach / peak, peak_source='measured cuBLAS FP64 GEMM in this run')
+        elif unit == 'flop':
+            ach = amount / (avg_ms / 1e3) / 1e12
+            peak = peaks['bf16_tflops']
+            roof.update(bound='tensor', achieved=ach, peak=peak, unit='TFLOP/s',
+                        frac=ach / peak, peak_source=src + ' bf16 burst')
         else:
             ach = amount / (avg_ms / 1e3) / 1e9
-            roof = dict(kernel=top[0], bound=bound, achieved=ach,
-                        peak=peaks['hbm_gbs'], unit='GB/s',
-                        frac=ach / peaks['hbm_gbs'], traffic=None,
-                        peak_source=src)
-    else:
-        roof = dict(kernel=top[0], bound='hbm', achieved=None, peak=None,
-                    unit=None, frac=None, traffic=None)
+            roof.update(bound=bound, achieved=ach, peak=peaks['hbm_gbs'], unit='GB/s',
+                        frac=ach / peaks['hbm_gbs'], peak_source=src,
+                        algorithmic_bytes=amount)
     share = {k: round(v[0] / sum(x[0] for x in tim.values()), 4)
              for k, v in tim.items()}
 
@@ -281,8 +336,30 @@ def run_ours(args):
                d2h_bytes_per_step=uh.numel() * 8,
                time_to_tol_s=e2e_secs / args.steps)
 
+    fp64 = None
+    if not args.no_fp64_compare and args.precision != 'fp64':
+        s64 = rte.Solver(p, precision=rte.FP64)
+        q64 = s64.rhs(qn)
+        u64 = s64.even(p.nrhs)
+        _, i64 = s64.solve(q64, u=u64, tol=p.tol)    # warm-up
+        u64.zero_()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        f0.record(s64.stream)
+        _, i64 = s64.solve(q64, u=u64, tol=p.tol)
+        f1.record(s64.stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1e3
+        fp64 = dict(precision='fp64 (SIMT FP64 GEMMs, inner solves to 1e-12)',
+                    time_to_tol_s=t64, iterations=i64['iterations'],
+                    value=dofs * i64['iterations'] / t64, unit='DOF*iter/s',
+                    mixed_speedup_time_to_tol=t64 / (secs / args.steps))
+        s64.close()
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = serving_bench(args, torch, rte)
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
 
     if rank == 0:
@@ -299,10 +376,81 @@ def run_ours(args):
                                   % (d['nRm'] * d['nSm'] * 8 // 2 ** 20),
                                parallelism='replicas' if world > 1 else 'single'),
                    e2e=e2e, gpu_launches=launches, roofline=roof,
-                   kernel_share=share, clocks=clk.summary(), cpu_baseline=cpu)
+                   kernel_share=share, clocks=clk.summary(), cpu_baseline=cpu,
+                   fp64_compare=fp64, serving=serving)
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def serving_requests(n, seed=0):
+    """A seeded stream of solve requests mixing the sizes and parameters of
+    the other workloads (plain 32x32/128-triangle problems, uneven instances
+    with 32..64 meshes, 128 or 512 triangles, g in [0.3, 0.9], log-uniform
+    sigma_t, sigma_s/sigma_t in [0.5, 0.999], 1..4 Gaussian sources)."""
+    import numpy as np
+    import workloads
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        kind = rng.integers(0, 3)
+        if kind == 0:
+            p = workloads.plain_fp64()
+        else:
+            p = workloads.batch_instances(1, seed=int(rng.integers(1 << 30)),
+                                          m_range=(32, 64), levels=(2, 3),
+                                          nrhs_range=(1, 4))[0]
+        out.append(p)
+    return out
+
+
+def serving_bench(args, torch, rte):
+    """Continuous batching: requests arrive as a Poisson stream (rate set to
+    ~1.5x the measured sequential throughput, so the server must overlap
+    them), are admitted by an HBM budget into worker slots, and their
+    latencies (submission to completion) give p50/p99.  The same requests
+    solved one after another in plain FP64 give the sequential baseline."""
+    import numpy as np
+    reqs = serving_requests(args.serve_requests, seed=1)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.6)
+    opts = dict(precision=rte.MIXED_BF16)
+    # sequential FP64 reference on a sample
+    sample = reqs[:6]
+    t0 = time.perf_counter()
+    for p in sample:
+        s = rte.Solver(p, max_rhs=p.nrhs)
+        q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
+        s.solve(q, tol=1e-6)
+        torch.cuda.synchronize()
+        s.close()
+    seq_rate = len(sample) / (time.perf_counter() - t0)
+    sv = rte.Server(budget, slots=8, **opts)
+    # warm-up request
+    sv.wait(sv.submit(reqs[0], reqs[0].q_nodal, tol=1e-6))
+    rng = np.random.default_rng(2)
+    rate = 1.5 * seq_rate
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    t0 = time.perf_counter()
+    ids = []
+    for p, ta in zip(reqs, arrivals):
+        delay = ta - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(sv.submit(p, p.q_nodal, tol=1e-6))
+    lat, iters = [], []
+    for rid in ids:
+        _, info = sv.wait(rid)
+        lat.append(info['latency'])
+        iters.append(info['iterations'])
+    wall = time.perf_counter() - t0
+    sv.close()
+    lat = np.array(lat)
+    return dict(requests=len(reqs), arrival_rate_per_s=rate, hbm_budget_bytes=budget, slots=8,
+                precision='mixed_bf16', p50_latency_s=float(np.percentile(lat, 50)),
+                p99_latency_s=float(np.percentile(lat, 99)), solves_per_s=len(reqs) / wall,
+                sequential_fp64_solves_per_s=seq_rate,
+                sequential_fp64_sample=len(sample), mean_iterations=float(np.mean(iters)))
 
 
 def cpu_baseline(p, budget_s=30.0):

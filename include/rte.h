@@ -48,6 +48,16 @@ extern "C" {
 #define RTE_MIXED_FP32 1    /* inner applies in FP32 (TF32 tensor GEMMs)     */
 #define RTE_MIXED_BF16 2    /* inner applies in FP32, scattering GEMMs BF16  */
 
+/* How the FP64 dense contractions (eigenbasis of (M^- - K^-)^{-1}, U S^+)
+ * are computed: RTE_DGEMM_AUTO picks SIMT in RTE_FP64 mode and SPLIT in the
+ * mixed modes; RTE_DGEMM_SIMT uses FP64 arithmetic units; RTE_DGEMM_SPLIT
+ * cuts the FP64 operands into exact BF16 digit slices whose tensor-core
+ * products are summed in FP64 (about 2^-49 relative to the operand scales
+ * with the default 7 slices). */
+#define RTE_DGEMM_AUTO 0
+#define RTE_DGEMM_SIMT 1
+#define RTE_DGEMM_SPLIT 2
+
 /* How (M^- - K^-)^{-1} is applied inside Apply-E (Algorithm 1, line 2). */
 #define RTE_MK_EIGEN 0      /* exact, in the full eigenbasis of (S^-, M_S^-) */
 #define RTE_MK_PCG 1        /* PCG with the Lemma apply_high_order_pre prec. */
@@ -83,6 +93,8 @@ typedef struct {
     int coarse_maxit;
     int max_iter;           /* outer Richardson iterations                   */
     int max_rhs;            /* workspace is sized for this many RHS          */
+    int dgemm;              /* RTE_DGEMM_AUTO | RTE_DGEMM_SIMT | _SPLIT      */
+    int split_slices;       /* digit slices per operand for RTE_DGEMM_SPLIT  */
 } rte_options;
 
 typedef struct {
@@ -183,6 +195,13 @@ int rte_operator(rte_handle* h, int op, const double* in, double* out,
 int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K,
                   int bf16, int out_bf16, void* stream);
 
+/* The FP64 split GEMM of RTE_DGEMM_SPLIT, exposed for testing and
+ * profiling: C[M x N] = A[M x K] * Bt[N x K]^T, all FP64 row-major device
+ * arrays, with `slices` digit slices per operand (1..10).  Allocates its own
+ * temporaries. */
+int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, int K,
+                    int slices, void* stream);
+
 /* Copies an assembled matrix to host memory (for checks against an
  * independent assembly).  what: 0 S^+ (n_S^+^2), 1 S^- (n_S^-^2),
  * 2 M_S^+ diagonal (n_S^+), 3 M_S^- blocks (n_S^+ x 9), 4 A_1 (n_S^+ x 3),
@@ -199,11 +218,62 @@ int rte_timing_enable(rte_handle* h, int on);
 int rte_timing_read(rte_handle* h, const char** names, double* ms,
                     long long* launches, int cap, int* count);
 
+/* Phase trace of the persistent solver kernels, for profiling: with on != 0
+ * the next E_0 / E_c solves record the time after every grid barrier of
+ * their launch; rte_trace_read copies the intervals (microseconds) of the
+ * most recent launch into us[0..cap) and their number into *count. */
+int rte_trace_enable(rte_handle* h, int on);
+int rte_trace_read(rte_handle* h, double* us, int cap, int* count);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * handles, all threads), for counting launches inside a timed region. */
 long long rte_kernel_launches(void);
 
 void rte_destroy(rte_handle* h);
+
+/* ------------------------------------------------------------------------
+ * Serving and batching (not part of the paper's method).
+ *
+ * A server runs `slots` worker threads, each with its own CUDA stream on the
+ * current device.  Submitted requests (problem + nodal source) are admitted
+ * in arrival order when a slot is free and the estimated device memory of
+ * the admitted requests stays within hbm_budget_bytes (a request larger than
+ * the budget runs alone).  A request runs rte_setup, rte_rhs and rte_solve on
+ * its slot's stream and copies u back to host memory; the device work of
+ * concurrent requests overlaps.  The server copies the problem arrays and
+ * the source at submission; the caller keeps ownership of its buffers.
+ * ------------------------------------------------------------------------ */
+typedef struct rte_server rte_server;
+
+/* Device bytes a solve of this problem with nrhs right-hand sides needs
+ * (an upper estimate used for admission). */
+size_t rte_estimate_bytes(const rte_problem* prob, const rte_options* opts, int nrhs);
+
+int rte_server_create(size_t hbm_budget_bytes, int slots, const rte_options* opts,
+                      rte_server** out);
+
+/* Queues a solve of (E - K^+) u = q with q from the host nodal source
+ * q_nodal (nrhs x n_R^+) to the relative residual tol; *id identifies it. */
+int rte_server_submit(rte_server* sv, const rte_problem* prob, const double* q_nodal,
+                      int nrhs, double tol, long long* id);
+
+/* Waits (timeout_s < 0: without limit) for request id, copies its solution
+ * (nrhs x n_R^+ x n_S^+) into host u (u_len doubles; may be NULL), its
+ * statistics, its latency from submission to completion and its queueing
+ * time.  Returns the request's own status; RTE_ERR_TIMEOUT if it has not
+ * finished in time (the request stays queryable). */
+int rte_server_wait(rte_server* sv, long long id, double timeout_s, double* u, size_t u_len,
+                    rte_stats* stats, double* latency_s, double* queue_s);
+
+/* Finishes the running requests and stops the workers; requests still
+ * queued are dropped. */
+void rte_server_destroy(rte_server* sv);
+
+/* Solves `count` independent problems at once through a temporary server:
+ * q_nodal[i] (host, nrhs[i] x n_R^+), u[i] (host, nrhs[i] x n_R^+ x n_S^+). */
+int rte_solve_batch(const rte_problem* probs, const double* const* q_nodal, const int* nrhs,
+                    double* const* u, int count, double tol, const rte_options* opts,
+                    size_t hbm_budget_bytes, int slots, rte_stats* stats);
 
 /* Message of the calling thread's last error ("" if none). */
 const char* rte_last_error(void);

@@ -16,6 +16,7 @@ __all__ = ['Solver', 'RteError', 'load', 'OPS', 'FP64', 'MIXED_FP32',
 
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 MK_EIGEN, MK_PCG = 0, 1
+DGEMM_AUTO, DGEMM_SIMT, DGEMM_SPLIT = 0, 1, 2
 OPS = dict(A=1, AT=2, KPLUS=3, MK=4, MK_INV=5, MK_PREC=6, E=7, E0_INV=8,
            P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13, E_LO=14, EK_LO=15)
 EXPORTS = dict(Splus=0, Sminus=1, m=2, MSm=3, A1=4, A2=5, omx=6, omy=7,
@@ -47,7 +48,8 @@ class _Options(ctypes.Structure):
                 ('mk_maxit', ctypes.c_int), ('e0_tol', ctypes.c_double),
                 ('e0_maxit', ctypes.c_int), ('coarse_tol', ctypes.c_double),
                 ('coarse_maxit', ctypes.c_int), ('max_iter', ctypes.c_int),
-                ('max_rhs', ctypes.c_int)]
+                ('max_rhs', ctypes.c_int), ('dgemm', ctypes.c_int),
+                ('split_slices', ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -64,7 +66,10 @@ _lib = None
 EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs',
             'rte_apply', 'rte_precond', 'rte_solve', 'rte_operator',
             'rte_export', 'rte_timing_enable', 'rte_timing_read',
-            'rte_kernel_launches', 'rte_gemm_lowp', 'rte_destroy',
+            'rte_kernel_launches', 'rte_gemm_lowp', 'rte_dgemm_split',
+            'rte_trace_enable', 'rte_estimate_bytes', 'rte_server_create',
+            'rte_server_submit', 'rte_server_wait', 'rte_server_destroy', 'rte_solve_batch',
+            'rte_trace_read', 'rte_destroy',
             'rte_last_error']
 
 
@@ -94,13 +99,28 @@ def load(path=LIB_PATH):
                                     ctypes.POINTER(ctypes.c_longlong), I,
                                     ctypes.POINTER(I)]
     lib.rte_gemm_lowp.argtypes = [P, P, P, I, I, I, I, I, P]
+    lib.rte_dgemm_split.argtypes = [P, P, P, I, I, I, I, P]
+    lib.rte_estimate_bytes.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Options), I]
+    lib.rte_estimate_bytes.restype = ctypes.c_size_t
+    lib.rte_server_create.argtypes = [ctypes.c_size_t, I, ctypes.POINTER(_Options),
+                                      ctypes.POINTER(P)]
+    lib.rte_server_submit.argtypes = [P, ctypes.POINTER(_Problem), ctypes.POINTER(D), I, D,
+                                      ctypes.POINTER(ctypes.c_longlong)]
+    lib.rte_server_wait.argtypes = [P, ctypes.c_longlong, D, ctypes.POINTER(D),
+                                    ctypes.c_size_t, ctypes.POINTER(_Stats),
+                                    ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.rte_server_destroy.argtypes = [P]
+    lib.rte_server_destroy.restype = V
+    lib.rte_trace_enable.argtypes = [P, I]
+    lib.rte_trace_read.argtypes = [P, ctypes.POINTER(D), I, ctypes.POINTER(I)]
     lib.rte_kernel_launches.argtypes = []
     lib.rte_kernel_launches.restype = ctypes.c_longlong
     lib.rte_destroy.argtypes = [P]
     lib.rte_destroy.restype = V
     lib.rte_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ('rte_destroy', 'rte_last_error', 'rte_kernel_launches'):
+        if name not in ('rte_destroy', 'rte_last_error', 'rte_kernel_launches',
+                        'rte_estimate_bytes', 'rte_server_destroy'):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -129,6 +149,22 @@ def gemm_lowp(A, Bt, out_bf16=False, stream=None):
     return C
 
 
+def dgemm_split(A, Bt, slices=7, stream=None):
+    """C = A @ Bt.T for float64 CUDA tensors by the exact BF16 digit-slice
+    tensor-core GEMM."""
+    import torch
+    load()
+    A = A.contiguous()
+    Bt = Bt.contiguous()
+    M, K = A.shape
+    N = Bt.shape[0]
+    C = torch.empty((M, N), device=A.device, dtype=torch.float64)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.rte_dgemm_split(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, slices,
+                                ctypes.c_void_p(st.cuda_stream)))
+    return C
+
+
 def _check(rc):
     if rc != 0:
         raise RteError(rc, _lib.rte_last_error().decode())
@@ -147,6 +183,81 @@ def default_options(**kw):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _problem_struct(problem):
+    import numpy as np
+    st = np.ascontiguousarray(problem.sigma_t, dtype=np.float64)
+    ss = np.ascontiguousarray(problem.sigma_s, dtype=np.float64)
+    pr = _Problem(int(problem.m), int(problem.levels),
+                  st.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                  ss.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(problem.g))
+    return pr, (st, ss)
+
+
+def estimate_bytes(problem, nrhs=1, **options):
+    lib = load()
+    pr, keep = _problem_struct(problem)
+    o = default_options(**options)
+    return int(lib.rte_estimate_bytes(ctypes.byref(pr), ctypes.byref(o), nrhs))
+
+
+class Server:
+    """Continuous-batching solve server on the current CUDA device (see
+    rte_server_* in rte.h): requests are admitted in arrival order as worker
+    slots and the HBM budget free up; their device work overlaps."""
+
+    def __init__(self, hbm_budget_bytes, slots=4, **options):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError('librte needs a CUDA device; there is no CPU path')
+        lib = load()
+        self.options = default_options(**options)
+        h = ctypes.c_void_p()
+        _check(lib.rte_server_create(int(hbm_budget_bytes), int(slots),
+                                     ctypes.byref(self.options), ctypes.byref(h)))
+        self._h = h
+        self._shapes = {}
+
+    def submit(self, problem, q_nodal, tol=1e-6):
+        """Queue a solve; q_nodal: host array (nrhs, (m+1)^2).  Returns an id."""
+        import numpy as np
+        q = np.ascontiguousarray(np.atleast_2d(q_nodal), dtype=np.float64)
+        pr, keep = _problem_struct(problem)
+        rid = ctypes.c_longlong()
+        _check(_lib.rte_server_submit(self._h, ctypes.byref(pr),
+                                      q.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      q.shape[0], float(tol), ctypes.byref(rid)))
+        self._shapes[rid.value] = (q.shape[0], (problem.m + 1) ** 2, 4 * 4 ** problem.levels)
+        return rid.value
+
+    def wait(self, rid, timeout=-1.0):
+        """Wait for a request; returns (u, info) with u of shape
+        (nrhs, n_R^+, n_S^+) and info holding stats and latency."""
+        import numpy as np
+        shape = self._shapes.pop(rid)
+        u = np.empty(shape, dtype=np.float64)
+        st = _Stats()
+        lat, que = ctypes.c_double(), ctypes.c_double()
+        rc = _lib.rte_server_wait(self._h, ctypes.c_longlong(rid), float(timeout),
+                                  u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), u.size,
+                                  ctypes.byref(st), ctypes.byref(lat), ctypes.byref(que))
+        if rc == 5:   # still running: keep the shape for the next wait
+            self._shapes[rid] = shape
+        _check(rc)
+        return u, dict(iterations=st.iterations, rel_residual=st.rel_residual,
+                       latency=lat.value, queue=que.value, seconds=st.seconds)
+
+    def close(self):
+        if getattr(self, '_h', None):
+            _lib.rte_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:
@@ -281,6 +392,16 @@ class Solver:
         _check(_lib.rte_timing_read(self._h, names, ms, cnt, cap,
                                     ctypes.byref(n)))
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n.value, cap))}
+
+    def trace(self, on=True):
+        """Record per-barrier phase times of the next persistent solves."""
+        _check(_lib.rte_trace_enable(self._h, int(on)))
+
+    def trace_read(self, cap=65536):
+        buf = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(_lib.rte_trace_read(self._h, buf, cap, ctypes.byref(n)))
+        return list(buf[:min(n.value, cap)])
 
     def close(self):
         if getattr(self, '_h', None):

@@ -12,7 +12,8 @@ SRC = os.path.join(HERE, 'csrc')
 OUT = os.path.join(HERE, '_build')
 LIB = os.path.join(OUT, 'librte.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
-SOURCES = ['setup_host.cpp', 'mg_host.cpp', 'kernels.cu', 'mg.cu', 'tc_gemm.cu', 'rte.cu']
+SOURCES = ['setup_host.cpp', 'mg_host.cpp', 'server.cpp', 'kernels.cu', 'mg.cu', 'tc_gemm.cu',
+           'rte.cu']
 
 
 def nvcc():
@@ -59,7 +60,7 @@ def build(force=False, verbose=False, extra=()):
                 sys.stderr.write(log)
     tmp = LIB + '.tmp'
     cmd = [nvcc(), '-shared', '-o', tmp] + objs + ARCH + [
-        '-L/usr/local/cuda/lib64', '-lcusolver', '-lcudart']
+        '-L/usr/local/cuda/lib64', '-lcusolver', '-lcudart', '-lpthread']
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError('link failed:\n%s%s' % (r.stdout, r.stderr))

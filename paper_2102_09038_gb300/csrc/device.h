@@ -12,6 +12,7 @@ namespace rte {
 // FP32 copies of the operator data used by the mixed-precision paths, and
 // the low-precision GEMM operands (BF16 or FP32 read as TF32), K-major.
 struct DevLow {
+    const float* ell4;         // M_t^+, M_s^+, B_x, B_y in ELL form [4][7][nRp]
     const float* cell_D;       // [nRm][6]
     const float* cell_at;      // [nRm]
     const float* cell_as;      // [nRm]
@@ -31,7 +32,9 @@ struct DevLow {
 
 // Raw device pointers of an assembled system (owned by rte_handle).
 struct DevSystem {
+    int m;                     // mesh: m x m squares
     int nRp, nRm, nSp, nSm, dP, dM, nnz;
+    const double* ell4;        // M_t^+, M_s^+, B_x, B_y in ELL form [4][7][nRp]
     double g, c, gamma;
     // spatial
     const int* cell_nodes;     // [nRm][3]
@@ -69,9 +72,18 @@ struct DevSystem {
     const double* ec_val;
     const double* ec_dinv;     // [nRp][dP][dP]
     DevLow lo;                 // mixed-precision copies (null in FP64 mode)
-    // E_0 level-0 stencil coefficients per direction, [nnz][nSp]
+    // E_0 level-0 stencil coefficients per direction, ELL [7][nRp][nSp]
     const double* e0coef;
     const float* e0coef_f;
+    const double* ec_ell;      // E_c in ELL form [7][nRp][dP][dP]
+    // digit slices of the constant second operands for the split FP64 GEMM
+    int split_S;               // 0: FP64 GEMMs on the FP64 units
+    const void* sl_VmT;        // [S][nSm][nSm] BF16 (+ exponents below)
+    const int* ex_VmT;
+    const void* sl_Vm;
+    const int* ex_Vm;
+    const void* sl_Sp;
+    const int* ex_Sp;
     MGDevice e0mg;             // multigrid of the E_0 direction blocks
     MGDevice ecmg;             // multigrid of E_c
 };
@@ -162,8 +174,11 @@ size_t coarse_cg_work_bytes(const DevSystem& d, int nrhs);
 void coarse_apply(cudaStream_t s, const DevSystem& d, const double* X,
                   double* Y, int nrhs);
 
-// coef[p][k] = sum_s e0s[k][s] sval[slot_s][p] (E_0 direction-block entries)
-void e0_coefficients(cudaStream_t s, const DevSystem& d, double* coef, float* coef_f);
+// coef[dir][i][k] = sum_s e0s[k][s] ell6[s][dir][i]: the E_0 direction-block
+// entries in ELL form (ell6: the six spatial parts K11, K12, K22, B_x, B_y,
+// M_t^+ in ELL form, FP64)
+void e0_coefficients(cudaStream_t s, int nRp, int nSp, const double* ell6, const double* e0s,
+                     double* coef, float* coef_f);
 
 // Assembly of S^+ and S^- by the quadrature rule (setup).
 struct QuadDev {
@@ -175,6 +190,10 @@ void assemble_scattering(cudaStream_t s, int n, double g, const QuadDev& q,
                          double* Sp, double* Sm);
 
 int device_sm_count();
+
+// Phase trace of the persistent solver kernels: when buf is set, block 0
+// records %globaltimer after every grid barrier (cap entries per launch).
+void set_phase_trace(unsigned long long* buf, int cap);
 
 // Count of kernel launches issued by the library (host-side counter).
 void count_launches(long long n);

@@ -103,13 +103,13 @@ __global__ void k_apply_A(int nRm, int nRp, int nSp, int nrhs,
                           const TC* __restrict__ A1,
                           const TC* __restrict__ A2,
                           const TIn* __restrict__ U, TOut* __restrict__ Z) {
-    const size_t total = (size_t)nrhs * nRm * nSp;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % nSp);
-        const size_t rj = e / nSp;
-        const int j = (int)(rj % nRm);
-        const int r = (int)(rj / nRm);
+    const unsigned total = (unsigned)nrhs * nRm * nSp;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int k = (int)(e % (unsigned)nSp);
+        const unsigned rj = e / (unsigned)nSp;
+        const int j = (int)(rj % (unsigned)nRm);
+        const int r = (int)(rj / (unsigned)nRm);
         const TIn* Ur = U + (size_t)r * nRp * nSp;
         TC g1 = 0, g2 = 0;
 #pragma unroll
@@ -142,17 +142,17 @@ __global__ void k_apply_even(int nRm, int nRp, int nSp, int nrhs, int nnz,
                              const T* __restrict__ Zp,
                              const T* __restrict__ X,
                              const T* __restrict__ V, T* __restrict__ Y) {
-    const size_t total = (size_t)nrhs * nRp * nSp;
+    const unsigned total = (unsigned)nrhs * nRp * nSp;
     const T* Mt = sval + (size_t)kMt * nnz;
     const T* Ms = sval + (size_t)kMs * nnz;
     const T* Bx = sval + (size_t)kBx * nnz;
     const T* By = sval + (size_t)kBy * nnz;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % nSp);
-        const size_t ri = e / nSp;
-        const int i = (int)(ri % nRp);
-        const int r = (int)(ri / nRp);
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int k = (int)(e % (unsigned)nSp);
+        const unsigned ri = e / (unsigned)nSp;
+        const int i = (int)(ri % (unsigned)nRp);
+        const int r = (int)(ri / (unsigned)nRp);
         T acc = 0;
         if (flags & 1) {
             const T a1[3] = {A1[3 * k], A1[3 * k + 1], A1[3 * k + 2]};
@@ -187,12 +187,12 @@ __global__ void k_mk_combine(int nRm, int nSp, int nrhs,
                              const double* __restrict__ MSm,
                              const double* __restrict__ Z,
                              const double* __restrict__ G, double* __restrict__ Y) {
-    const size_t total = (size_t)nrhs * nRm * nSp;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % nSp);
-        const size_t rj = e / nSp;
-        const int j = (int)(rj % nRm);
+    const unsigned total = (unsigned)nrhs * nRm * nSp;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int k = (int)(e % (unsigned)nSp);
+        const unsigned rj = e / (unsigned)nSp;
+        const int j = (int)(rj % (unsigned)nRm);
         const size_t base = rj * 3 * nSp + 3 * k;
         const double z[3] = {Z[base], Z[base + 1], Z[base + 2]};
         const double* M = MSm + 9 * k;
@@ -209,12 +209,12 @@ __global__ void k_mk_minv_scale(int nRm, int nSp, int nrhs,
                                 const double* __restrict__ at,
                                 const double* __restrict__ MSm_inv,
                                 const double* __restrict__ B, double* __restrict__ Y) {
-    const size_t total = (size_t)nrhs * nRm * nSp;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % nSp);
-        const size_t rj = e / nSp;
-        const int j = (int)(rj % nRm);
+    const unsigned total = (unsigned)nrhs * nRm * nSp;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int k = (int)(e % (unsigned)nSp);
+        const unsigned rj = e / (unsigned)nSp;
+        const int j = (int)(rj % (unsigned)nRm);
         const size_t base = rj * 3 * nSp + 3 * k;
         const double b[3] = {B[base], B[base + 1], B[base + 2]};
         const double* M = MSm_inv + 9 * k;
@@ -289,10 +289,10 @@ template <typename T>
 __global__ void k_axpby(const T* __restrict__ x, T* __restrict__ y,
                         size_t len, int nrhs, const double* __restrict__ a,
                         double ca, const double* __restrict__ b, double cb) {
-    const size_t total = len * nrhs;
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / len);
+    const unsigned total = (unsigned)(len * nrhs);
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int r = nrhs == 1 ? 0 : (int)(e / (unsigned)len);
         const T av = static_cast<T>(a ? a[r] : ca);
         const T bv = static_cast<T>(b ? b[r] : cb);
         const T yv = bv == T(0) ? T(0) : bv * y[e];
@@ -427,15 +427,16 @@ __global__ void k_symmetrise(int n, double* __restrict__ S) {
     S[(size_t)j * n + i] = v;
 }
 
-__global__ void k_e0_coef(int nnz, int nSp, const double* __restrict__ sval,
+__global__ void k_e0_coef(int nRp, int nSp, const double* __restrict__ ell6,
                           const double* __restrict__ e0s, double* __restrict__ coef,
                           float* __restrict__ coef_f) {
     const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    if (e >= (size_t)nnz * nSp) return;
-    const int p = (int)(e / nSp), k = (int)(e % nSp);
-    const int slots[6] = {kK11, kK12, kK22, kBx, kBy, kMt};
+    const size_t per = (size_t)7 * nRp;
+    if (e >= per * nSp) return;
+    const size_t di = e / nSp;          // dir * nRp + i
+    const int k = (int)(e % nSp);
     double c = 0.0;
-    for (int q = 0; q < 6; ++q) c += e0s[6 * k + q] * sval[(size_t)slots[q] * nnz + p];
+    for (int q = 0; q < 6; ++q) c += e0s[6 * k + q] * ell6[(size_t)q * per + di];
     coef[e] = c;
     if (coef_f) coef_f[e] = (float)c;
 }
@@ -444,6 +445,102 @@ __global__ void k_near_rows(int n, const int* __restrict__ near_ptr, int* __rest
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     for (int p = near_ptr[k]; p < near_ptr[k + 1]; ++p) row[p] = k;
+}
+
+// ------------------------------------------- structured-mesh versions
+// The m x m "/"-mesh: node (x, y) = y (m+1) + x; square (I, J) holds cells
+// 2 (J m + I) (lower: (I,J),(I+1,J),(I+1,J+1)) and 2 (J m + I) + 1 (upper:
+// (I,J),(I+1,J+1),(I,J+1)).  Adjacency is computed, not looked up.
+template <typename TIn, typename TOut, typename TC>
+__global__ void k_apply_A_s(int m, int nSp, int nrhs, const TC* __restrict__ cell_D,
+                            const TC* __restrict__ A1, const TC* __restrict__ A2,
+                            const TIn* __restrict__ U, TOut* __restrict__ Z) {
+    const int nRm = 2 * m * m, nRp = (m + 1) * (m + 1);
+    const unsigned total = (unsigned)nrhs * nRm * nSp;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int k = (int)(e % (unsigned)nSp);
+        const unsigned rj = e / (unsigned)nSp;
+        const int j = (int)(rj % (unsigned)nRm);
+        const int r = (int)(rj / (unsigned)nRm);
+        const int q = j >> 1, I = q % m, J = q / m;
+        const int n00 = J * (m + 1) + I;
+        const int nd[3] = {n00, (j & 1) ? n00 + m + 2 : n00 + 1,
+                           (j & 1) ? n00 + m + 1 : n00 + m + 2};
+        const TIn* Ur = U + (size_t)r * nRp * nSp + k;
+        TC g1 = 0, g2 = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const TC u = static_cast<TC>(Ur[(size_t)nd[a] * nSp]);
+            g1 = fma(cell_D[6 * j + a], u, g1);
+            g2 = fma(cell_D[6 * j + 3 + a], u, g2);
+        }
+        TOut* z = Z + (size_t)rj * (3 * (size_t)nSp) + 3 * k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            z[c] = static_cast<TOut>(A1[3 * k + c] * g1 + A2[3 * k + c] * g2);
+    }
+}
+
+// Y = [A^T Zp] + [M^+ X + R X] - [M_s^+ V] on the structured mesh; ell4 holds
+// M_t^+, M_s^+, B_x, B_y in ELL form [4][7][nRp].
+template <typename T>
+__global__ void k_apply_even_s(int m, int nSp, int nrhs, int flags,
+                               const T* __restrict__ cell_D, const T* __restrict__ A1,
+                               const T* __restrict__ A2, const T* __restrict__ ell4,
+                               const T* __restrict__ mk, const T* __restrict__ omx,
+                               const T* __restrict__ omy, const T* __restrict__ Zp,
+                               const T* __restrict__ X, const T* __restrict__ V,
+                               T* __restrict__ Y) {
+    const int nRp = (m + 1) * (m + 1), nRm = 2 * m * m;
+    const unsigned total = (unsigned)nrhs * nRp * nSp;
+    const int off[7] = {0, 1, -1, m + 1, -(m + 1), m + 2, -(m + 2)};
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int k = (int)(e % (unsigned)nSp);
+        const unsigned ri = e / (unsigned)nSp;
+        const int i = (int)(ri % (unsigned)nRp);
+        const int r = (int)(ri / (unsigned)nRp);
+        const int x = i % (m + 1), y = i / (m + 1);
+        T acc = 0;
+        if (flags & 1) {
+            const T a1[3] = {A1[3 * k], A1[3 * k + 1], A1[3 * k + 2]};
+            const T a2[3] = {A2[3 * k], A2[3 * k + 1], A2[3 * k + 2]};
+            const T* Zr = Zp + (size_t)r * nRm * 3 * nSp + 3 * k;
+            // the six cells around node (x, y) and the node's local index
+            const int cI[6] = {x, x, x - 1, x - 1, x - 1, x};
+            const int cJ[6] = {y, y, y, y - 1, y - 1, y - 1};
+            const int up[6] = {0, 1, 0, 0, 1, 1};
+            const int loc[6] = {0, 0, 1, 2, 1, 2};
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                if (cI[t] < 0 || cJ[t] < 0 || cI[t] >= m || cJ[t] >= m) continue;
+                const int j = 2 * (cJ[t] * m + cI[t]) + up[t];
+                const T* z = Zr + (size_t)j * 3 * nSp;
+                const T z0 = z[0], z1 = z[1], z2 = z[2];
+                const T t1 = a1[0] * z0 + a1[1] * z1 + a1[2] * z2;
+                const T t2 = a2[0] * z0 + a2[1] * z1 + a2[2] * z2;
+                acc += cell_D[6 * j + loc[t]] * t1 + cell_D[6 * j + 3 + loc[t]] * t2;
+            }
+        }
+        if (flags & 6) {
+            const T mkv = mk[k], ox = omx[k], oy = omy[k];
+            const T* Xr = X + (size_t)r * nRp * nSp + k;
+            const T* Vr = V ? V + (size_t)r * nRp * nSp + k : nullptr;
+            const size_t sl = (size_t)7 * nRp;
+#pragma unroll
+            for (int dir = 0; dir < 7; ++dir) {
+                int jn = i + off[dir];
+                jn = jn < 0 ? 0 : (jn >= nRp ? nRp - 1 : jn);
+                const size_t pe = (size_t)dir * nRp + i;
+                if (flags & 2)
+                    acc += (mkv * ell4[pe] + ox * ell4[2 * sl + pe] + oy * ell4[3 * sl + pe]) *
+                           Xr[(size_t)jn * nSp];
+                if (flags & 4) acc -= ell4[sl + pe] * Vr[(size_t)jn * nSp];
+            }
+        }
+        Y[e] = acc;
+    }
 }
 
 }  // namespace
@@ -477,8 +574,8 @@ void gemm_f64(cudaStream_t s, int M, int N, int K, const double* A, int lda,
 void apply_A(cudaStream_t s, const DevSystem& d, const double* U, double* Z, int nrhs) {
     const size_t total = (size_t)nrhs * d.nRm * d.nSp;
     count_launches(1);
-    k_apply_A<double, double, double><<<grid_for(total), kThreads, 0, s>>>(
-        d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes, d.cell_D, d.ang_A1, d.ang_A2, U, Z);
+    k_apply_A_s<double, double, double><<<grid_for(total), kThreads, 0, s>>>(
+        d.m, d.nSp, nrhs, d.cell_D, d.ang_A1, d.ang_A2, U, Z);
 }
 
 void apply_A_lo(cudaStream_t s, const DevSystem& d, const float* U, void* Z, bool bf16,
@@ -486,22 +583,19 @@ void apply_A_lo(cudaStream_t s, const DevSystem& d, const float* U, void* Z, boo
     const size_t total = (size_t)nrhs * d.nRm * d.nSp;
     count_launches(1);
     if (bf16)
-        k_apply_A<float, __nv_bfloat16, float><<<grid_for(total), kThreads, 0, s>>>(
-            d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes, d.lo.cell_D, d.lo.A1, d.lo.A2, U,
-            static_cast<__nv_bfloat16*>(Z));
+        k_apply_A_s<float, __nv_bfloat16, float><<<grid_for(total), kThreads, 0, s>>>(
+            d.m, d.nSp, nrhs, d.lo.cell_D, d.lo.A1, d.lo.A2, U, static_cast<__nv_bfloat16*>(Z));
     else
-        k_apply_A<float, float, float><<<grid_for(total), kThreads, 0, s>>>(
-            d.nRm, d.nRp, d.nSp, nrhs, d.cell_nodes, d.lo.cell_D, d.lo.A1, d.lo.A2, U,
-            static_cast<float*>(Z));
+        k_apply_A_s<float, float, float><<<grid_for(total), kThreads, 0, s>>>(
+            d.m, d.nSp, nrhs, d.lo.cell_D, d.lo.A1, d.lo.A2, U, static_cast<float*>(Z));
 }
 
 void apply_even(cudaStream_t s, const DevSystem& d, const double* Zp, const double* X,
                 const double* V, double* Y, int nrhs, int flags) {
     const size_t total = (size_t)nrhs * d.nRp * d.nSp;
     count_launches(1);
-    k_apply_even<double><<<grid_for(total), kThreads, 0, s>>>(
-        d.nRm, d.nRp, d.nSp, nrhs, d.nnz, flags, d.adj_ptr, d.adj_cell, d.adj_loc,
-        d.cell_D, d.ang_A1, d.ang_A2, d.st_ptr, d.st_col, d.sval, d.ang_m, d.ang_omx,
+    k_apply_even_s<double><<<grid_for(total), kThreads, 0, s>>>(
+        d.m, d.nSp, nrhs, flags, d.cell_D, d.ang_A1, d.ang_A2, d.ell4, d.ang_m, d.ang_omx,
         d.ang_omy, Zp, X, V, Y);
 }
 
@@ -509,9 +603,8 @@ void apply_even_lo(cudaStream_t s, const DevSystem& d, const float* Zp, const fl
                    const float* V, float* Y, int nrhs, int flags) {
     const size_t total = (size_t)nrhs * d.nRp * d.nSp;
     count_launches(1);
-    k_apply_even<float><<<grid_for(total), kThreads, 0, s>>>(
-        d.nRm, d.nRp, d.nSp, nrhs, d.nnz, flags, d.adj_ptr, d.adj_cell, d.adj_loc,
-        d.lo.cell_D, d.lo.A1, d.lo.A2, d.st_ptr, d.st_col, d.lo.sval, d.lo.m, d.lo.omx,
+    k_apply_even_s<float><<<grid_for(total), kThreads, 0, s>>>(
+        d.m, d.nSp, nrhs, flags, d.lo.cell_D, d.lo.A1, d.lo.A2, d.lo.ell4, d.lo.m, d.lo.omx,
         d.lo.omy, Zp, X, V, Y);
 }
 
@@ -596,10 +689,10 @@ void coarse_apply(cudaStream_t s, const DevSystem& d, const double* X, double* Y
                                                         d.st_col, d.ec_val, X, Y);
 }
 
-void e0_coefficients(cudaStream_t s, const DevSystem& d, double* coef, float* coef_f) {
-    const size_t n = (size_t)d.nnz * d.nSp;
-    k_e0_coef<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d.nnz, d.nSp, d.sval, d.e0s, coef,
-                                                         coef_f);
+void e0_coefficients(cudaStream_t s, int nRp, int nSp, const double* ell6, const double* e0s,
+                     double* coef, float* coef_f) {
+    const size_t n = (size_t)7 * nRp * nSp;
+    k_e0_coef<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(nRp, nSp, ell6, e0s, coef, coef_f);
 }
 
 void assemble_scattering(cudaStream_t s, int n, double g, const QuadDev& q, double* Sp,

@@ -3,15 +3,16 @@
 //  * E_0^{-1} (eq. equivalence_bE_bE0): the n_S^+ decoupled direction blocks,
 //    block k = gamma (a11 K11 + a12 K12 + a22 K22) + om^x B_x + om^y B_y +
 //    m_k M_t^+, all (rhs, direction) columns at once, each column stopping
-//    on its own relative residual.  This is the "multigrid" route the paper
-//    names for these anisotropic diffusion blocks (Section 5.5).
+//    on its own relative residual.  Multigrid is the route the paper names for
+//    these anisotropic diffusion blocks (Section 5.5).
 //  * E_c^{-1} (Section 5.4): the coarse Galerkin system, d x d blocks on the
 //    node stencil, one CG per right-hand side.
-// The preconditioner is one symmetric V-cycle in FP32 on the nested meshes
-// (damped Jacobi / block Jacobi smoothing, nu sweeps before and after,
-// restriction P^T, dense inverse on the coarsest level); the CG recurrences
-// run in the solve's precision T with FP64 reductions.  Blocks meet at
-// bounded grid barriers (persist.cuh).
+// The preconditioner is one symmetric V-cycle in FP32 on the nested meshes:
+// damped Jacobi (block Jacobi for E_c) smoothing, nu sweeps before and after,
+// restriction P^T, a dense inverse on the coarsest level.  The CG recurrences
+// run in the solve's precision T with FP64 reductions.  Operators are in the
+// 7-direction ELL form of mg.h with computed neighbour indices; blocks meet
+// at bounded grid barriers (persist.cuh).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,50 +29,89 @@ namespace {
 constexpr float kOmega = 0.7f;          // Jacobi damping
 constexpr int kCoarseSweeps = 30;       // coarsest-level sweeps without a dense inverse
 
+__device__ __forceinline__ int nbr(int i, int dir, int m, int n) {
+    const int off[7] = {0, 1, -1, m + 1, -(m + 1), m + 2, -(m + 2)};
+    const int j = i + off[dir];
+    return j < 0 ? 0 : (j >= n ? n - 1 : j);
+}
+
+// restriction P^T: the (up to) 7 fine nodes that interpolate from coarse node
+// (X, Y); fine mesh mf = 2 mc
+__device__ __forceinline__ int restrict_src(int I, int mc, int q, float& w) {
+    const int dx[7] = {0, 1, -1, 0, 0, 1, -1};
+    const int dy[7] = {0, 0, 0, 1, -1, 1, -1};
+    const int X = I % (mc + 1), Y = I / (mc + 1), mf = 2 * mc;
+    const int x = 2 * X + dx[q], y = 2 * Y + dy[q];
+    if (x < 0 || y < 0 || x > mf || y > mf) {
+        w = 0.f;
+        return 0;
+    }
+    w = q == 0 ? 1.f : 0.5f;
+    return y * (mf + 1) + x;
+}
+
+// prolongation: coarse nodes (and weights) interpolating fine node i
+__device__ __forceinline__ void prolong_src(int i, int mf, int& c0, int& c1, float& w0,
+                                            float& w1) {
+    const int mc = mf / 2, x = i % (mf + 1), y = i / (mf + 1);
+    if (!(x & 1) && !(y & 1)) {
+        c0 = c1 = (y / 2) * (mc + 1) + x / 2;
+        w0 = 1.f;
+        w1 = 0.f;
+    } else if ((x & 1) && !(y & 1)) {
+        c0 = (y / 2) * (mc + 1) + (x - 1) / 2;
+        c1 = c0 + 1;
+        w0 = w1 = 0.5f;
+    } else if (!(x & 1)) {
+        c0 = ((y - 1) / 2) * (mc + 1) + x / 2;
+        c1 = c0 + (mc + 1);
+        w0 = w1 = 0.5f;
+    } else {
+        c0 = ((y - 1) / 2) * (mc + 1) + (x - 1) / 2;
+        c1 = c0 + (mc + 2);
+        w0 = w1 = 0.5f;
+    }
+}
+
+// Grid-stride loop over the items (i, c) = (e / nc, e % nc) of an n x nc
+// array, with the quotient and remainder advanced incrementally (no division
+// inside the loop).  Item counts stay below 2^31.
+#define ITEMS(n, ncv)                                                           \
+    {                                                                            \
+    const unsigned it_nc__ = (unsigned)(ncv);                                    \
+    const unsigned it_total__ = (unsigned)(n) * it_nc__;                         \
+    const unsigned it_stride__ = gridDim.x * blockDim.x;                         \
+    const unsigned it_sq__ = it_stride__ / it_nc__, it_sr__ = it_stride__ % it_nc__; \
+    unsigned e = blockIdx.x * blockDim.x + threadIdx.x;                          \
+    int i = (int)(e / it_nc__), c = (int)(e % it_nc__);                          \
+    for (; e < it_total__; e += it_stride__, i += it_sq__, c += it_sr__,         \
+                           (c >= (int)it_nc__ ? (c -= it_nc__, ++i) : 0))
+
 // ================================================================ E_0 V-cycle
-struct E0Level {
-    int n;
-    const int *ptr, *col, *diag;
-    const float* val;      // [6][nnz] in the order of e0s
-    int nnz;
-    const int *rptr, *ridx, *p0, *p1;
-    const float *rw, *w0, *w1;
-    float *X, *Xt, *B;     // [n][ncols]
-};
-
-__device__ __forceinline__ void e0_load_s(const float* e0s, int k, float* s) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) s[q] = __ldg(e0s + 6 * k + q);
-}
-
-__device__ __forceinline__ float e0_c(const E0Level& L, const float* s, int p) {
-    const float* v = L.val + p;
-    return s[0] * __ldg(v) + s[1] * __ldg(v + L.nnz) + s[2] * __ldg(v + 2 * L.nnz) +
-           s[3] * __ldg(v + 3 * L.nnz) + s[4] * __ldg(v + 4 * L.nnz) +
-           s[5] * __ldg(v + 5 * L.nnz);
-}
-
-// y = A x at item (i, c), and the diagonal coefficient
-__device__ __forceinline__ float e0_apply(const E0Level& L, const float* s, const float* x,
-                                          int i, int c, int ncols, float& dg) {
-    float y = 0.f;
-    for (int p = L.ptr[i]; p < L.ptr[i + 1]; ++p)
-        y += e0_c(L, s, p) * ldg2(x + (size_t)L.col[p] * ncols + c);
-    dg = e0_c(L, s, L.diag[i]);
-    return y;
-}
-
 struct E0MG {
     int L, ncols, nSp, nu;
     bool dense;
-    const float* cinv;     // [nSp][n_c][n_c]
+    const float* cinv;     // [n_c][n_c][nSp]
     const float* e0s;      // [nSp][6]
-    E0Level lev[kMaxMGLevels];
+    MGDeviceLevel lev[kMaxMGLevels];
 };
 
-#define GSTRIDE(e, total)                                                        \
-    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (total); \
-         e += (size_t)gridDim.x * blockDim.x)
+// per-direction coefficient of stencil direction `dir` at node i
+__device__ __forceinline__ float e0_cf(const MGDeviceLevel& L, int nSp, int dir, int i, int k) {
+    return __ldg(L.cdir + ((size_t)dir * L.n + i) * nSp + k);
+}
+
+__device__ __forceinline__ float e0_apply(const MGDeviceLevel& L, int nSp, int k, const float* x,
+                                          int i, int c, int nc, float& dg) {
+    float y = 0.f;
+#pragma unroll
+    for (int dir = 0; dir < 7; ++dir) {
+        const float cf = e0_cf(L, nSp, dir, i, k);
+        y += cf * ldg2(x + (size_t)nbr(i, dir, L.m, L.n) * nc + c);
+        if (dir == 0) dg = cf;
+    }
+    return y;
+}
 
 // One symmetric V-cycle on B_0; returns the buffer holding z on level 0.
 __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
@@ -79,73 +119,75 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
     int cur[kMaxMGLevels];
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
-    // ---- pre-smoothing from zero, residual, restriction
     auto jacobi = [&](int l) -> bool {
-        const E0Level& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         const float* x = buf(l, cur[l]);
         float* xt = buf(l, cur[l] ^ 1);
-        GSTRIDE(e, (size_t)Lv.n * nc) {
-            const int i = (int)(e / nc), c = (int)(e % nc);
-            float s[6];
-            e0_load_s(mg.e0s, c % mg.nSp, s);
+        ITEMS(Lv.n, nc) {
             float dg;
-            const float y = e0_apply(Lv, s, x, i, c, nc, dg);
+            const float y = e0_apply(Lv, mg.nSp, c % mg.nSp, x, i, c, nc, dg);
             xt[e] = ldg2(x + e) + kOmega * (ldg2(Lv.B + e) - y) / dg;
-        }
+        }}
         cur[l] ^= 1;
         return grid_sync(bar);
     };
     auto first = [&](int l) -> bool {
-        const E0Level& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, 0);
-        GSTRIDE(e, (size_t)Lv.n * nc) {
-            const int i = (int)(e / nc), c = (int)(e % nc);
-            float s[6];
-            e0_load_s(mg.e0s, c % mg.nSp, s);
-            x[e] = kOmega * ldg2(Lv.B + e) / e0_c(Lv, s, Lv.diag[i]);
-        }
+        ITEMS(Lv.n, nc) {
+            x[e] = kOmega * ldg2(Lv.B + e) / e0_cf(Lv, mg.nSp, 0, i, c % mg.nSp);
+        }}
         cur[l] = 0;
         return grid_sync(bar);
     };
     for (int l = 0; l + 1 < mg.L; ++l) {
-        const E0Level& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         if (!first(l)) return false;
         for (int k = 1; k < mg.nu; ++k)
             if (!jacobi(l)) return false;
-        // residual into the spare buffer
         const float* x = buf(l, cur[l]);
         float* t = buf(l, cur[l] ^ 1);
-        GSTRIDE(e, (size_t)Lv.n * nc) {
-            const int i = (int)(e / nc), c = (int)(e % nc);
-            float s[6];
-            e0_load_s(mg.e0s, c % mg.nSp, s);
+        ITEMS(Lv.n, nc) {
             float dg;
-            t[e] = ldg2(Lv.B + e) - e0_apply(Lv, s, x, i, c, nc, dg);
-        }
+            t[e] = ldg2(Lv.B + e) - e0_apply(Lv, mg.nSp, c % mg.nSp, x, i, c, nc, dg);
+        }}
         if (!grid_sync(bar)) return false;
-        const E0Level& Cv = mg.lev[l + 1];
-        GSTRIDE(e, (size_t)Cv.n * nc) {
-            const int I = (int)(e / nc), c = (int)(e % nc);
+        const MGDeviceLevel& Cv = mg.lev[l + 1];
+        ITEMS(Cv.n, nc) {
+            const int I = i;
             float acc = 0.f;
-            for (int q = Lv.rptr[I]; q < Lv.rptr[I + 1]; ++q)
-                acc += Lv.rw[q] * ldg2(t + (size_t)Lv.ridx[q] * nc + c);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                float w;
+                const int f = restrict_src(I, Cv.m, q, w);
+                acc += w * ldg2(t + (size_t)f * nc + c);
+            }
             Cv.B[e] = acc;
-        }
+        }}
         if (!grid_sync(bar)) return false;
     }
-    // ---- coarsest level
     {
         const int l = mg.L - 1;
-        const E0Level& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         if (mg.dense) {
             float* x = buf(l, 0);
-            GSTRIDE(e, (size_t)Lv.n * nc) {
-                const int i = (int)(e / nc), c = (int)(e % nc);
-                const float* row = mg.cinv + ((size_t)(c % mg.nSp) * Lv.n + i) * Lv.n;
-                float acc = 0.f;
-                for (int j = 0; j < Lv.n; ++j) acc += __ldg(row + j) * ldg2(Lv.B + (size_t)j * nc + c);
-                x[e] = acc;
-            }
+            ITEMS(Lv.n, nc) {
+                // cinv is [i][j][direction], so a warp's lanes (consecutive
+                // columns) read consecutive words
+                const int k = c % mg.nSp;
+                const float* row = mg.cinv + (size_t)i * Lv.n * mg.nSp + k;
+                const float* bc = Lv.B + c;
+                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                int j = 0;
+                for (; j + 4 <= Lv.n; j += 4) {
+                    a0 += __ldg(row + (size_t)j * mg.nSp) * ldg2(bc + (size_t)j * nc);
+                    a1 += __ldg(row + (size_t)(j + 1) * mg.nSp) * ldg2(bc + (size_t)(j + 1) * nc);
+                    a2 += __ldg(row + (size_t)(j + 2) * mg.nSp) * ldg2(bc + (size_t)(j + 2) * nc);
+                    a3 += __ldg(row + (size_t)(j + 3) * mg.nSp) * ldg2(bc + (size_t)(j + 3) * nc);
+                }
+                for (; j < Lv.n; ++j) a0 += __ldg(row + (size_t)j * mg.nSp) * ldg2(bc + (size_t)j * nc);
+                x[e] = (a0 + a1) + (a2 + a3);
+            }}
             cur[l] = 0;
             if (!grid_sync(bar)) return false;
         } else {
@@ -154,17 +196,17 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
                 if (!jacobi(l)) return false;
         }
     }
-    // ---- prolongation and post-smoothing
     for (int l = mg.L - 2; l >= 0; --l) {
-        const E0Level& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, cur[l]);
         const float* xc = buf(l + 1, cur[l + 1]);
-        GSTRIDE(e, (size_t)Lv.n * nc) {
-            const int i = (int)(e / nc), c = (int)(e % nc);
-            float v = Lv.w0[i] * ldg2(xc + (size_t)Lv.p0[i] * nc + c);
-            if (Lv.p1[i] >= 0) v += Lv.w1[i] * ldg2(xc + (size_t)Lv.p1[i] * nc + c);
-            x[e] = ldg2(x + e) + v;
-        }
+        ITEMS(Lv.n, nc) {
+            int c0, c1;
+            float w0, w1;
+            prolong_src(i, Lv.m, c0, c1, w0, w1);
+            x[e] = ldg2(x + e) + w0 * ldg2(xc + (size_t)c0 * nc + c) +
+                   w1 * ldg2(xc + (size_t)c1 * nc + c);
+        }}
         if (!grid_sync(bar)) return false;
         for (int k = 0; k < mg.nu; ++k)
             if (!jacobi(l)) return false;
@@ -176,11 +218,9 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
 // ================================================================ E_0 PCG
 template <typename T>
 struct E0Args {
-    int nRp, nSp, nrhs, ncols, kTiles, chunks, units, maxit;
+    int nRp, m, nSp, nrhs, ncols, kTiles, chunks, units, maxit;
     double tol2;
-    const int* st_ptr;
-    const int* st_col;
-    const T* coef;      // level-0 coefficients [nnz][nSp] in the CG precision
+    const T* coef;      // level-0 coefficients [7][nRp][nSp] in the CG precision
     const double* B;
     double* X;
     T* R;
@@ -213,14 +253,13 @@ __device__ void col_add(double v, double* sh, double* dst, int col, bool valid) 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_e0_pcg(E0Args<T> a) {
+__global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
     __shared__ double sh[256];
     __shared__ int s_stop;
     const int kx = threadIdx.x & 31, ny = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_stop = 0;
     const int nc = a.ncols;
     float* B0 = a.mg.lev[0].B;
-    // unit u -> (rhs r, direction tile kt, node chunk)
 #define UNIT_LOOP                                                   \
     for (int u = blockIdx.x; u < a.units; u += gridDim.x) {         \
         const int chunk = u % a.chunks;                             \
@@ -282,9 +321,10 @@ __global__ void __launch_bounds__(256) k_e0_pcg(E0Args<T> a) {
                 const T* Pr = a.P + (size_t)r * a.nRp * a.nSp;
                 NODE_LOOP
                     T y = 0;
-                    for (int p = a.st_ptr[i]; p < a.st_ptr[i + 1]; ++p)
-                        y += __ldg(a.coef + (size_t)p * a.nSp + k) *
-                             ldg2(Pr + (size_t)a.st_col[p] * a.nSp + k);
+#pragma unroll
+                    for (int dir = 0; dir < 7; ++dir)
+                        y += __ldg(a.coef + ((size_t)dir * a.nRp + i) * a.nSp + k) *
+                             ldg2(Pr + (size_t)nbr(i, dir, a.m, a.nRp) * a.nSp + k);
                     a.AP[e] = y;
                     ppap += (double)y * (double)ldg2(a.P + e);
                 }
@@ -367,39 +407,36 @@ __global__ void __launch_bounds__(256) k_e0_pcg(E0Args<T> a) {
 }
 
 // ============================================================ E_c V-cycle
-struct EcLevel {
-    int n;
-    const int *ptr, *col;
-    const float* val;      // [nnz][d][d]
-    const float* dinv;     // [n][d][d]
-    const int *rptr, *ridx, *p0, *p1;
-    const float *rw, *w0, *w1;
-    float *X, *Xt, *B;     // [nrhs][n][d]
-};
-
 struct EcMG {
     int L, nrhs, d, nu;
     bool dense;
     const float* cinv;     // [(n_c d)][(n_c d)]
-    EcLevel lev[kMaxMGLevels];
+    MGDeviceLevel lev[kMaxMGLevels];
 };
 
 // warp-level loop over (rhs, node) pairs of a level; lane = mode
 #define WARP_LOOP(nn)                                                              \
-    for (size_t wi = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5;         \
-         wi < (size_t)mg.nrhs * (nn); wi += ((size_t)gridDim.x * blockDim.x) >> 5) { \
-        const int r = (int)(wi / (nn)), i = (int)(wi % (nn));                      \
-        const size_t base = ((size_t)r * (nn) + i) * d;
+    {                                                                              \
+    const unsigned wl_n__ = (unsigned)(nn);                                        \
+    const unsigned wl_stride__ = (gridDim.x * blockDim.x) >> 5;                    \
+    const unsigned wl_sq__ = wl_stride__ / wl_n__, wl_sr__ = wl_stride__ % wl_n__; \
+    unsigned wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;                    \
+    int r = (int)(wi / wl_n__), i = (int)(wi % wl_n__);                            \
+    for (; wi < (unsigned)mg.nrhs * wl_n__; wi += wl_stride__, r += wl_sq__, i += wl_sr__, \
+         (i >= (int)wl_n__ ? (i -= wl_n__, ++r) : 0)) {                            \
+        const size_t base = ((size_t)r * wl_n__ + i) * d;
 
-__device__ __forceinline__ float ec_apply(const EcLevel& L, const float* x, int r, int i, int d,
-                                          int lane) {
+__device__ __forceinline__ float ec_apply(const MGDeviceLevel& L, const float* x, int r, int i,
+                                          int d, int lane) {
     float y = 0.f;
-    if (lane < d)
-        for (int p = L.ptr[i]; p < L.ptr[i + 1]; ++p) {
-            const float* blk = L.val + ((size_t)p * d + lane) * d;
-            const float* xv = x + ((size_t)r * L.n + L.col[p]) * d;
+    const float* xr = x + (size_t)r * L.n * d;
+#pragma unroll
+    for (int dir = 0; dir < 7; ++dir) {
+        const float* xv = xr + (size_t)nbr(i, dir, L.m, L.n) * d;
+        const float* blk = L.val + (((size_t)dir * L.n + i) * d + lane) * d;
+        if (lane < d)
             for (int b = 0; b < d; ++b) y += __ldg(blk + b) * ldg2(xv + b);
-        }
+    }
     return y;
 }
 
@@ -419,7 +456,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
     auto jacobi = [&](int l) -> bool {
-        const EcLevel& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         const float* x = buf(l, cur[l]);
         float* xt = buf(l, cur[l] ^ 1);
         WARP_LOOP(Lv.n)
@@ -427,23 +464,23 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
             const float res = lane < d ? ldg2(Lv.B + base + lane) - y : 0.f;
             const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, res, lane);
             if (lane < d) xt[base + lane] = ldg2(x + base + lane) + kOmega * dx;
-        }
+        }}
         cur[l] ^= 1;
         return grid_sync(bar);
     };
     auto first = [&](int l) -> bool {
-        const EcLevel& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, 0);
         WARP_LOOP(Lv.n)
             const float bv = lane < d ? ldg2(Lv.B + base + lane) : 0.f;
             const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, bv, lane);
             if (lane < d) x[base + lane] = kOmega * dx;
-        }
+        }}
         cur[l] = 0;
         return grid_sync(bar);
     };
     for (int l = 0; l + 1 < mg.L; ++l) {
-        const EcLevel& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         if (!first(l)) return false;
         for (int k = 1; k < mg.nu; ++k)
             if (!jacobi(l)) return false;
@@ -452,33 +489,46 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         WARP_LOOP(Lv.n)
             const float y = ec_apply(Lv, x, r, i, d, lane);
             if (lane < d) t[base + lane] = ldg2(Lv.B + base + lane) - y;
-        }
+        }}
         if (!grid_sync(bar)) return false;
-        const EcLevel& Cv = mg.lev[l + 1];
+        const MGDeviceLevel& Cv = mg.lev[l + 1];
         WARP_LOOP(Cv.n)
             if (lane < d) {
                 float acc = 0.f;
-                for (int q = Lv.rptr[i]; q < Lv.rptr[i + 1]; ++q)
-                    acc += Lv.rw[q] * ldg2(t + ((size_t)r * Lv.n + Lv.ridx[q]) * d + lane);
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    float w;
+                    const int f = restrict_src(i, Cv.m, q, w);
+                    acc += w * ldg2(t + ((size_t)r * Lv.n + f) * d + lane);
+                }
                 Cv.B[base + lane] = acc;
             }
-        }
+        }}
         if (!grid_sync(bar)) return false;
     }
     {
         const int l = mg.L - 1;
-        const EcLevel& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         if (mg.dense) {
             float* x = buf(l, 0);
             const int N = Lv.n * d;
-            WARP_LOOP(Lv.n)
-                if (lane < d) {
-                    const float* row = mg.cinv + (size_t)(i * d + lane) * N;
-                    const float* b = Lv.B + (size_t)r * N;
-                    float acc = 0.f;
-                    for (int j = 0; j < N; ++j) acc += __ldg(row + j) * ldg2(b + j);
-                    x[base + lane] = acc;
+            // one warp per output entry (rhs, row q): lanes stride over the row
+            const unsigned nw = (unsigned)mg.nrhs * N;
+            for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nw;
+                 w += (gridDim.x * blockDim.x) >> 5) {
+                const int r = (int)(w / (unsigned)N), q = (int)(w % (unsigned)N);
+                const float* row = mg.cinv + (size_t)q * N;
+                const float* b = Lv.B + (size_t)r * N;
+                float acc = 0.f, acc2 = 0.f;
+                int j = lane;
+                for (; j + 32 < N; j += 64) {
+                    acc += __ldg(row + j) * ldg2(b + j);
+                    acc2 += __ldg(row + j + 32) * ldg2(b + j + 32);
                 }
+                if (j < N) acc += __ldg(row + j) * ldg2(b + j);
+                acc += acc2;
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) x[(size_t)r * N + q] = acc;
             }
             cur[l] = 0;
             if (!grid_sync(bar)) return false;
@@ -489,17 +539,20 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         }
     }
     for (int l = mg.L - 2; l >= 0; --l) {
-        const EcLevel& Lv = mg.lev[l];
+        const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, cur[l]);
         const float* xc = buf(l + 1, cur[l + 1]);
         const int ncn = mg.lev[l + 1].n;
         WARP_LOOP(Lv.n)
             if (lane < d) {
-                float v = Lv.w0[i] * ldg2(xc + ((size_t)r * ncn + Lv.p0[i]) * d + lane);
-                if (Lv.p1[i] >= 0) v += Lv.w1[i] * ldg2(xc + ((size_t)r * ncn + Lv.p1[i]) * d + lane);
+                int c0, c1;
+                float w0, w1;
+                prolong_src(i, Lv.m, c0, c1, w0, w1);
+                const float v = w0 * ldg2(xc + ((size_t)r * ncn + c0) * d + lane) +
+                                w1 * ldg2(xc + ((size_t)r * ncn + c1) * d + lane);
                 x[base + lane] = ldg2(x + base + lane) + v;
             }
-        }
+        }}
         if (!grid_sync(bar)) return false;
         for (int k = 0; k < mg.nu; ++k)
             if (!jacobi(l)) return false;
@@ -510,11 +563,9 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
 
 // ============================================================== E_c PCG
 struct EcArgs {
-    int nRp, d, nrhs, maxit;
+    int nRp, m, d, nrhs, maxit;
     double tol2;
-    const int* st_ptr;
-    const int* st_col;
-    const double* ec;   // FP64 blocks of E_c
+    const double* ec;   // FP64 E_c in ELL form [7][nRp][d][d]
     const double* B;
     double* X;
     double* R;
@@ -527,12 +578,12 @@ struct EcArgs {
     EcMG mg;
 };
 
-__device__ void rhs_add(double v, double* sh, double* dst, int r) {
+__device__ void rhs_add(double v, double* dst, int r) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(dst + r, v);
 }
 
-__global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
+__global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     __shared__ int s_stop;
     if (threadIdx.x == 0) s_stop = 0;
     const int d = a.d;
@@ -549,8 +600,8 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
             B0[base + lane] = (float)b;
             pbb = b * b;
         }
-        rhs_add(pbb, nullptr, a.bb, r);
-    }
+        rhs_add(pbb, a.bb, r);
+    }}
     if (!grid_sync(a.bar)) return;
     float* z = nullptr;
     if (!ec_vcycle(mg, a.bar, z)) return;
@@ -561,8 +612,8 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
             a.P[base + lane] = zv;
             prz = ldg2(a.R + base + lane) * zv;
         }
-        rhs_add(prz, nullptr, sl(2, 1), r);
-    }
+        rhs_add(prz, sl(2, 1), r);
+    }}
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nrhs; c += gridDim.x * blockDim.x)
         sl(2, 2)[c] = ldg2(a.bb + c);
     if (!grid_sync(a.bar)) return;
@@ -576,10 +627,12 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
             const bool act = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
             if (!act) continue;
             double y = 0.0;
+            const double* Pr = a.P + (size_t)r * a.nRp * d;
             if (lane < d)
-                for (int p = a.st_ptr[i]; p < a.st_ptr[i + 1]; ++p) {
-                    const double* blk = a.ec + ((size_t)p * d + lane) * d;
-                    const double* xv = a.P + ((size_t)r * a.nRp + a.st_col[p]) * d;
+#pragma unroll
+                for (int dir = 0; dir < 7; ++dir) {
+                    const double* blk = a.ec + (((size_t)dir * a.nRp + i) * d + lane) * d;
+                    const double* xv = Pr + (size_t)nbr(i, dir, a.m, a.nRp) * d;
                     for (int b = 0; b < d; ++b) y = fma(__ldg(blk + b), ldg2(xv + b), y);
                 }
             double ppap = 0.0;
@@ -587,8 +640,8 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
                 a.AP[base + lane] = y;
                 ppap = y * ldg2(a.P + base + lane);
             }
-            rhs_add(ppap, nullptr, sl(cur, 0), r);
-        }
+            rhs_add(ppap, sl(cur, 0), r);
+        }}
         if (!grid_sync(a.bar)) return;
         WARP_LOOP(a.nRp)
             const bool act = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
@@ -604,8 +657,8 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
             } else if (lane < d) {
                 B0[base + lane] = 0.f;
             }
-            if (act) rhs_add(prr, nullptr, sl(cur, 2), r);
-        }
+            if (act) rhs_add(prr, sl(cur, 2), r);
+        }}
         if (!grid_sync(a.bar)) return;
         if (!ec_vcycle(mg, a.bar, z)) return;
         WARP_LOOP(a.nRp)
@@ -613,8 +666,8 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
             if (!act) continue;
             double prz = 0.0;
             if (lane < d) prz = ldg2(a.R + base + lane) * (double)ldg2(z + base + lane);
-            rhs_add(prz, nullptr, sl(cur, 1), r);
-        }
+            rhs_add(prz, sl(cur, 1), r);
+        }}
         if (!grid_sync(a.bar)) return;
         WARP_LOOP(a.nRp)
             const bool was = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
@@ -629,7 +682,7 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
             const double rzo = ldg2(sl(prev, 1) + r);
             const double beta = rzo != 0.0 ? ldg2(sl(cur, 1) + r) / rzo : 0.0;
             a.P[base + lane] = (double)ldg2(z + base + lane) + beta * ldg2(a.P + base + lane);
-        }
+        }}
         if (!grid_sync(a.bar)) return;
         if (threadIdx.x == 0) s_stop = 1;
         __syncthreads();
@@ -650,50 +703,36 @@ __global__ void __launch_bounds__(256) k_ec_pcg(EcArgs a) {
 
 __global__ void k_copy_err(const GridBar* bar, SolveStatus* st) { st->timed_out = bar->err; }
 
-int coop_grid(const void* fn, int threads, int cap_blocks) {
+// Blocks per SM of a persistent kernel: as many as fit (the grid barrier
+// requires them all to be resident), at most 4.
+int coop_grid(const void* fn, int threads) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
-    per_sm = std::max(1, std::min(per_sm, 2));
-    return std::max(1, std::min(per_sm * device_sm_count(), cap_blocks));
+    per_sm = std::max(1, std::min(per_sm, 4));
+    return per_sm * device_sm_count();
 }
 
-E0MG e0_mg_view(const MGDevice& m, int ncols, int nSp) {
-    E0MG g{};
+template <typename V>
+V view(const MGDevice& m) {
+    V g{};
     g.L = m.L;
-    g.ncols = ncols;
-    g.nSp = nSp;
     g.nu = m.nu;
     g.dense = m.dense;
     g.cinv = m.cinv;
-    g.e0s = m.e0s;
-    for (int l = 0; l < m.L; ++l) {
-        const MGDeviceLevel& s = m.lev[l];
-        E0Level& t = g.lev[l];
-        t.n = s.n; t.ptr = s.ptr; t.col = s.col; t.diag = s.diag; t.val = s.val; t.nnz = s.nnz;
-        t.rptr = s.rptr; t.ridx = s.ridx; t.p0 = s.p0; t.p1 = s.p1;
-        t.rw = s.rw; t.w0 = s.w0; t.w1 = s.w1;
-        t.X = s.X; t.Xt = s.Xt; t.B = s.B;
-    }
+    for (int l = 0; l < m.L; ++l) g.lev[l] = m.lev[l];
     return g;
 }
 
-EcMG ec_mg_view(const MGDevice& m, int nrhs, int d) {
-    EcMG g{};
-    g.L = m.L;
-    g.nrhs = nrhs;
-    g.d = d;
-    g.nu = m.nu;
-    g.dense = m.dense;
-    g.cinv = m.cinv;
-    for (int l = 0; l < m.L; ++l) {
-        const MGDeviceLevel& s = m.lev[l];
-        EcLevel& t = g.lev[l];
-        t.n = s.n; t.ptr = s.ptr; t.col = s.col; t.val = s.val; t.dinv = s.dinv;
-        t.rptr = s.rptr; t.ridx = s.ridx; t.p0 = s.p0; t.p1 = s.p1;
-        t.rw = s.rw; t.w0 = s.w0; t.w1 = s.w1;
-        t.X = s.X; t.Xt = s.Xt; t.B = s.B;
-    }
-    return g;
+// Optional phase trace of the persistent kernels (set by set_phase_trace).
+unsigned long long* g_trace_buf = nullptr;
+int g_trace_cap = 0;
+
+int init_bar(cudaStream_t s, GridBar* bar) {
+    GridBar h{};
+    h.trace = g_trace_buf;
+    h.cap = g_trace_cap;
+    RTE_CUDA_TRY(cudaMemcpyAsync(bar, &h, sizeof(GridBar), cudaMemcpyHostToDevice, s));
+    return RTE_OK;
 }
 
 template <typename T>
@@ -702,7 +741,8 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
                 SolveStatus* status_dev) {
     if (work_bytes < e0_cg_work_bytes(d, nrhs))
         return fail(RTE_ERR_ARG, "E_0 CG workspace too small");
-    if (nrhs > d.e0mg.cap_cols / d.nSp) return fail(RTE_ERR_ARG, "E_0 multigrid sized for fewer RHS");
+    if (nrhs * d.nSp > d.e0mg.cap_cols)
+        return fail(RTE_ERR_ARG, "E_0 multigrid sized for fewer RHS");
     const size_t n = (size_t)nrhs * d.nRp * d.nSp;
     const int ncols = nrhs * d.nSp;
     char* p = static_cast<char*>(work);
@@ -715,9 +755,10 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     a.bar = carve<GridBar>(p, 1);
     RTE_CUDA_TRY(cudaMemsetAsync(a.acc, 0, 9 * (size_t)ncols * 8, s));
     RTE_CUDA_TRY(cudaMemsetAsync(a.bb, 0, (size_t)ncols * 8, s));
-    RTE_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(GridBar), s));
+    RTE_TRY(init_bar(s, a.bar));
     RTE_CUDA_TRY(cudaMemsetAsync(status_dev, 0, sizeof(SolveStatus), s));
     a.nRp = d.nRp;
+    a.m = d.e0mg.lev[0].m;
     a.nSp = d.nSp;
     a.nrhs = nrhs;
     a.ncols = ncols;
@@ -726,15 +767,16 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     a.units = nrhs * a.kTiles * a.chunks;
     a.maxit = maxit;
     a.tol2 = tol * tol;
-    a.st_ptr = d.st_ptr;
-    a.st_col = d.st_col;
     a.coef = coef;
     a.B = B;
     a.X = X;
     a.status = status_dev;
-    a.mg = e0_mg_view(d.e0mg, ncols, d.nSp);
+    a.mg = view<E0MG>(d.e0mg);
+    a.mg.ncols = ncols;
+    a.mg.nSp = d.nSp;
+    a.mg.e0s = d.e0mg.e0s;
     const void* fn = (const void*)k_e0_pcg<T>;
-    const int grid = coop_grid(fn, 256, 1 << 20);
+    const int grid = coop_grid(fn, 256);
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, s));
     k_copy_err<<<1, 1, 0, s>>>(a.bar, status_dev);
@@ -743,6 +785,11 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
 }
 
 }  // namespace
+
+void set_phase_trace(unsigned long long* buf, int cap) {
+    g_trace_buf = buf;
+    g_trace_cap = cap;
+}
 
 size_t e0_cg_work_bytes(const DevSystem& d, int nrhs) {
     const size_t n = (size_t)nrhs * d.nRp * d.nSp;
@@ -786,22 +833,23 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     a.bar = carve<GridBar>(p, 1);
     RTE_CUDA_TRY(cudaMemsetAsync(a.acc, 0, 9 * (size_t)nrhs * 8, s));
     RTE_CUDA_TRY(cudaMemsetAsync(a.bb, 0, (size_t)nrhs * 8, s));
-    RTE_CUDA_TRY(cudaMemsetAsync(a.bar, 0, sizeof(GridBar), s));
+    RTE_TRY(init_bar(s, a.bar));
     RTE_CUDA_TRY(cudaMemsetAsync(status_dev, 0, sizeof(SolveStatus), s));
     a.nRp = d.nRp;
+    a.m = d.ecmg.lev[0].m;
     a.d = d.dP;
     a.nrhs = nrhs;
     a.maxit = maxit;
     a.tol2 = tol * tol;
-    a.st_ptr = d.st_ptr;
-    a.st_col = d.st_col;
-    a.ec = d.ec_val;
+    a.ec = d.ec_ell;
     a.B = B;
     a.X = X;
     a.status = status_dev;
-    a.mg = ec_mg_view(d.ecmg, nrhs, d.dP);
+    a.mg = view<EcMG>(d.ecmg);
+    a.mg.nrhs = nrhs;
+    a.mg.d = d.dP;
     const void* fn = (const void*)k_ec_pcg;
-    const int grid = coop_grid(fn, 256, 1 << 20);
+    const int grid = coop_grid(fn, 256);
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, s));
     k_copy_err<<<1, 1, 0, s>>>(a.bar, status_dev);

@@ -1,4 +1,10 @@
 // Device-side multigrid hierarchy shared by the E_0 and E_c solvers.
+//
+// Every level is the uniform (m+1) x (m+1) node grid of an m x m "/"-mesh.
+// Operators are stored in ELL form over the 7 stencil directions
+//   0: self, 1: +x, 2: -x, 3: +y, 4: -y, 5: +x+y, 6: -x-y
+// (zero coefficients where a neighbour does not exist), so neighbour,
+// restriction and prolongation indices are computed, not looked up.
 #pragma once
 
 namespace rte {
@@ -6,12 +12,10 @@ namespace rte {
 constexpr int kMaxMGLevels = 14;
 
 struct MGDeviceLevel {
-    int n = 0, nnz = 0;
-    const int *ptr = nullptr, *col = nullptr, *diag = nullptr;
-    const float* val = nullptr;    // E_0: [6][nnz]; E_c: [nnz][d][d]
+    int m = 0, n = 0;
+    const float* val = nullptr;    // E_0: [6][7][n]; E_c: [7][n][d][d]
     const float* dinv = nullptr;   // E_c: [n][d][d] inverse diagonal blocks
-    const int *rptr = nullptr, *ridx = nullptr, *p0 = nullptr, *p1 = nullptr;
-    const float *rw = nullptr, *w0 = nullptr, *w1 = nullptr;
+    const float* cdir = nullptr;   // E_0: per-direction coefficients [7][n][nSp]
     float *X = nullptr, *Xt = nullptr, *B = nullptr;   // work vectors
 };
 

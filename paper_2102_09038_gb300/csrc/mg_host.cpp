@@ -152,7 +152,7 @@ int build_hierarchy(int m, const Stencil& fine, const std::vector<double>& vals0
     while (true) {
         MGHostLevel& f = out.levels.back();
         const int nf = (f.m + 1) * (f.m + 1);
-        if (f.m % 2 != 0 || f.m < 4 || nf <= 25) break;
+        if (f.m % 2 != 0 || f.m < 4 || nf <= max_coarse_nodes) break;
         MGHostLevel c;
         c.m = f.m / 2;
         c.st = stencil_of_square(c.m);
@@ -186,14 +186,12 @@ int build_hierarchy(int m, const Stencil& fine, const std::vector<double>& vals0
     return RTE_OK;
 }
 
-int coarse_dense_inverse(const MGHostLevel& L, const std::vector<double>& weights, int slots,
-                         int bs, std::vector<float>& inv) {
-    // dense matrix sum_s weights[s] * vals[s] (bs x bs blocks) on the level's
-    // stencil, inverted
+void coarse_dense_matrix(const MGHostLevel& L, const std::vector<double>& weights, int slots,
+                         int bs, std::vector<double>& A) {
     const int n = (L.m + 1) * (L.m + 1);
     const int N = n * bs;
     const size_t nnz = L.st.col.size(), bb = (size_t)bs * bs;
-    std::vector<double> A((size_t)N * N, 0.0);
+    A.assign((size_t)N * N, 0.0);
     for (int i = 0; i < n; ++i)
         for (int q = L.st.ptr[i]; q < L.st.ptr[i + 1]; ++q) {
             const int j = L.st.col[q];
@@ -206,9 +204,6 @@ int coarse_dense_inverse(const MGHostLevel& L, const std::vector<double>& weight
                         A[(size_t)(i * bs + a) * N + j * bs + b] += w * v[a * bs + b];
             }
         }
-    if (!invert(N, A)) return fail(RTE_ERR_ARG, "singular coarsest multigrid matrix");
-    inv.assign(A.begin(), A.end());
-    return RTE_OK;
 }
 
 int block_diag_inverse(const MGHostLevel& L, int bs, std::vector<float>& dinv) {
@@ -221,6 +216,30 @@ int block_diag_inverse(const MGHostLevel& L, int bs, std::vector<float>& dinv) {
         if (!invert(bs, A)) return fail(RTE_ERR_ARG, "singular multigrid diagonal block");
         for (size_t t = 0; t < bb; ++t) dinv[(size_t)i * bb + t] = (float)A[t];
     }
+    return RTE_OK;
+}
+
+int to_ell(const MGHostLevel& L, int slots, int bs, std::vector<double>& out) {
+    const int m = L.m, n = (m + 1) * (m + 1);
+    const size_t nnz = L.st.col.size(), bb = (size_t)bs * bs;
+    out.assign((size_t)slots * 7 * n * bb, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int q = L.st.ptr[i]; q < L.st.ptr[i + 1]; ++q) {
+            const int off = L.st.col[q] - i;
+            int dir = -1;
+            if (off == 0) dir = 0;
+            else if (off == 1) dir = 1;
+            else if (off == -1) dir = 2;
+            else if (off == m + 1) dir = 3;
+            else if (off == -(m + 1)) dir = 4;
+            else if (off == m + 2) dir = 5;
+            else if (off == -(m + 2)) dir = 6;
+            if (dir < 0) return fail(RTE_ERR_ARG, "stencil entry outside the 7-point pattern");
+            for (int s = 0; s < slots; ++s)
+                for (size_t t = 0; t < bb; ++t)
+                    out[(((size_t)s * 7 + dir) * n + i) * bb + t] =
+                        L.vals[((size_t)s * nnz + q) * bb + t];
+        }
     return RTE_OK;
 }
 

@@ -32,11 +32,17 @@ Stencil stencil_of_square(int m);
 int build_hierarchy(int m, const Stencil& fine, const std::vector<double>& vals0, int slots,
                     int bs, int max_coarse_nodes, MGHost& out);
 
-// Inverse of sum_s weights[s] vals[s] on level L (dense, (n bs)^2 floats).
-int coarse_dense_inverse(const MGHostLevel& L, const std::vector<double>& weights, int slots,
-                         int bs, std::vector<float>& inv);
+// Dense matrix sum_s weights[s] vals[s] on level L ((n bs)^2 doubles,
+// row-major); weights empty means all ones.
+void coarse_dense_matrix(const MGHostLevel& L, const std::vector<double>& weights, int slots,
+                         int bs, std::vector<double>& A);
 
 // Inverses of the diagonal bs x bs blocks (slot 0) of level L.
 int block_diag_inverse(const MGHostLevel& L, int bs, std::vector<float>& dinv);
+
+// The 7 stencil directions of the "/"-mesh: self, +x, -x, +y, -y, +x+y, -x-y.
+// ELL form of slot values on a level: out[s][dir][node][bs][bs] (zero where
+// the neighbour does not exist).  Fails if an entry is not one of the 7.
+int to_ell(const MGHostLevel& L, int slots, int bs, std::vector<double>& out);
 
 }  // namespace rte

@@ -12,6 +12,9 @@ struct GridBar {
     unsigned count;
     unsigned gen;
     int err;
+    int n;                       // trace entries written
+    unsigned long long* trace;   // optional: %globaltimer after each barrier
+    int cap;
     int pad;
 };
 
@@ -45,6 +48,11 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb) {
             }
         }
         __threadfence();
+        if (blockIdx.x == 0 && gb->trace && gb->n < gb->cap) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            gb->trace[gb->n++] = t;
+        }
     }
     __syncthreads();
     return *((volatile int*)&gb->err) == 0;

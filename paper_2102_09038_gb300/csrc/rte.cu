@@ -52,6 +52,7 @@ struct rte_handle {
     int cap_rhs = 0;
     double *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr;   // odd
     double *z5 = nullptr, *z6 = nullptr, *z7 = nullptr, *zsk = nullptr;  // PCG route
+    void* slices = nullptr;                                             // split GEMM operand
     double *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr, *e5 = nullptr,
            *e6 = nullptr, *e7 = nullptr, *e8 = nullptr;                     // even
     double *c1 = nullptr, *c2 = nullptr;                                    // coarse
@@ -66,6 +67,7 @@ struct rte_handle {
     void* cowork = nullptr;
     size_t cobytes = 0;
     SolveStatus* status = nullptr;
+    unsigned long long* trace = nullptr;   // phase trace buffer (profiling)
     // statistics of the last inner solves
     int e0_iters = 0, co_iters = 0, mk_iters = 0;
     // timing
@@ -195,6 +197,64 @@ int sym_eig(rte_handle* h, std::vector<double>& C, std::vector<double>& w, int n
     return rc;
 }
 
+// Inverses of `count` SPD n x n matrices (row-major, consecutive in A) by
+// Cholesky on the device (cusolverDnDpotrf / potrs against the identity,
+// setup only); written to inv as FP32.
+int spd_inverse_batch(rte_handle* h, int n, int count, const std::vector<double>& A,
+                      std::vector<float>& inv) {
+    cusolverDnHandle_t cs = nullptr;
+    if (cusolverDnCreate(&cs) != CUSOLVER_STATUS_SUCCESS)
+        return fail(RTE_ERR_CUDA, "cusolverDnCreate failed");
+    cusolverDnSetStream(cs, h->stream);
+    const size_t nn = (size_t)n * n;
+    double *dA = nullptr, *dB = nullptr, *dWork = nullptr;
+    int* dInfo = nullptr;
+    int rc = RTE_OK, lwork = 0;
+    std::vector<double> I(nn, 0.0), out(nn);
+    for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
+    inv.resize(nn * count);
+    if (cudaMalloc(&dA, nn * 8) != cudaSuccess || cudaMalloc(&dB, nn * 8) != cudaSuccess ||
+        cudaMalloc(&dInfo, sizeof(int)) != cudaSuccess)
+        rc = fail(RTE_ERR_NOMEM, "coarse inverse allocation failed");
+    if (rc == RTE_OK &&
+        cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, n, dA, n, &lwork) !=
+            CUSOLVER_STATUS_SUCCESS)
+        rc = fail(RTE_ERR_CUDA, "potrf_bufferSize failed");
+    if (rc == RTE_OK && cudaMalloc(&dWork, sizeof(double) * std::max(lwork, 1)) != cudaSuccess)
+        rc = fail(RTE_ERR_NOMEM, "coarse inverse workspace allocation failed");
+    for (int b = 0; b < count && rc == RTE_OK; ++b) {
+        // symmetric: the row-major matrix is its own column-major transpose
+        cudaMemcpyAsync(dA, A.data() + nn * b, nn * 8, cudaMemcpyHostToDevice, h->stream);
+        cudaMemcpyAsync(dB, I.data(), nn * 8, cudaMemcpyHostToDevice, h->stream);
+        int info = 0;
+        if (cusolverDnDpotrf(cs, CUBLAS_FILL_MODE_LOWER, n, dA, n, dWork, lwork, dInfo) !=
+                CUSOLVER_STATUS_SUCCESS ||
+            cudaMemcpyAsync(&info, dInfo, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess || info != 0) {
+            rc = fail(RTE_ERR_ARG, "coarsest multigrid matrix is not positive definite");
+            break;
+        }
+        if (cusolverDnDpotrs(cs, CUBLAS_FILL_MODE_LOWER, n, n, dA, n, dB, n, dInfo) !=
+            CUSOLVER_STATUS_SUCCESS) {
+            rc = fail(RTE_ERR_CUDA, "potrs failed");
+            break;
+        }
+        cudaMemcpyAsync(out.data(), dB, nn * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            rc = fail(RTE_ERR_CUDA, "coarse inverse synchronisation failed");
+            break;
+        }
+        for (size_t t = 0; t < nn; ++t) inv[nn * b + t] = (float)out[t];
+    }
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dWork);
+    cudaFree(dInfo);
+    cusolverDnDestroy(cs);
+    return rc;
+}
+
 bool chol_inv_sym(int d, const double* A, double* Ainv) {
     // Gauss-Jordan inverse with partial pivoting of a small d x d matrix
     std::vector<double> M(A, A + d * d), I(d * d, 0.0);
@@ -256,8 +316,8 @@ void inv_lower3(const double* L, double* Li) {
     }
 }
 
-// Uploads a host multigrid hierarchy; work vectors hold cols columns of bs
-// values per node.
+// Uploads a host multigrid hierarchy in ELL form; work vectors hold cols
+// columns of bs values per node.
 int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv,
               MGDevice& out) {
     out.L = (int)mh.levels.size();
@@ -268,25 +328,15 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
     for (int l = 0; l < out.L; ++l) {
         const MGHostLevel& L = mh.levels[l];
         MGDeviceLevel& D = out.lev[l];
+        D.m = L.m;
         D.n = (L.m + 1) * (L.m + 1);
-        D.nnz = (int)L.st.col.size();
-        RTE_TRY(upload(h, &D.ptr, L.st.ptr));
-        RTE_TRY(upload(h, &D.col, L.st.col));
-        RTE_TRY(upload(h, &D.diag, L.st.diag));
-        RTE_TRY(upload(h, &D.val, std::vector<float>(L.vals.begin(), L.vals.end())));
+        std::vector<double> ell;
+        RTE_TRY(to_ell(L, mh.slots, bs, ell));
+        RTE_TRY(upload(h, &D.val, std::vector<float>(ell.begin(), ell.end())));
         if (block_dinv) {
             std::vector<float> di;
             RTE_TRY(block_diag_inverse(L, bs, di));
             RTE_TRY(upload(h, &D.dinv, di));
-        }
-        if (l + 1 < out.L) {
-            RTE_TRY(upload(h, &D.rptr, L.rptr));
-            RTE_TRY(upload(h, &D.ridx, L.ridx));
-            RTE_TRY(upload(h, &D.rw, L.rw));
-            RTE_TRY(upload(h, &D.p0, L.p0));
-            RTE_TRY(upload(h, &D.p1, L.p1));
-            RTE_TRY(upload(h, &D.w0, L.w0));
-            RTE_TRY(upload(h, &D.w1, L.w1));
         }
         const size_t nv = (size_t)D.n * cols * bs;
         RTE_TRY(dalloc(h, &D.X, nv));
@@ -296,8 +346,9 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
     return RTE_OK;
 }
 
-// Coarsest-level inverses no larger than this many nodes are formed densely.
-constexpr int kDenseCoarseNodes = 256;
+// Coarsening stops at a level of at most this many nodes, which is then
+// solved with a dense inverse.
+constexpr int kDenseCoarseNodes = 300;
 
 int setup_multigrid(rte_handle* h, const HostSystem& hs) {
     DevSystem& d = h->d;
@@ -313,23 +364,50 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         MGHost mh;
         RTE_TRY(build_hierarchy(hs.m, hs.st, v, 6, 1, kDenseCoarseNodes, mh));
         RTE_TRY(upload_mg(h, mh, cap * hs.nSp, 1, false, d.e0mg));
+        // per-direction FP32 coefficients of every level: cdir[dir][i][k]
+        for (int l = 0; l < d.e0mg.L; ++l) {
+            std::vector<double> ell;
+            RTE_TRY(to_ell(mh.levels[l], 6, 1, ell));
+            const size_t nl = (size_t)(mh.levels[l].m + 1) * (mh.levels[l].m + 1);
+            std::vector<float> cd((size_t)7 * nl * hs.nSp);
+            for (size_t di = 0; di < 7 * nl; ++di)
+                for (int k = 0; k < hs.nSp; ++k) {
+                    double c = 0.0;
+                    for (int q = 0; q < 6; ++q) c += hs.e0s[6 * k + q] * ell[(size_t)q * 7 * nl + di];
+                    cd[di * hs.nSp + k] = (float)c;
+                }
+            RTE_TRY(upload(h, &d.e0mg.lev[l].cdir, cd));
+        }
         const float* e0f = nullptr;
         RTE_TRY(upload(h, &e0f, std::vector<float>(hs.e0s.begin(), hs.e0s.end())));
         d.e0mg.e0s = e0f;
         if (d.e0mg.dense) {
-            std::vector<float> all, one;
+            const int nc = (mh.levels.back().m + 1) * (mh.levels.back().m + 1);
+            std::vector<double> all((size_t)nc * nc * hs.nSp), one;
             for (int k = 0; k < hs.nSp; ++k) {
                 std::vector<double> w(hs.e0s.begin() + 6 * k, hs.e0s.begin() + 6 * k + 6);
-                RTE_TRY(coarse_dense_inverse(mh.levels.back(), w, 6, 1, one));
-                all.insert(all.end(), one.begin(), one.end());
+                coarse_dense_matrix(mh.levels.back(), w, 6, 1, one);
+                std::copy(one.begin(), one.end(), all.begin() + (size_t)nc * nc * k);
             }
-            RTE_TRY(upload(h, &d.e0mg.cinv, all));
+            std::vector<float> inv;
+            RTE_TRY(spd_inverse_batch(h, nc, hs.nSp, all, inv));
+            // [k][i][j] -> [i][j][k] (coalesced over directions on the device)
+            std::vector<float> tr(inv.size());
+            const size_t nn = (size_t)nc * nc;
+            for (int k = 0; k < hs.nSp; ++k)
+                for (size_t ij = 0; ij < nn; ++ij) tr[ij * hs.nSp + k] = inv[k * nn + ij];
+            RTE_TRY(upload(h, &d.e0mg.cinv, tr));
         }
+        // level-0 operator of the CG in ELL form, per direction
+        std::vector<double> ell6;
+        RTE_TRY(to_ell(mh.levels[0], 6, 1, ell6));
+        const double* dell = nullptr;
+        RTE_TRY(upload(h, &dell, ell6));
         double* c = nullptr;
         float* cf = nullptr;
-        RTE_TRY(dalloc(h, &c, nnz * hs.nSp));
-        if (h->mixed) RTE_TRY(dalloc(h, &cf, nnz * hs.nSp));
-        e0_coefficients(h->stream, d, c, cf);
+        RTE_TRY(dalloc(h, &c, (size_t)7 * hs.nRp * hs.nSp));
+        if (h->mixed) RTE_TRY(dalloc(h, &cf, (size_t)7 * hs.nRp * hs.nSp));
+        e0_coefficients(h->stream, hs.nRp, hs.nSp, dell, d.e0s, c, cf);
         d.e0coef = c;
         d.e0coef_f = cf;
     }
@@ -339,10 +417,16 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         RTE_TRY(build_hierarchy(hs.m, hs.st, h->h_ec, 1, d.dP, kDenseCoarseNodes, mh));
         RTE_TRY(upload_mg(h, mh, cap, d.dP, true, d.ecmg));
         if (d.ecmg.dense) {
+            std::vector<double> A;
+            coarse_dense_matrix(mh.levels.back(), {}, 1, d.dP, A);
             std::vector<float> inv;
-            RTE_TRY(coarse_dense_inverse(mh.levels.back(), {}, 1, d.dP, inv));
+            const int N = (mh.levels.back().m + 1) * (mh.levels.back().m + 1) * d.dP;
+            RTE_TRY(spd_inverse_batch(h, N, 1, A, inv));
             RTE_TRY(upload(h, &d.ecmg.cinv, inv));
         }
+        std::vector<double> ell;
+        RTE_TRY(to_ell(mh.levels[0], 1, d.dP, ell));
+        RTE_TRY(upload(h, &d.ec_ell, ell));
     }
     return RTE_OK;
 }
@@ -368,6 +452,13 @@ int alloc_workspace(rte_handle* h, int nrhs) {
         RTE_TRY(dalloc(h, &h->z7, no));
     }
     RTE_TRY(dalloc(h, &h->zsk, (size_t)nrhs * d.nRm * d.dM));
+    if (d.split_S > 0) {
+        const size_t b = std::max(ozaki_slice_bytes(nrhs * d.nRm, d.nSm, d.split_S),
+                                  ozaki_slice_bytes(nrhs * d.nRp, d.nSp, d.split_S));
+        char* p = nullptr;
+        RTE_TRY(dalloc(h, &p, b));
+        h->slices = p;
+    }
     double** ev[] = {&h->e1, &h->e2, &h->e3, &h->e4, &h->e5, &h->e6, &h->e7, &h->e8};
     for (auto p : ev) RTE_TRY(dalloc(h, p, ne));
     RTE_TRY(dalloc(h, &h->c1, nc));
@@ -406,6 +497,20 @@ int alloc_workspace(rte_handle* h, int nrhs) {
 int mk_inv_eigen(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
     const DevSystem& d = h->d;
     const int rows = nrhs * d.nRm;
+    if (d.split_S > 0) {
+        int* ea = nullptr;
+        {
+            Scope sc(h, "dgemm_split_mk1");
+            RTE_TRY(ozaki_split(h->stream, Z1, rows, d.nSm, d.split_S, h->slices, &ea));
+            RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_VmT, d.ex_VmT, d.nSm, d.nSm,
+                               d.split_S, h->z4, d.nSm, 1, d.cell_at, d.cell_as, d.lamM, d.nRm));
+        }
+        Scope sc(h, "dgemm_split_mk2");
+        RTE_TRY(ozaki_split(h->stream, h->z4, rows, d.nSm, d.split_S, h->slices, &ea));
+        RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_Vm, d.ex_Vm, d.nSm, d.nSm,
+                           d.split_S, Z2, d.nSm, 0, nullptr, nullptr, nullptr, 1));
+        return RTE_OK;
+    }
     {
         Scope sc(h, "gemm_mk_eig1");
         gemm_f64(h->stream, rows, d.nSm, d.nSm, Z1, d.nSm, d.Vm, d.nSm, h->z4, d.nSm, 1.0,
@@ -521,9 +626,17 @@ int apply_E(rte_handle* h, const double* x, double* y, int nrhs, bool with_k) {
     double* V = nullptr;
     if (with_k) {
         V = h->e8;
-        Scope sc(h, "gemm_kplus");
-        gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.nSp, x, d.nSp, d.Sp, d.nSp, V, d.nSp, 1.0,
-                 0.0, 0, nullptr, nullptr, nullptr, 1);
+        if (d.split_S > 0) {
+            Scope sc(h, "dgemm_split_kplus");
+            int* ea = nullptr;
+            RTE_TRY(ozaki_split(h->stream, x, nrhs * d.nRp, d.nSp, d.split_S, h->slices, &ea));
+            RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRp, d.sl_Sp, d.ex_Sp, d.nSp,
+                               d.nSp, d.split_S, V, d.nSp, 0, nullptr, nullptr, nullptr, 1));
+        } else {
+            Scope sc(h, "gemm_kplus");
+            gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.nSp, x, d.nSp, d.Sp, d.nSp, V, d.nSp, 1.0,
+                     0.0, 0, nullptr, nullptr, nullptr, 1);
+        }
     }
     Scope sc(h, "apply_even");
     apply_even(h->stream, d, h->z2, x, V, y, nrhs, with_k ? 7 : 3);
@@ -702,12 +815,14 @@ int rte_default_options(rte_options* o) {
     o->mk_route = RTE_MK_EIGEN;
     o->mk_tol = 1e-12;
     o->mk_maxit = 500;
-    o->e0_tol = 1e-12;
+    o->e0_tol = 0.0;          // 0: per precision (1e-12 FP64, 1e-2 mixed)
     o->e0_maxit = 20000;
-    o->coarse_tol = 1e-12;
+    o->coarse_tol = 0.0;      // 0: per precision (1e-12 FP64, 1e-4 mixed)
     o->coarse_maxit = 20000;
     o->max_iter = 200;
     o->max_rhs = 1;
+    o->dgemm = RTE_DGEMM_AUTO;
+    o->split_slices = 7;
     return RTE_OK;
 }
 
@@ -725,6 +840,12 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         return fail(RTE_ERR_ARG, "unknown precision mode");
     if (o.precision != RTE_FP64 && o.mk_route != RTE_MK_EIGEN)
         return fail(RTE_ERR_ARG, "mixed precision uses the eigenbasis route for (M-K)^-1");
+    // inner tolerances left at 0 follow the precision mode: the plain FP64
+    // method solves E_0 and E_c to 1e-12; under the mixed modes' FP64 outer
+    // residual (iterative refinement) loose inner solves cost no outer
+    // iterations
+    if (!(o.e0_tol > 0)) o.e0_tol = o.precision == RTE_FP64 ? 1e-12 : 1e-2;
+    if (!(o.coarse_tol > 0)) o.coarse_tol = o.precision == RTE_FP64 ? 1e-12 : 1e-4;
     HostSystem hs;
     RTE_TRY(build_host_system(*prob, o, hs));
     rte_handle* h = new rte_handle();
@@ -735,6 +856,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         return rc;
     };
     DevSystem& d = h->d;
+    d.m = hs.m;
     d.nRp = hs.nRp; d.nRm = hs.nRm; d.nSp = hs.nSp; d.nSm = hs.nSm;
     d.dP = hs.dP; d.dM = hs.dM; d.nnz = (int)hs.st.col.size();
     d.g = hs.g; d.c = hs.c; d.gamma = hs.gamma;
@@ -751,6 +873,21 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     UP(st_col, hs.st.col);
     UP(st_diag, hs.st.diag);
     UP(sval, hs.sval);
+    std::vector<double> ell4;
+    {
+        MGHostLevel L;
+        L.m = hs.m;
+        L.st = hs.st;
+        const size_t nnz = hs.st.col.size();
+        const int slots[4] = {kMt, kMs, kBx, kBy};
+        L.vals.resize(4 * nnz);
+        for (int q = 0; q < 4; ++q)
+            std::copy(hs.sval.begin() + (size_t)slots[q] * nnz,
+                      hs.sval.begin() + (size_t)(slots[q] + 1) * nnz, L.vals.begin() + q * nnz);
+        rc = to_ell(L, 4, 1, ell4);
+        if (rc) return bail(rc);
+    }
+    UP(ell4, ell4);
     UP(ang_m, hs.m_);
     UP(ang_omx, hs.omx);
     UP(ang_omy, hs.omy);
@@ -978,6 +1115,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
             return std::vector<float>(v.begin(), v.end());
         };
 #define UPF(dst, src) do { rc = upload(h, &lo.dst, tof(src)); if (rc) return bail(rc); } while (0)
+        UPF(ell4, ell4);
         UPF(cell_D, hs.cell_D);
         UPF(cell_at, hs.cell_at);
         UPF(cell_as, hs.cell_as);
@@ -1006,6 +1144,30 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
                 const float* p = nullptr;
                 rc = upload(h, &p, tof(v)); if (rc) return bail(rc);
                 *dsts[t] = p;
+            }
+        }
+    }
+    // ---------------------------------------- split FP64 GEMM operands
+    {
+        const bool split = o.dgemm == RTE_DGEMM_SPLIT ||
+                           (o.dgemm == RTE_DGEMM_AUTO && o.precision != RTE_FP64);
+        if (split) {
+            if (o.split_slices < 1 || o.split_slices > 10)
+                return bail(fail(RTE_ERR_ARG, "split_slices must be in [1, 10]"));
+            d.split_S = o.split_slices;
+            struct Src { const double* m; int rows, K; const void** sl; const int** ex; };
+            Src srcs[3] = {{d.VmT, nm, nm, &d.sl_VmT, &d.ex_VmT},
+                           {d.Vm, nm, nm, &d.sl_Vm, &d.ex_Vm},
+                           {d.Sp, n, n, &d.sl_Sp, &d.ex_Sp}};
+            for (auto& sr : srcs) {
+                char* p = nullptr;
+                rc = dalloc(h, &p, ozaki_slice_bytes(sr.rows, sr.K, d.split_S));
+                if (rc) return bail(rc);
+                int* ex = nullptr;
+                rc = ozaki_split(h->stream, sr.m, sr.rows, sr.K, d.split_S, p, &ex);
+                if (rc) return bail(rc);
+                *sr.sl = p;
+                *sr.ex = ex;
             }
         }
     }
@@ -1221,6 +1383,53 @@ int rte_timing_read(rte_handle* h, const char** names, double* ms, long long* la
 }
 
 long long rte_kernel_launches(void) { return launches_total(); }
+
+constexpr int kTraceCap = 1 << 16;
+
+int rte_trace_enable(rte_handle* h, int on) {
+    if (!h) return fail(RTE_ERR_ARG, "NULL handle");
+    if (on && !h->trace) RTE_TRY(dalloc(h, &h->trace, kTraceCap));
+    set_phase_trace(on ? h->trace : nullptr, on ? kTraceCap : 0);
+    return RTE_OK;
+}
+
+int rte_trace_read(rte_handle* h, double* us, int cap, int* count) {
+    if (!h || !count) return fail(RTE_ERR_ARG, "bad argument");
+    *count = 0;
+    if (!h->trace) return RTE_OK;
+    // the barrier struct of the last launch holds the entry count; the
+    // entries themselves are in the trace buffer
+    std::vector<unsigned long long> t(kTraceCap);
+    RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    RTE_CUDA_TRY(cudaMemcpy(t.data(), h->trace, t.size() * 8, cudaMemcpyDeviceToHost));
+    int n = 0;
+    while (n + 1 < kTraceCap && t[n + 1] > t[n] && t[n] != 0) ++n;
+    for (int i = 0; i < n && i < cap; ++i) us[i] = (t[i + 1] - t[i]) * 1e-3;
+    *count = n;
+    return RTE_OK;
+}
+
+int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, int K,
+                    int slices, void* stream) {
+    if (!A || !Bt || !C || M < 0 || N < 0 || K < 0 || slices < 1 || slices > 10)
+        return fail(RTE_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    char *pa = nullptr, *pb = nullptr;
+    if (cudaMallocAsync(&pa, ozaki_slice_bytes(M, K, slices), s) != cudaSuccess ||
+        cudaMallocAsync(&pb, ozaki_slice_bytes(N, K, slices), s) != cudaSuccess) {
+        cudaFreeAsync(pa, s);
+        return fail(RTE_ERR_NOMEM, "split GEMM temporaries");
+    }
+    int *ea = nullptr, *eb = nullptr;
+    int rc = ozaki_split(s, A, M, K, slices, pa, &ea);
+    if (!rc) rc = ozaki_split(s, Bt, N, K, slices, pb, &eb);
+    if (!rc) rc = ozaki_gemm(s, pa, ea, M, pb, eb, N, K, slices, C, N, 0, nullptr, nullptr,
+                             nullptr, 1);
+    cudaFreeAsync(pa, s);
+    cudaFreeAsync(pb, s);
+    if (rc) return rc;
+    return tc_gemm_error(s);
+}
 
 int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K, int bf16,
                   int out_bf16, void* stream) {

@@ -24,105 +24,16 @@
 #include "device.h"
 #include "rte_internal.h"
 #include "tc_gemm.h"
+#include "tcgen05.cuh"
 
 namespace rte {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kBM = 128;
 constexpr int kStages = 4;
-constexpr int kRowBytes = 128;   // one K block of a row: 64 bf16 or 32 tf32
-constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
-
-__device__ int g_tc_error = 0;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if (clock64() - t0 > kWaitCycles) {
-            atomicExch(&g_tc_error, 1);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile stored with the
-// 128-byte swizzle: rows of 128 bytes, 8-row atoms of 1024 bytes
-// (stride-dimension offset 1024 B), descriptor version 1, swizzle mode 2.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)1 << 16;              // leading offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;    // stride offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;              // descriptor version
-    d |= (uint64_t)2 << 61;              // 128-byte swizzle
-    return d;
-}
-
-__device__ __forceinline__ void mma_issue(bool tf32, uint32_t tmem, uint64_t a, uint64_t b,
-                                          uint32_t idesc, uint32_t acc) {
-    if (tf32)
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    else
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 template <int BN, bool TF32, typename TOut>
 __global__ void __launch_bounds__(128, 1)
@@ -259,40 +170,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                      "r"(kTmemCols));
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void* p = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// 2-D K-major tensor map: rows x cols (cols = K contiguous), box = box_rows x
-// 128 bytes, 128-byte swizzle, zero fill out of bounds.
-int make_map(CUtensorMap* map, const void* base, bool tf32, int rows, int cols, int box_rows) {
-    auto fn = encode_fn();
-    if (!fn) return fail(RTE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-    const size_t esz = tf32 ? 4 : 2;
-    if ((reinterpret_cast<uintptr_t>(base) & 15) || ((size_t)cols * esz) % 16)
-        return fail(RTE_ERR_ARG, "tensor-core GEMM operand is not 16-byte aligned");
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
-    cuuint32_t box[2] = {(cuuint32_t)(kRowBytes / esz), (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                    2, const_cast<void*>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(RTE_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-    return RTE_OK;
-}
-
 template <int BN>
 constexpr size_t smem_bytes() {
     return 1024 + (size_t)kStages * (kBM + BN) * kRowBytes + (2 * kStages + 1) * 8 + 16;
@@ -344,6 +221,263 @@ int tc_gemm_error(cudaStream_t s) {
         cudaMemcpyToSymbolAsync(g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
         return fail(RTE_ERR_TIMEOUT, "a tensor-core GEMM pipeline wait timed out");
     }
+    return RTE_OK;
+}
+
+}  // namespace rte
+
+// ======================================================================
+// FP64-accurate GEMM from exact BF16 tensor-core products (error-free
+// splitting of the operands, after Ozaki, Ogita, Oishi and Rump).
+//
+// Every row of A (and of the K-major second operand Bt) is scaled by a power
+// of two 2^e so that its entries lie in (-1, 1), then cut into S digit
+// slices: r <- r * 2^7, d = rint(r), r <- r - d.  The digits are integers
+// with |d| <= 128, exact in BF16, and A = 2^e sum_s d_s 2^{-7(s+1)} up to a
+// remainder below 2^{-7S-1}.  A product of two digit slices summed over at
+// most 1024 terms is an integer below 2^24, so the tensor cores' FP32
+// accumulation of it is exact.  The kernel accumulates the slice pairs
+// (s, t) with s + t <= S - 1 (the others lie below the truncation level),
+// each in a tensor-memory buffer, into FP64 registers with its weight
+// 2^{-7(s+t+2)}, and finally applies the row and column scales.
+// ======================================================================
+namespace rte {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kOzBM = 128, kOzBN = 128, kOzStages = 4, kOzKChunk = 16;   // 16 x 64 = 1024
+constexpr int kOzMaxPairs = 64;
+
+struct OzPairs {
+    int n;
+    unsigned char s[kOzMaxPairs], t[kOzMaxPairs];
+};
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// 10 warps: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..9 drain
+// the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31, the half
+// (w - 2) / 4 of the 128 columns), so the producer and the MMA issuer never
+// wait on the epilogue's own arrivals.
+constexpr int kOzThreads = 320;
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+        int M, int N, int K, const OzPairs pairs, const int* __restrict__ ea,
+        const int* __restrict__ eb, double* __restrict__ C, int ldc, int epi,
+        const double* __restrict__ at, const double* __restrict__ as,
+        const double* __restrict__ lam, int rows) {
+    constexpr uint32_t kABytes = kOzBM * kRowBytes, kBBytes = kOzBN * kRowBytes;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kOzStages * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kOzStages * kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kOzStages + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kOzBM, n0 = blockIdx.x * kOzBN;
+    const int kblocks = (K + 63) / 64;
+    const int nchunks = (kblocks + kOzKChunk - 1) / kOzKChunk;
+    const int jobs = pairs.n * nchunks;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kOzStages),
+                   accf0 = smem_u32(bars + 2 * kOzStages), acce0 = smem_u32(bars + 2 * kOzStages + 2);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, 8);   // one arrival per warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        // --------------------------------------------- TMA producer
+        int g = 0;
+        for (int j = 0; j < jobs && ok; ++j) {
+            const int p = j / nchunks, ch = j % nchunks;
+            const int ya = pairs.s[p] * M + m0, yb = pairs.t[p] * N + n0;
+            const int kb1 = min(kblocks, (ch + 1) * kOzKChunk);
+            for (int kb = ch * kOzKChunk; kb < kb1; ++kb, ++g) {
+                const int st = g % kOzStages;
+                const uint32_t ph = (g / kOzStages) & 1;
+                if (!mbar_wait(empty0 + 8 * st, ph ^ 1)) { ok = false; break; }
+                mbar_expect_tx(full0 + 8 * st, kABytes + kBBytes);
+                tma_load_2d(smem_u32(sA + st * kABytes), &mapA, full0 + 8 * st, kb * 64, ya);
+                tma_load_2d(smem_u32(sB + st * kBBytes), &mapB, full0 + 8 * st, kb * 64, yb);
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------- MMA issuer
+        const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                               ((uint32_t)(kOzBN >> 3) << 17) | ((uint32_t)(kOzBM >> 4) << 24);
+        int g = 0;
+        for (int j = 0; j < jobs && ok; ++j) {
+            const int b = j & 1;
+            const uint32_t bph = (j >> 1) & 1;
+            if (!mbar_wait(acce0 + 8 * b, bph ^ 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dtm = tmem + (uint32_t)(b * kOzBN);
+            const int ch = j % nchunks;
+            const int kb0 = ch * kOzKChunk, kb1 = min(kblocks, kb0 + kOzKChunk);
+            for (int kb = kb0; kb < kb1 && ok; ++kb, ++g) {
+                const int st = g % kOzStages;
+                const uint32_t ph = (g / kOzStages) & 1;
+                if (!mbar_wait(full0 + 8 * st, ph)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + st * kABytes), b0 = smem_u32(sB + st * kBBytes);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_issue(false, dtm, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), idesc,
+                              (kb > kb0 || kk > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * st);
+            }
+            mma_commit(accf0 + 8 * b);
+        }
+    }
+    __syncwarp();
+    if (warp < 2) {
+        // producer and MMA warps: wait for the epilogue, then free TMEM
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (warp == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                         "r"(256));
+        return;
+    }
+    // ------------------------------------------------------------ epilogue
+    const int wq = warp & 3, half = (warp - 2) >> 2;
+    double acc[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) acc[i] = 0.0;
+    for (int j = 0; j < jobs; ++j) {
+        const int b = j & 1;
+        const uint32_t bph = (j >> 1) & 1;
+        if (ok) ok = mbar_wait(accf0 + 8 * b, bph);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int p = j / nchunks;
+        const double w = ldexp(1.0, -7 * (pairs.s[p] + pairs.t[p] + 2));
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * kOzBN + half * 64 + c0), v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[c0 + i] = fma(w, (double)v[i], acc[c0 + i]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acce0 + 8 * b);
+    }
+    const int row = m0 + wq * 32 + lane;
+    if (ok && row < M) {
+        const int er = ea[row];
+        double fat = 0.0, fas = 0.0;
+        if (epi == 1) {
+            fat = at[row % rows];
+            fas = as[row % rows];
+        }
+        double* dst = C + (size_t)row * ldc;
+#pragma unroll
+        for (int i = 0; i < 64; ++i) {
+            const int col = n0 + half * 64 + i;
+            if (col < N) {
+                double x = ldexp(acc[i], er + eb[col]);
+                if (epi == 1) x = x / (fat - lam[col] * fas);
+                dst[col] = x;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+}
+
+// One warp per row: exponent of the row maximum, then S digit slices.
+__global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int S,
+                           __nv_bfloat16* __restrict__ out, int* __restrict__ e) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const double* x = X + (size_t)row * K;
+    double mx = 0.0;
+    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(x[k]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int ex = 0;
+    frexp(mx, &ex);   // mx = f 2^ex, f in [0.5, 1): |x| 2^-ex < 1
+    if (lane == 0) e[row] = ex;
+    for (int k = lane; k < K; k += 32) {
+        double r = ldexp(x[k], -ex);
+        for (int s = 0; s < S; ++s) {
+            const double t = r * 128.0;
+            const double d = rint(t);
+            r = t - d;
+            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn((float)d);
+        }
+    }
+}
+
+}  // namespace
+
+size_t ozaki_slice_bytes(int rows, int K, int S) {
+    return (size_t)S * rows * K * sizeof(__nv_bfloat16) + (size_t)rows * sizeof(int) + 512;
+}
+
+int ozaki_split(cudaStream_t s, const double* X, int rows, int K, int S, void* out, int** e) {
+    char* p = static_cast<char*>(out);
+    __nv_bfloat16* sl = reinterpret_cast<__nv_bfloat16*>(p);
+    int* ex = reinterpret_cast<int*>(p + (((size_t)S * rows * K * 2 + 255) / 256) * 256);
+    count_launches(1);
+    k_oz_split<<<(unsigned)(((size_t)rows * 32 + 255) / 256), 256, 0, s>>>(X, rows, K, S, sl, ex);
+    RTE_CUDA_TRY(cudaGetLastError());
+    if (e) *e = ex;
+    return RTE_OK;
+}
+
+int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const void* Bslices,
+               const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
+               const double* as, const double* lam, int rows) {
+    if (M <= 0 || N <= 0 || K <= 0) return RTE_OK;
+    if (S < 1 || S * (S + 1) / 2 > kOzMaxPairs) return fail(RTE_ERR_ARG, "bad slice count");
+    OzPairs pairs{};
+    for (int a = 0; a < S; ++a)
+        for (int b = 0; a + b <= S - 1; ++b) {
+            pairs.s[pairs.n] = (unsigned char)a;
+            pairs.t[pairs.n] = (unsigned char)b;
+            ++pairs.n;
+        }
+    CUtensorMap ma, mb;
+    RTE_TRY(make_map(&ma, Aslices, false, S * M, K, kOzBM));
+    RTE_TRY(make_map(&mb, Bslices, false, S * N, K, kOzBN));
+    const size_t sm = 1024 + (size_t)kOzStages * (kOzBM + kOzBN) * kRowBytes +
+                      (2 * kOzStages + 4) * 8 + 16;
+    static bool attr = false;
+    if (!attr) {
+        RTE_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)sm));
+        attr = true;
+    }
+    dim3 grid((N + kOzBN - 1) / kOzBN, (M + kOzBM - 1) / kOzBM);
+    count_launches(1);
+    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, pairs, ea, eb, C, ldc, epi, at, as,
+                                         lam, rows);
+    RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }
 

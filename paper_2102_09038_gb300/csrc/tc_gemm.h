@@ -21,7 +21,19 @@ struct TcGemmArgs {
 };
 
 int tc_gemm(cudaStream_t s, const TcGemmArgs& g);
-// Reads and clears the device-side timeout flag of the GEMM pipeline.
+// Reads and clears the device-side timeout flag of the GEMM pipelines.
 int tc_gemm_error(cudaStream_t s);
+
+// FP64-accurate GEMM from exact BF16 products of digit slices (tc_gemm.cu).
+// ozaki_split: S slices of the rows of X (rows x K, FP64) into `out`
+// (ozaki_slice_bytes), *e = per-row exponents inside `out`.
+size_t ozaki_slice_bytes(int rows, int K, int S);
+int ozaki_split(cudaStream_t s, const double* X, int rows, int K, int S, void* out, int** e);
+// C (M x N, FP64) = A B^T from the slices of A (M x K) and of Bt (N x K);
+// epi 1 divides by (at[r % rows] - lam[c] as[r % rows]).  K <= any; exact
+// accumulation within chunks of 1024.
+int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const void* Bslices,
+               const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
+               const double* as, const double* lam, int rows);
 
 }  // namespace rte
