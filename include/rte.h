@@ -95,6 +95,8 @@ typedef struct {
     int max_rhs;            /* workspace is sized for this many RHS          */
     int dgemm;              /* RTE_DGEMM_AUTO | RTE_DGEMM_SIMT | _SPLIT      */
     int split_slices;       /* digit slices per operand for RTE_DGEMM_SPLIT  */
+    int mg_sweeps;          /* smoothing sweeps before and after each coarse
+                               correction in the multigrid preconditioners   */
 } rte_options;
 
 typedef struct {
@@ -197,7 +199,7 @@ int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K,
 
 /* The FP64 split GEMM of RTE_DGEMM_SPLIT, exposed for testing and
  * profiling: C[M x N] = A[M x K] * Bt[N x K]^T, all FP64 row-major device
- * arrays, with `slices` digit slices per operand (1..10).  Allocates its own
+ * arrays, with `slices` digit slices per operand (1..9).  Allocates its own
  * temporaries. */
 int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, int K,
                     int slices, void* stream);

@@ -49,7 +49,7 @@ class _Options(ctypes.Structure):
                 ('e0_maxit', ctypes.c_int), ('coarse_tol', ctypes.c_double),
                 ('coarse_maxit', ctypes.c_int), ('max_iter', ctypes.c_int),
                 ('max_rhs', ctypes.c_int), ('dgemm', ctypes.c_int),
-                ('split_slices', ctypes.c_int)]
+                ('split_slices', ctypes.c_int), ('mg_sweeps', ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):

@@ -322,7 +322,7 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
               MGDevice& out) {
     out.L = (int)mh.levels.size();
     if (out.L > kMaxMGLevels) return fail(RTE_ERR_ARG, "too many multigrid levels");
-    out.nu = 2;
+    out.nu = std::max(1, std::min(h->opt.mg_sweeps, 16));
     out.cap_cols = cols;
     out.dense = mh.dense_coarse;
     for (int l = 0; l < out.L; ++l) {
@@ -500,13 +500,19 @@ int mk_inv_eigen(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
     if (d.split_S > 0) {
         int* ea = nullptr;
         {
-            Scope sc(h, "dgemm_split_mk1");
+            Scope sc(h, "split_digits");
             RTE_TRY(ozaki_split(h->stream, Z1, rows, d.nSm, d.split_S, h->slices, &ea));
+        }
+        {
+            Scope sc(h, "dgemm_split_mk1");
             RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_VmT, d.ex_VmT, d.nSm, d.nSm,
                                d.split_S, h->z4, d.nSm, 1, d.cell_at, d.cell_as, d.lamM, d.nRm));
         }
+        {
+            Scope sc(h, "split_digits");
+            RTE_TRY(ozaki_split(h->stream, h->z4, rows, d.nSm, d.split_S, h->slices, &ea));
+        }
         Scope sc(h, "dgemm_split_mk2");
-        RTE_TRY(ozaki_split(h->stream, h->z4, rows, d.nSm, d.split_S, h->slices, &ea));
         RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_Vm, d.ex_Vm, d.nSm, d.nSm,
                            d.split_S, Z2, d.nSm, 0, nullptr, nullptr, nullptr, 1));
         return RTE_OK;
@@ -823,6 +829,7 @@ int rte_default_options(rte_options* o) {
     o->max_rhs = 1;
     o->dgemm = RTE_DGEMM_AUTO;
     o->split_slices = 7;
+    o->mg_sweeps = 2;
     return RTE_OK;
 }
 
@@ -1152,8 +1159,8 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         const bool split = o.dgemm == RTE_DGEMM_SPLIT ||
                            (o.dgemm == RTE_DGEMM_AUTO && o.precision != RTE_FP64);
         if (split) {
-            if (o.split_slices < 1 || o.split_slices > 10)
-                return bail(fail(RTE_ERR_ARG, "split_slices must be in [1, 10]"));
+            if (o.split_slices < 1 || o.split_slices > 9)
+                return bail(fail(RTE_ERR_ARG, "split_slices must be in [1, 9]"));
             d.split_S = o.split_slices;
             struct Src { const double* m; int rows, K; const void** sl; const int** ex; };
             Src srcs[3] = {{d.VmT, nm, nm, &d.sl_VmT, &d.ex_VmT},
@@ -1411,7 +1418,7 @@ int rte_trace_read(rte_handle* h, double* us, int cap, int* count) {
 
 int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, int K,
                     int slices, void* stream) {
-    if (!A || !Bt || !C || M < 0 || N < 0 || K < 0 || slices < 1 || slices > 10)
+    if (!A || !Bt || !C || M < 0 || N < 0 || K < 0 || slices < 1 || slices > 9)
         return fail(RTE_ERR_ARG, "bad argument");
     cudaStream_t s = (cudaStream_t)stream;
     char *pa = nullptr, *pb = nullptr;

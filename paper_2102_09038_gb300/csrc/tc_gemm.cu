@@ -259,11 +259,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// 10 warps: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..9 drain
-// the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31, the half
-// (w - 2) / 4 of the 128 columns), so the producer and the MMA issuer never
-// wait on the epilogue's own arrivals.
-constexpr int kOzThreads = 320;
+// 18 warps: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..17 drain
+// the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the
+// quarter (w - 2) / 4 of the 128 columns), so the producer and the MMA
+// issuer never wait on the epilogue's own arrivals.
+constexpr int kOzThreads = 576;
+constexpr int kOzEpiWarps = 16;
 
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -286,6 +287,15 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
     const int jobs = pairs.n * nchunks;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kOzStages),
                    accf0 = smem_u32(bars + 2 * kOzStages), acce0 = smem_u32(bars + 2 * kOzStages + 2);
+    // slice-pair table in shared memory (a dynamically indexed kernel
+    // parameter would live in local memory)
+    __shared__ int s_ya[kOzMaxPairs], s_yb[kOzMaxPairs];
+    __shared__ float s_w[kOzMaxPairs];
+    for (int p = threadIdx.x; p < pairs.n; p += blockDim.x) {
+        s_ya[p] = pairs.s[p] * M + m0;
+        s_yb[p] = pairs.t[p] * N + n0;
+        s_w[p] = ldexpf(1.0f, -7 * (pairs.s[p] + pairs.t[p] + 2));
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < kOzStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -293,7 +303,7 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
-            mbar_init(acce0 + 8 * b, 8);   // one arrival per warp
+            mbar_init(acce0 + 8 * b, kOzEpiWarps);   // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -314,7 +324,7 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         int g = 0;
         for (int j = 0; j < jobs && ok; ++j) {
             const int p = j / nchunks, ch = j % nchunks;
-            const int ya = pairs.s[p] * M + m0, yb = pairs.t[p] * N + n0;
+            const int ya = s_ya[p], yb = s_yb[p];
             const int kb1 = min(kblocks, (ch + 1) * kOzKChunk);
             for (int kb = ch * kOzKChunk; kb < kb1; ++kb, ++g) {
                 const int st = g % kOzStages;
@@ -364,23 +374,37 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         return;
     }
     // ------------------------------------------------------------ epilogue
-    const int wq = warp & 3, half = (warp - 2) >> 2;
-    double acc[64];
+    const int wq = warp & 3, quarter = (warp - 2) >> 2;
+    // Double-float accumulators (hi + lo, about 48 significant bits): every
+    // job adds v 2^-7(s+t+2) with v an integer below 2^24, exact in FP32; the
+    // two-sum keeps the rounding error of each addition in lo.  FP32 runs at
+    // many times the FP64 rate of this GPU.
+    float hi[32], lo[32];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 32; ++i) {
+        hi[i] = 0.f;
+        lo[i] = 0.f;
+    }
     for (int j = 0; j < jobs; ++j) {
         const int b = j & 1;
         const uint32_t bph = (j >> 1) & 1;
         if (ok) ok = mbar_wait(accf0 + 8 * b, bph);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int p = j / nchunks;
-        const double w = ldexp(1.0, -7 * (pairs.s[p] + pairs.t[p] + 2));
+        const float w = s_w[j / nchunks];
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = 0; c0 < 32; c0 += 16) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * kOzBN + half * 64 + c0), v);
+            tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * kOzBN + quarter * 32 + c0), v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[c0 + i] = fma(w, (double)v[i], acc[c0 + i]);
+            for (int i = 0; i < 16; ++i) {
+                const float x = v[i] * w;                 // exact
+                const float sum = __fadd_rn(hi[c0 + i], x);
+                const float bb = __fsub_rn(sum, hi[c0 + i]);
+                const float err = __fadd_rn(__fsub_rn(hi[c0 + i], __fsub_rn(sum, bb)),
+                                            __fsub_rn(x, bb));
+                hi[c0 + i] = sum;
+                lo[c0 + i] = __fadd_rn(lo[c0 + i], err);
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
@@ -396,10 +420,10 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         }
         double* dst = C + (size_t)row * ldc;
 #pragma unroll
-        for (int i = 0; i < 64; ++i) {
-            const int col = n0 + half * 64 + i;
+        for (int i = 0; i < 32; ++i) {
+            const int col = n0 + quarter * 32 + i;
             if (col < N) {
-                double x = ldexp(acc[i], er + eb[col]);
+                double x = ldexp((double)hi[i] + (double)lo[i], er + eb[col]);
                 if (epi == 1) x = x / (fat - lam[col] * fas);
                 dst[col] = x;
             }
@@ -409,27 +433,49 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
     __syncthreads();
 }
 
-// One warp per row: exponent of the row maximum, then S digit slices.
+// One warp per row: exponent ex of the row maximum (|x| < 2^ex), then the
+// S balanced base-128 digits of X = round(x 2^(7S - ex)) in integer
+// arithmetic: the FP64 mantissa is shifted once to the row's fixed point,
+// and the digits are peeled from the least significant end,
+// d = ((X + 64) mod 128) - 64, X <- (X - d) / 128; the leading digit keeps
+// the rest (|d_0| <= 128).  x 2^-ex = sum_s d_s 2^{-7(s+1)} + r with
+// |r| <= 2^{-7S-1}.
 __global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int S,
                            __nv_bfloat16* __restrict__ out, int* __restrict__ e) {
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= rows) return;
     const double* x = X + (size_t)row * K;
-    double mx = 0.0;
-    for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(x[k]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int ex = 0;
-    frexp(mx, &ex);   // mx = f 2^ex, f in [0.5, 1): |x| 2^-ex < 1
-    if (lane == 0) e[row] = ex;
+    // row maximum of the biased exponent field
+    int emax = 0;
     for (int k = lane; k < K; k += 32) {
-        double r = ldexp(x[k], -ex);
-        for (int s = 0; s < S; ++s) {
-            const double t = r * 128.0;
-            const double d = rint(t);
-            r = t - d;
+        const int be = (int)((__double_as_longlong(x[k]) >> 52) & 0x7FF);
+        emax = max(emax, be);
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    // |x| < 2^(be - 1022) for a normal x with biased exponent be
+    const int ex = emax - 1022;
+    if (lane == 0) e[row] = emax == 0 ? 0 : ex;
+    for (int k = lane; k < K; k += 32) {
+        const long long bits = __double_as_longlong(x[k]);
+        const int be = (int)((bits >> 52) & 0x7FF);
+        long long v = 0;
+        if (be != 0 && emax != 0) {
+            const long long mant = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
+            // x 2^(7S - ex) = mant 2^(be - 1075 + 7S - ex)
+            const int sh = be - 1075 + 7 * S - ex;
+            if (sh >= 0)
+                v = sh <= 10 ? (mant << sh) : 0;   // S = 8, 9 (|v| < 2^(7S) <= 2^63)
+            else if (sh > -60)
+                v = (mant + (1ll << (-sh - 1))) >> (-sh);
+            if (bits < 0) v = -v;
+        }
+        for (int s = S - 1; s >= 1; --s) {
+            const long long d = ((v + 64) & 127) - 64;
+            v = (v - d) >> 7;
             out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn((float)d);
         }
+        out[(size_t)row * K + k] = __float2bfloat16_rn((float)v);
     }
 }
 
