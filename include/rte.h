@@ -204,6 +204,36 @@ int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K,
 int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, int K,
                     int slices, void* stream);
 
+/* Allocation-free variant of rte_dgemm_split.  The paper has no counterpart:
+ * this serves callers that must not allocate device memory when they call,
+ * such as a process whose device memory is already handed to another
+ * allocator (a framework's caching pool, a serving memory budget), or a
+ * latency-critical loop in which an allocation could block or fail.
+ *
+ * Same arguments, kernels and result as rte_dgemm_split, but the digit
+ * slices and row exponents of both operands live in one static device array
+ * of RTE_SPLIT_STATIC_SCRATCH_BYTES inside the library; it allocates nothing
+ * (no cudaMalloc, no pool, no library allocator).  Nothing in the scratch
+ * has to start at zero: every call writes all it reads.
+ *
+ * Limit: the operands need ceil256(2 slices M K + 4 M + 512) +
+ * 2 slices N K + 4 N + 512 bytes of scratch, at most
+ * RTE_SPLIT_STATIC_SCRATCH_BYTES = 32 MiB (e.g. slices = 7 with
+ * M = N = K = 1024).  Larger operands return RTE_ERR_ARG, with the bytes
+ * needed in rte_last_error(), before any device work.  K must be a multiple
+ * of 8 (16-byte rows of BF16 slices); K = 0 writes C = 0.
+ *
+ * The first call on each device looks up the scratch's device address and
+ * sets the GEMM kernel's shared-memory attribute: make it before any stream
+ * capture begins on that device.  Calls that overlap in time on one device
+ * (from several host threads, or on streams whose work overlaps) share the
+ * one scratch and race: order them (one stream, or an event between them).
+ * Synchronises `stream` before returning (it reads the GEMM's timeout
+ * flag). */
+#define RTE_SPLIT_STATIC_SCRATCH_BYTES (32u << 20)
+int rte_dgemm_split_static(const double* A, const double* Bt, double* C, int M, int N, int K,
+                           int slices, void* stream);
+
 /* Copies an assembled matrix to host memory (for checks against an
  * independent assembly).  what: 0 S^+ (n_S^+^2), 1 S^- (n_S^-^2),
  * 2 M_S^+ diagonal (n_S^+), 3 M_S^- blocks (n_S^+ x 9), 4 A_1 (n_S^+ x 3),

@@ -100,6 +100,7 @@ def load(path=LIB_PATH):
                                     ctypes.POINTER(I)]
     lib.rte_gemm_lowp.argtypes = [P, P, P, I, I, I, I, I, P]
     lib.rte_dgemm_split.argtypes = [P, P, P, I, I, I, I, P]
+    lib.rte_dgemm_split_static.argtypes = [P, P, P, I, I, I, I, P]
     lib.rte_estimate_bytes.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Options), I]
     lib.rte_estimate_bytes.restype = ctypes.c_size_t
     lib.rte_server_create.argtypes = [ctypes.c_size_t, I, ctypes.POINTER(_Options),
@@ -162,6 +163,24 @@ def dgemm_split(A, Bt, slices=7, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(_lib.rte_dgemm_split(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, slices,
                                 ctypes.c_void_p(st.cuda_stream)))
+    return C
+
+
+def dgemm_split_static(A, Bt, slices=7, out=None, stream=None):
+    """C = A @ Bt.T like dgemm_split, through the allocation-free entry point
+    (temporaries in the library's fixed 32 MiB device scratch; calls must not
+    overlap in time on one device).  Pass `out` (M x N float64, contiguous)
+    so that nothing is allocated on this path at all."""
+    import torch
+    load()
+    A = A.contiguous()
+    Bt = Bt.contiguous()
+    M, K = A.shape
+    N = Bt.shape[0]
+    C = out if out is not None else torch.empty((M, N), device=A.device, dtype=torch.float64)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.rte_dgemm_split_static(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, slices,
+                                       ctypes.c_void_p(st.cuda_stream)))
     return C
 
 

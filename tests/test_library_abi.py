@@ -53,3 +53,22 @@ def test_solver_refuses_without_cuda(lib_path):
         pytest.skip('a GPU is present')
     with pytest.raises(RuntimeError):
         rte.Solver(workloads.constant(2, 0, 0.5, 1.0, 0.5))
+
+
+def test_static_split_gemm_refuses_oversize_operands_on_the_host(lib_path):
+    """The allocation-free split GEMM checks its operand sizes against the
+    fixed scratch before any CUDA call, so this runs without a GPU (the
+    pointers are never dereferenced)."""
+    import ctypes
+    import paper_2102_09038_gb300 as rte
+    lib = rte.load()
+    fake = ctypes.c_void_p(256)
+    # 2 * 7 * (4096 + 4096) * 4096 bytes of slices, far above 32 MiB
+    assert lib.rte_dgemm_split_static(fake, fake, fake, 4096, 4096, 4096, 7, None) == 1
+    assert b'scratch' in lib.rte_last_error()
+    # sizes whose byte count would overflow 64 bits
+    big = 2 ** 31 - 1
+    assert lib.rte_dgemm_split_static(fake, fake, fake, big, big, big, 9, None) == 1
+    # just above the limit: M = N = 1024, K = 1176 needs 33,718,272 bytes of slices
+    assert lib.rte_dgemm_split_static(fake, fake, fake, 1024, 1024, 1176, 7, None) == 1
+    assert lib.rte_dgemm_split_static(fake, fake, fake, 1, 1, 1, 0, None) == 1
