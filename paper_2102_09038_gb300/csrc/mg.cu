@@ -407,51 +407,116 @@ __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
 }
 
 // ============================================================ E_c V-cycle
+// E_c work is spread over lane groups: G lanes (8, 16 or 32, the smallest
+// power of two that holds d) per (rhs, node) item, 32 / G items per warp;
+// lane a of a group owns row a of the item's d values.  Blocks are stored
+// transposed, [dir][n][b][a], so the lanes of a group read consecutive words.
 struct EcMG {
-    int L, nrhs, d, nu;
+    int L, nrhs, d, nu, G;
     bool dense;
     const float* cinv;     // [(n_c d)][(n_c d)]
     MGDeviceLevel lev[kMaxMGLevels];
 };
 
-// warp-level loop over (rhs, node) pairs of a level; lane = mode
-#define WARP_LOOP(nn)                                                              \
+// Loop over the (rhs, node) items of an array of nn nodes.  All lanes of a
+// warp make the same number of trips (an item past the end has ok == false),
+// so group shuffles inside the body stay convergent.  Needs `mg`, `d`, `gpw`
+// and `grp` in scope; defines r, i, ok and base (offset of the item's first
+// value).
+#define GROUP_LOOP(nn)                                                             \
     {                                                                              \
-    const unsigned wl_n__ = (unsigned)(nn);                                        \
-    const unsigned wl_stride__ = (gridDim.x * blockDim.x) >> 5;                    \
-    const unsigned wl_sq__ = wl_stride__ / wl_n__, wl_sr__ = wl_stride__ % wl_n__; \
-    unsigned wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;                    \
-    int r = (int)(wi / wl_n__), i = (int)(wi % wl_n__);                            \
-    for (; wi < (unsigned)mg.nrhs * wl_n__; wi += wl_stride__, r += wl_sq__, i += wl_sr__, \
-         (i >= (int)wl_n__ ? (i -= wl_n__, ++r) : 0)) {                            \
-        const size_t base = ((size_t)r * wl_n__ + i) * d;
+    const unsigned gl_n__ = (unsigned)(nn);                                        \
+    const unsigned gl_total__ = (unsigned)mg.nrhs * gl_n__;                        \
+    const unsigned gl_stride__ = (gridDim.x * blockDim.x) >> 5;                    \
+    for (unsigned gw__ = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;             \
+         gw__ * (unsigned)gpw < gl_total__; gw__ += gl_stride__) {                 \
+        const unsigned item__ = gw__ * (unsigned)gpw + (unsigned)grp;              \
+        const bool ok = item__ < gl_total__;                                       \
+        const int r = ok ? (int)(item__ / gl_n__) : 0;                             \
+        const int i = ok ? (int)(item__ % gl_n__) : 0;                             \
+        const size_t base = ((size_t)r * gl_n__ + i) * d;
 
+// y_a = sum over the 7 stencil directions of (E_c block) x, row a = gl
 __device__ __forceinline__ float ec_apply(const MGDeviceLevel& L, const float* x, int r, int i,
-                                          int d, int lane) {
+                                          int d, int gl, bool act) {
     float y = 0.f;
+    if (!act) return y;
     const float* xr = x + (size_t)r * L.n * d;
 #pragma unroll
     for (int dir = 0; dir < 7; ++dir) {
         const float* xv = xr + (size_t)nbr(i, dir, L.m, L.n) * d;
-        const float* blk = L.val + (((size_t)dir * L.n + i) * d + lane) * d;
-        if (lane < d)
-            for (int b = 0; b < d; ++b) y += __ldg(blk + b) * ldg2(xv + b);
+        const float* blk = L.val + ((size_t)dir * L.n + i) * d * d + gl;
+        for (int b = 0; b < d; ++b) y += __ldg(blk + (size_t)b * d) * ldg2(xv + b);
     }
     return y;
 }
 
-__device__ __forceinline__ float ec_dmul(const float* D, int d, float v, int lane) {
+// (D v)_a for the group's vector v (value b held by group lane b)
+__device__ __forceinline__ float ec_dmul(const float* D, int d, int G, float v, int gl, bool act) {
     float y = 0.f;
     for (int b = 0; b < d; ++b) {
-        const float vb = __shfl_sync(0xffffffffu, v, b);
-        if (lane < d) y += __ldg(D + lane * d + b) * vb;
+        const float vb = __shfl_sync(0xffffffffu, v, b, G);
+        if (act) y += __ldg(D + (size_t)b * d + gl) * vb;
     }
     return y;
+}
+
+// Per-rhs sums: every lane accumulates its own partial while its rhs stays
+// the same (a change, only at a right-hand-side boundary, flushes with an
+// atomic); rhs_flush then combines the lanes of the block and adds once.
+struct RhsSum {
+    double v;
+    int r;
+    __device__ RhsSum() : v(0.0), r(-1) {}
+    __device__ void add(double x, int rr, double* dst) {
+        if (rr != r) {
+            if (r >= 0 && v != 0.0) atomicAdd(dst + r, v);
+            v = 0.0;
+            r = rr;
+        }
+        v += x;
+    }
+};
+
+// All threads of the block call this at the same point.
+__device__ void rhs_flush(RhsSum& s, double* dst, double* sh_v, int* sh_r) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rlo = __reduce_min_sync(0xffffffffu, s.r < 0 ? 0x7fffffff : s.r);
+    const int rhi = __reduce_max_sync(0xffffffffu, s.r);
+    double v = s.v;
+    if (rlo == rhi) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            sh_v[warp] = v;
+            sh_r[warp] = rhi;
+        }
+    } else {
+        if (s.r >= 0 && v != 0.0) atomicAdd(dst + s.r, v);
+        if (lane == 0) sh_r[warp] = -1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        int cur = -1;
+        for (int w = 0; w < nw; ++w) {
+            if (sh_r[w] < 0) continue;
+            if (sh_r[w] != cur) {
+                if (cur >= 0) atomicAdd(dst + cur, acc);
+                acc = 0.0;
+                cur = sh_r[w];
+            }
+            acc += sh_v[w];
+        }
+        if (cur >= 0) atomicAdd(dst + cur, acc);
+    }
+    __syncthreads();
+    s.v = 0.0;
+    s.r = -1;
 }
 
 __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
-    const int d = mg.d;
-    const int lane = threadIdx.x & 31;
+    const int d = mg.d, G = mg.G, gpw = 32 / G;
+    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
     int cur[kMaxMGLevels];
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
@@ -459,11 +524,12 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         const MGDeviceLevel& Lv = mg.lev[l];
         const float* x = buf(l, cur[l]);
         float* xt = buf(l, cur[l] ^ 1);
-        WARP_LOOP(Lv.n)
-            const float y = ec_apply(Lv, x, r, i, d, lane);
-            const float res = lane < d ? ldg2(Lv.B + base + lane) - y : 0.f;
-            const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, res, lane);
-            if (lane < d) xt[base + lane] = ldg2(x + base + lane) + kOmega * dx;
+        GROUP_LOOP(Lv.n)
+            const bool act = ok && gl < d;
+            const float y = ec_apply(Lv, x, r, i, d, gl, act);
+            const float res = act ? ldg2(Lv.B + base + gl) - y : 0.f;
+            const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, G, res, gl, act);
+            if (act) xt[base + gl] = ldg2(x + base + gl) + kOmega * dx;
         }}
         cur[l] ^= 1;
         return grid_sync(bar);
@@ -471,10 +537,11 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
     auto first = [&](int l) -> bool {
         const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, 0);
-        WARP_LOOP(Lv.n)
-            const float bv = lane < d ? ldg2(Lv.B + base + lane) : 0.f;
-            const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, bv, lane);
-            if (lane < d) x[base + lane] = kOmega * dx;
+        GROUP_LOOP(Lv.n)
+            const bool act = ok && gl < d;
+            const float bv = act ? ldg2(Lv.B + base + gl) : 0.f;
+            const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, G, bv, gl, act);
+            if (act) x[base + gl] = kOmega * dx;
         }}
         cur[l] = 0;
         return grid_sync(bar);
@@ -486,22 +553,23 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
             if (!jacobi(l)) return false;
         const float* x = buf(l, cur[l]);
         float* t = buf(l, cur[l] ^ 1);
-        WARP_LOOP(Lv.n)
-            const float y = ec_apply(Lv, x, r, i, d, lane);
-            if (lane < d) t[base + lane] = ldg2(Lv.B + base + lane) - y;
+        GROUP_LOOP(Lv.n)
+            const bool act = ok && gl < d;
+            const float y = ec_apply(Lv, x, r, i, d, gl, act);
+            if (act) t[base + gl] = ldg2(Lv.B + base + gl) - y;
         }}
         if (!grid_sync(bar)) return false;
         const MGDeviceLevel& Cv = mg.lev[l + 1];
-        WARP_LOOP(Cv.n)
-            if (lane < d) {
+        GROUP_LOOP(Cv.n)
+            if (ok && gl < d) {
                 float acc = 0.f;
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     float w;
                     const int f = restrict_src(i, Cv.m, q, w);
-                    acc += w * ldg2(t + ((size_t)r * Lv.n + f) * d + lane);
+                    acc += w * ldg2(t + ((size_t)r * Lv.n + f) * d + gl);
                 }
-                Cv.B[base + lane] = acc;
+                Cv.B[base + gl] = acc;
             }
         }}
         if (!grid_sync(bar)) return false;
@@ -543,14 +611,14 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         float* x = buf(l, cur[l]);
         const float* xc = buf(l + 1, cur[l + 1]);
         const int ncn = mg.lev[l + 1].n;
-        WARP_LOOP(Lv.n)
-            if (lane < d) {
+        GROUP_LOOP(Lv.n)
+            if (ok && gl < d) {
                 int c0, c1;
                 float w0, w1;
                 prolong_src(i, Lv.m, c0, c1, w0, w1);
-                const float v = w0 * ldg2(xc + ((size_t)r * ncn + c0) * d + lane) +
-                                w1 * ldg2(xc + ((size_t)r * ncn + c1) * d + lane);
-                x[base + lane] = ldg2(x + base + lane) + v;
+                const float v = w0 * ldg2(xc + ((size_t)r * ncn + c0) * d + gl) +
+                                w1 * ldg2(xc + ((size_t)r * ncn + c1) * d + gl);
+                x[base + gl] = ldg2(x + base + gl) + v;
             }
         }}
         if (!grid_sync(bar)) return false;
@@ -565,7 +633,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
 struct EcArgs {
     int nRp, m, d, nrhs, maxit;
     double tol2;
-    const double* ec;   // FP64 E_c in ELL form [7][nRp][d][d]
+    const double* ec;   // FP64 E_c in ELL form, blocks transposed: [7][nRp][b][a]
     const double* B;
     double* X;
     double* R;
@@ -578,42 +646,38 @@ struct EcArgs {
     EcMG mg;
 };
 
-__device__ void rhs_add(double v, double* dst, int r) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(dst + r, v);
-}
-
 __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     __shared__ int s_stop;
+    __shared__ double sh_v[32];
+    __shared__ int sh_r[32];
     if (threadIdx.x == 0) s_stop = 0;
-    const int d = a.d;
-    const int lane = threadIdx.x & 31;
     const EcMG& mg = a.mg;
+    const int d = a.d, G = mg.G, gpw = 32 / G;
+    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
     float* B0 = mg.lev[0].B;
     auto sl = [&](int s, int q) { return a.acc + ((size_t)s * 3 + q) * a.nrhs; };
-    WARP_LOOP(a.nRp)
-        double pbb = 0.0;
-        if (lane < d) {
-            const double b = a.B[base + lane];
-            a.X[base + lane] = 0.0;
-            a.R[base + lane] = b;
-            B0[base + lane] = (float)b;
-            pbb = b * b;
+    RhsSum sum;
+    GROUP_LOOP(a.nRp)
+        if (ok && gl < d) {
+            const double b = a.B[base + gl];
+            a.X[base + gl] = 0.0;
+            a.R[base + gl] = b;
+            B0[base + gl] = (float)b;
+            sum.add(b * b, r, a.bb);
         }
-        rhs_add(pbb, a.bb, r);
     }}
+    rhs_flush(sum, a.bb, sh_v, sh_r);
     if (!grid_sync(a.bar)) return;
     float* z = nullptr;
     if (!ec_vcycle(mg, a.bar, z)) return;
-    WARP_LOOP(a.nRp)
-        double prz = 0.0;
-        if (lane < d) {
-            const double zv = ldg2(z + base + lane);
-            a.P[base + lane] = zv;
-            prz = ldg2(a.R + base + lane) * zv;
+    GROUP_LOOP(a.nRp)
+        if (ok && gl < d) {
+            const double zv = ldg2(z + base + gl);
+            a.P[base + gl] = zv;
+            sum.add(ldg2(a.R + base + gl) * zv, r, sl(2, 1));
         }
-        rhs_add(prz, sl(2, 1), r);
     }}
+    rhs_flush(sum, sl(2, 1), sh_v, sh_r);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.nrhs; c += gridDim.x * blockDim.x)
         sl(2, 2)[c] = ldg2(a.bb + c);
     if (!grid_sync(a.bar)) return;
@@ -623,65 +687,62 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
         if (blockIdx.x == 0)
             for (int c = threadIdx.x; c < 3 * a.nrhs; c += blockDim.x)
                 a.acc[(size_t)next * 3 * a.nrhs + c] = 0.0;
-        WARP_LOOP(a.nRp)
-            const bool act = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
-            if (!act) continue;
-            double y = 0.0;
-            const double* Pr = a.P + (size_t)r * a.nRp * d;
-            if (lane < d)
+        GROUP_LOOP(a.nRp)
+            const bool act = ok && gl < d && ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
+            if (act) {
+                double y = 0.0;
+                const double* Pr = a.P + (size_t)r * a.nRp * d;
 #pragma unroll
                 for (int dir = 0; dir < 7; ++dir) {
-                    const double* blk = a.ec + (((size_t)dir * a.nRp + i) * d + lane) * d;
+                    const double* blk = a.ec + ((size_t)dir * a.nRp + i) * d * d + gl;
                     const double* xv = Pr + (size_t)nbr(i, dir, a.m, a.nRp) * d;
-                    for (int b = 0; b < d; ++b) y = fma(__ldg(blk + b), ldg2(xv + b), y);
+                    for (int b = 0; b < d; ++b) y = fma(__ldg(blk + (size_t)b * d), ldg2(xv + b), y);
                 }
-            double ppap = 0.0;
-            if (lane < d) {
-                a.AP[base + lane] = y;
-                ppap = y * ldg2(a.P + base + lane);
+                a.AP[base + gl] = y;
+                sum.add(y * ldg2(a.P + base + gl), r, sl(cur, 0));
             }
-            rhs_add(ppap, sl(cur, 0), r);
         }}
+        rhs_flush(sum, sl(cur, 0), sh_v, sh_r);
         if (!grid_sync(a.bar)) return;
-        WARP_LOOP(a.nRp)
-            const bool act = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
-            double prr = 0.0;
-            if (act && lane < d) {
-                const double pap = ldg2(sl(cur, 0) + r);
-                const double alpha = pap != 0.0 ? ldg2(sl(prev, 1) + r) / pap : 0.0;
-                a.X[base + lane] += alpha * ldg2(a.P + base + lane);
-                const double rv = ldg2(a.R + base + lane) - alpha * ldg2(a.AP + base + lane);
-                a.R[base + lane] = rv;
-                prr = rv * rv;
-                B0[base + lane] = (float)rv;
-            } else if (lane < d) {
-                B0[base + lane] = 0.f;
+        GROUP_LOOP(a.nRp)
+            if (ok && gl < d) {
+                const bool act = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
+                if (act) {
+                    const double pap = ldg2(sl(cur, 0) + r);
+                    const double alpha = pap != 0.0 ? ldg2(sl(prev, 1) + r) / pap : 0.0;
+                    a.X[base + gl] += alpha * ldg2(a.P + base + gl);
+                    const double rv = ldg2(a.R + base + gl) - alpha * ldg2(a.AP + base + gl);
+                    a.R[base + gl] = rv;
+                    B0[base + gl] = (float)rv;
+                    sum.add(rv * rv, r, sl(cur, 2));
+                } else {
+                    B0[base + gl] = 0.f;
+                }
             }
-            if (act) rhs_add(prr, sl(cur, 2), r);
         }}
+        rhs_flush(sum, sl(cur, 2), sh_v, sh_r);
         if (!grid_sync(a.bar)) return;
         if (!ec_vcycle(mg, a.bar, z)) return;
-        WARP_LOOP(a.nRp)
-            const bool act = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
-            if (!act) continue;
-            double prz = 0.0;
-            if (lane < d) prz = ldg2(a.R + base + lane) * (double)ldg2(z + base + lane);
-            rhs_add(prz, sl(cur, 1), r);
+        GROUP_LOOP(a.nRp)
+            if (ok && gl < d && ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r))
+                sum.add(ldg2(a.R + base + gl) * (double)ldg2(z + base + gl), r, sl(cur, 1));
         }}
+        rhs_flush(sum, sl(cur, 1), sh_v, sh_r);
         if (!grid_sync(a.bar)) return;
-        WARP_LOOP(a.nRp)
-            const bool was = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
-            if (!was) {
-                if (i == 0 && lane == 0) {
-                    sl(cur, 2)[r] = ldg2(sl(prev, 2) + r);
-                    sl(cur, 1)[r] = ldg2(sl(prev, 1) + r);
+        GROUP_LOOP(a.nRp)
+            if (ok) {
+                const bool was = ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
+                if (!was) {
+                    if (i == 0 && gl == 0) {
+                        sl(cur, 2)[r] = ldg2(sl(prev, 2) + r);
+                        sl(cur, 1)[r] = ldg2(sl(prev, 1) + r);
+                    }
+                } else if (gl < d && ldg2(sl(cur, 2) + r) > a.tol2 * ldg2(a.bb + r)) {
+                    const double rzo = ldg2(sl(prev, 1) + r);
+                    const double beta = rzo != 0.0 ? ldg2(sl(cur, 1) + r) / rzo : 0.0;
+                    a.P[base + gl] = (double)ldg2(z + base + gl) + beta * ldg2(a.P + base + gl);
                 }
-                continue;
             }
-            if (!(ldg2(sl(cur, 2) + r) > a.tol2 * ldg2(a.bb + r)) || lane >= d) continue;
-            const double rzo = ldg2(sl(prev, 1) + r);
-            const double beta = rzo != 0.0 ? ldg2(sl(cur, 1) + r) / rzo : 0.0;
-            a.P[base + lane] = (double)ldg2(z + base + lane) + beta * ldg2(a.P + base + lane);
         }}
         if (!grid_sync(a.bar)) return;
         if (threadIdx.x == 0) s_stop = 1;
@@ -699,7 +760,7 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
         a.status->converged = s_stop;
     }
 }
-#undef WARP_LOOP
+#undef GROUP_LOOP
 
 __global__ void k_copy_err(const GridBar* bar, SolveStatus* st) { st->timed_out = bar->err; }
 
@@ -848,6 +909,7 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     a.mg = view<EcMG>(d.ecmg);
     a.mg.nrhs = nrhs;
     a.mg.d = d.dP;
+    a.mg.G = d.dP <= 8 ? 8 : (d.dP <= 16 ? 16 : 32);
     const void* fn = (const void*)k_ec_pcg;
     const int grid = coop_grid(fn, 256);
     void* args[] = {&a};

@@ -13,8 +13,8 @@ constexpr int kMaxMGLevels = 14;
 
 struct MGDeviceLevel {
     int m = 0, n = 0;
-    const float* val = nullptr;    // E_0: [6][7][n]; E_c: [7][n][d][d]
-    const float* dinv = nullptr;   // E_c: [n][d][d] inverse diagonal blocks
+    const float* val = nullptr;    // E_0: [6][7][n]; E_c: [7][n][d][d], blocks transposed
+    const float* dinv = nullptr;   // E_c: [n][d][d] inverse diagonal blocks, transposed
     const float* cdir = nullptr;   // E_0: per-direction coefficients [7][n][nSp]
     float *X = nullptr, *Xt = nullptr, *B = nullptr;   // work vectors
 };

@@ -316,6 +316,16 @@ void inv_lower3(const double* L, double* Li) {
     }
 }
 
+// Transposes every bs x bs block of a block array in place (the E_c kernels
+// read blocks column by column).
+template <typename V>
+void transpose_blocks(std::vector<V>& a, int bs) {
+    const size_t bb = (size_t)bs * bs;
+    for (size_t o = 0; o + bb <= a.size(); o += bb)
+        for (int x = 0; x < bs; ++x)
+            for (int y = x + 1; y < bs; ++y) std::swap(a[o + x * bs + y], a[o + y * bs + x]);
+}
+
 // Uploads a host multigrid hierarchy in ELL form; work vectors hold cols
 // columns of bs values per node.
 int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv,
@@ -332,10 +342,12 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
         D.n = (L.m + 1) * (L.m + 1);
         std::vector<double> ell;
         RTE_TRY(to_ell(L, mh.slots, bs, ell));
+        transpose_blocks(ell, bs);
         RTE_TRY(upload(h, &D.val, std::vector<float>(ell.begin(), ell.end())));
         if (block_dinv) {
             std::vector<float> di;
             RTE_TRY(block_diag_inverse(L, bs, di));
+            transpose_blocks(di, bs);
             RTE_TRY(upload(h, &D.dinv, di));
         }
         const size_t nv = (size_t)D.n * cols * bs;
@@ -426,6 +438,7 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         }
         std::vector<double> ell;
         RTE_TRY(to_ell(mh.levels[0], 1, d.dP, ell));
+        transpose_blocks(ell, d.dP);
         RTE_TRY(upload(h, &d.ec_ell, ell));
     }
     return RTE_OK;

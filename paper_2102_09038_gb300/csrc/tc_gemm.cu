@@ -182,12 +182,8 @@ int launch(cudaStream_t s, const TcGemmArgs& g) {
     RTE_TRY(make_map(&mb, g.Bt, TF32, g.N, g.K, BN));
     auto kern = k_tc_gemm<BN, TF32, TOut>;
     const size_t sm = smem_bytes<BN>();
-    static bool attr_done = false;
-    if (!attr_done) {
-        RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm));
-        attr_done = true;
-    }
+    // set on every call: the attribute is per device, and cheap to set
+    RTE_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid((g.N + BN - 1) / BN, (g.M + kBM - 1) / kBM);
     count_launches(1);
     kern<<<grid, 128, sm, s>>>(ma, mb, g.M, g.N, g.K, static_cast<TOut*>(g.C), g.ldc, g.epi,
@@ -513,12 +509,8 @@ int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const 
     RTE_TRY(make_map(&mb, Bslices, false, S * N, K, kOzBN));
     const size_t sm = 1024 + (size_t)kOzStages * (kOzBM + kOzBN) * kRowBytes +
                       (2 * kOzStages + 4) * 8 + 16;
-    static bool attr = false;
-    if (!attr) {
-        RTE_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)sm));
-        attr = true;
-    }
+    RTE_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm));
     dim3 grid((N + kOzBN - 1) / kOzBN, (M + kOzBM - 1) / kOzBM);
     count_launches(1);
     k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, pairs, ea, eb, C, ldc, epi, at, as,
