@@ -87,6 +87,29 @@ __device__ __forceinline__ void prolong_src(int i, int mf, int& c0, int& c1, flo
     for (; e < it_total__; e += it_stride__, i += it_sq__, c += it_sr__,         \
                            (c >= (int)it_nc__ ? (c -= it_nc__, ++i) : 0))
 
+// The same loop taking two items per trip, e0 and e1 = e0 + stride (v1 says
+// whether e1 exists), so that the loads of both are in flight together: a
+// store between two items would otherwise keep the second item's loads
+// behind the first item's store, one memory latency per item.
+#define ITEMS2(n, ncv)                                                          \
+    {                                                                            \
+    const int it_nc__ = (int)(ncv);                                              \
+    const unsigned it_total__ = (unsigned)(n) * (unsigned)it_nc__;               \
+    const unsigned it_stride__ = gridDim.x * blockDim.x;                         \
+    const int it_sq__ = (int)(it_stride__ / (unsigned)it_nc__);                  \
+    const int it_sr__ = (int)(it_stride__ % (unsigned)it_nc__);                  \
+    unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x;                         \
+    int i0 = (int)(e0 / (unsigned)it_nc__), c0 = (int)(e0 % (unsigned)it_nc__);  \
+    int i1 = i0 + it_sq__, c1 = c0 + it_sr__;                                    \
+    if (c1 >= it_nc__) { c1 -= it_nc__; ++i1; }                                  \
+    for (; e0 < it_total__; e0 += 2 * it_stride__,                               \
+         i0 = i1 + it_sq__, c0 = c1 + it_sr__,                                   \
+         (c0 >= it_nc__ ? (c0 -= it_nc__, ++i0) : 0),                            \
+         i1 = i0 + it_sq__, c1 = c0 + it_sr__,                                   \
+         (c1 >= it_nc__ ? (c1 -= it_nc__, ++i1) : 0)) {                          \
+        const unsigned e1 = e0 + it_stride__;                                    \
+        const bool v1 = e1 < it_total__;
+
 // ================================================================ E_0 V-cycle
 struct E0MG {
     int L, ncols, nSp, nu;
@@ -119,14 +142,22 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
     int cur[kMaxMGLevels];
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
+    const int km = mg.nSp - 1;   // n_S^+ is a power of two
     auto jacobi = [&](int l) -> bool {
         const MGDeviceLevel& Lv = mg.lev[l];
         const float* x = buf(l, cur[l]);
         float* xt = buf(l, cur[l] ^ 1);
-        ITEMS(Lv.n, nc) {
-            float dg;
-            const float y = e0_apply(Lv, mg.nSp, c % mg.nSp, x, i, c, nc, dg);
-            xt[e] = ldg2(x + e) + kOmega * (ldg2(Lv.B + e) - y) / dg;
+        ITEMS2(Lv.n, nc)
+            float dg0, dg1 = 1.f, y1 = 0.f, b1 = 0.f, x1 = 0.f;
+            const float y0 = e0_apply(Lv, mg.nSp, c0 & km, x, i0, c0, nc, dg0);
+            const float b0 = ldg2(Lv.B + e0), x0 = ldg2(x + e0);
+            if (v1) {
+                y1 = e0_apply(Lv, mg.nSp, c1 & km, x, i1, c1, nc, dg1);
+                b1 = ldg2(Lv.B + e1);
+                x1 = ldg2(x + e1);
+            }
+            xt[e0] = x0 + kOmega * __fdividef(b0 - y0, dg0);
+            if (v1) xt[e1] = x1 + kOmega * __fdividef(b1 - y1, dg1);
         }}
         cur[l] ^= 1;
         return grid_sync(bar);
@@ -134,8 +165,15 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
     auto first = [&](int l) -> bool {
         const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, 0);
-        ITEMS(Lv.n, nc) {
-            x[e] = kOmega * ldg2(Lv.B + e) / e0_cf(Lv, mg.nSp, 0, i, c % mg.nSp);
+        ITEMS2(Lv.n, nc)
+            const float b0 = ldg2(Lv.B + e0), d0 = e0_cf(Lv, mg.nSp, 0, i0, c0 & km);
+            float b1 = 0.f, d1 = 1.f;
+            if (v1) {
+                b1 = ldg2(Lv.B + e1);
+                d1 = e0_cf(Lv, mg.nSp, 0, i1, c1 & km);
+            }
+            x[e0] = kOmega * __fdividef(b0, d0);
+            if (v1) x[e1] = kOmega * __fdividef(b1, d1);
         }}
         cur[l] = 0;
         return grid_sync(bar);
@@ -147,22 +185,33 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
             if (!jacobi(l)) return false;
         const float* x = buf(l, cur[l]);
         float* t = buf(l, cur[l] ^ 1);
-        ITEMS(Lv.n, nc) {
-            float dg;
-            t[e] = ldg2(Lv.B + e) - e0_apply(Lv, mg.nSp, c % mg.nSp, x, i, c, nc, dg);
+        ITEMS2(Lv.n, nc)
+            float dg, r1 = 0.f;
+            const float r0 = ldg2(Lv.B + e0) - e0_apply(Lv, mg.nSp, c0 & km, x, i0, c0, nc, dg);
+            if (v1) r1 = ldg2(Lv.B + e1) - e0_apply(Lv, mg.nSp, c1 & km, x, i1, c1, nc, dg);
+            t[e0] = r0;
+            if (v1) t[e1] = r1;
         }}
         if (!grid_sync(bar)) return false;
         const MGDeviceLevel& Cv = mg.lev[l + 1];
-        ITEMS(Cv.n, nc) {
-            const int I = i;
-            float acc = 0.f;
+        ITEMS2(Cv.n, nc)
+            float a0 = 0.f, a1 = 0.f;
 #pragma unroll
             for (int q = 0; q < 7; ++q) {
                 float w;
-                const int f = restrict_src(I, Cv.m, q, w);
-                acc += w * ldg2(t + (size_t)f * nc + c);
+                const int f = restrict_src(i0, Cv.m, q, w);
+                a0 += w * ldg2(t + (size_t)f * nc + c0);
             }
-            Cv.B[e] = acc;
+            if (v1) {
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    float w;
+                    const int f = restrict_src(i1, Cv.m, q, w);
+                    a1 += w * ldg2(t + (size_t)f * nc + c1);
+                }
+            }
+            Cv.B[e0] = a0;
+            if (v1) Cv.B[e1] = a1;
         }}
         if (!grid_sync(bar)) return false;
     }
@@ -200,12 +249,20 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
         const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, cur[l]);
         const float* xc = buf(l + 1, cur[l + 1]);
-        ITEMS(Lv.n, nc) {
-            int c0, c1;
-            float w0, w1;
-            prolong_src(i, Lv.m, c0, c1, w0, w1);
-            x[e] = ldg2(x + e) + w0 * ldg2(xc + (size_t)c0 * nc + c) +
-                   w1 * ldg2(xc + (size_t)c1 * nc + c);
+        ITEMS2(Lv.n, nc)
+            int p0, p1, q0 = 0, q1 = 0;
+            float w0, w1, u0 = 0.f, u1 = 0.f;
+            prolong_src(i0, Lv.m, p0, p1, w0, w1);
+            const float z0 = ldg2(x + e0) + w0 * ldg2(xc + (size_t)p0 * nc + c0) +
+                             w1 * ldg2(xc + (size_t)p1 * nc + c0);
+            float z1 = 0.f;
+            if (v1) {
+                prolong_src(i1, Lv.m, q0, q1, u0, u1);
+                z1 = ldg2(x + e1) + u0 * ldg2(xc + (size_t)q0 * nc + c1) +
+                     u1 * ldg2(xc + (size_t)q1 * nc + c1);
+            }
+            x[e0] = z0;
+            if (v1) x[e1] = z1;
         }}
         if (!grid_sync(bar)) return false;
         for (int k = 0; k < mg.nu; ++k)
@@ -275,6 +332,15 @@ __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
         if (i >= a.nRp) continue;                                   \
         const size_t e = ((size_t)r * a.nRp + i) * a.nSp + k;       \
         const size_t em = (size_t)i * nc + col;
+#define NODE_PAIR_LOOP                                              \
+    for (int t = 0; t < kChunk / 16; ++t) {                         \
+        const int ia = chunk * kChunk + ny + 8 * t, ib = ia + kChunk / 2; \
+        if (ia >= a.nRp) break;                                     \
+        const bool vb = ib < a.nRp;                                 \
+        const size_t ea = ((size_t)r * a.nRp + ia) * a.nSp + k;     \
+        const size_t eb = ea + (size_t)(kChunk / 2) * a.nSp;        \
+        const size_t ema = (size_t)ia * nc + col;                   \
+        const size_t emb = ema + (size_t)(kChunk / 2) * nc;
     // ------------------------------------------------------------ init
     UNIT_LOOP
         double pbb = 0.0;
@@ -319,14 +385,27 @@ __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
             double ppap = 0.0;
             if (act) {
                 const T* Pr = a.P + (size_t)r * a.nRp * a.nSp;
-                NODE_LOOP
-                    T y = 0;
+                // nodes ia and ib = ia + kChunk / 2 together, loads before stores
+                NODE_PAIR_LOOP
+                    T ya = 0, yb = 0, pb = 0;
 #pragma unroll
                     for (int dir = 0; dir < 7; ++dir)
-                        y += __ldg(a.coef + ((size_t)dir * a.nRp + i) * a.nSp + k) *
-                             ldg2(Pr + (size_t)nbr(i, dir, a.m, a.nRp) * a.nSp + k);
-                    a.AP[e] = y;
-                    ppap += (double)y * (double)ldg2(a.P + e);
+                        ya += __ldg(a.coef + ((size_t)dir * a.nRp + ia) * a.nSp + k) *
+                              ldg2(Pr + (size_t)nbr(ia, dir, a.m, a.nRp) * a.nSp + k);
+                    const T pa = ldg2(a.P + ea);
+                    if (vb) {
+#pragma unroll
+                        for (int dir = 0; dir < 7; ++dir)
+                            yb += __ldg(a.coef + ((size_t)dir * a.nRp + ib) * a.nSp + k) *
+                                  ldg2(Pr + (size_t)nbr(ib, dir, a.m, a.nRp) * a.nSp + k);
+                        pb = ldg2(a.P + eb);
+                    }
+                    a.AP[ea] = ya;
+                    ppap += (double)ya * (double)pa;
+                    if (vb) {
+                        a.AP[eb] = yb;
+                        ppap += (double)yb * (double)pb;
+                    }
                 }
             }
             col_add(ppap, sh, slot(a, cur, 0), col, act);
@@ -382,8 +461,12 @@ __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
             if (!(ldg2(slot(a, cur, 2) + col) > a.tol2 * ldg2(a.bb + col))) continue;
             const double rzo = ldg2(slot(a, prev, 1) + col);
             const double beta = rzo != 0.0 ? ldg2(slot(a, cur, 1) + col) / rzo : 0.0;
-            NODE_LOOP
-                a.P[e] = static_cast<T>(ldg2(z + em)) + static_cast<T>(beta) * ldg2(a.P + e);
+            NODE_PAIR_LOOP
+                const T na = static_cast<T>(ldg2(z + ema)) + static_cast<T>(beta) * ldg2(a.P + ea);
+                T nb = 0;
+                if (vb) nb = static_cast<T>(ldg2(z + emb)) + static_cast<T>(beta) * ldg2(a.P + eb);
+                a.P[ea] = na;
+                if (vb) a.P[eb] = nb;
             }
         UNIT_END
         if (!grid_sync(a.bar)) return;
@@ -400,6 +483,7 @@ __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
 #undef UNIT_LOOP
 #undef UNIT_END
 #undef NODE_LOOP
+#undef NODE_PAIR_LOOP
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.status->iterations = it;
         a.status->converged = s_stop;

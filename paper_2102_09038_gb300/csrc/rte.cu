@@ -834,9 +834,9 @@ int rte_default_options(rte_options* o) {
     o->mk_route = RTE_MK_EIGEN;
     o->mk_tol = 1e-12;
     o->mk_maxit = 500;
-    o->e0_tol = 0.0;          // 0: per precision (1e-12 FP64, 1e-2 mixed)
+    o->e0_tol = 0.0;          // 0: per precision (1e-12 FP64, 1e-1 mixed)
     o->e0_maxit = 20000;
-    o->coarse_tol = 0.0;      // 0: per precision (1e-12 FP64, 1e-4 mixed)
+    o->coarse_tol = 0.0;      // 0: per precision (1e-12 FP64, 1e-2 mixed)
     o->coarse_maxit = 20000;
     o->max_iter = 200;
     o->max_rhs = 1;
@@ -864,8 +864,8 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     // method solves E_0 and E_c to 1e-12; under the mixed modes' FP64 outer
     // residual (iterative refinement) loose inner solves cost no outer
     // iterations
-    if (!(o.e0_tol > 0)) o.e0_tol = o.precision == RTE_FP64 ? 1e-12 : 1e-2;
-    if (!(o.coarse_tol > 0)) o.coarse_tol = o.precision == RTE_FP64 ? 1e-12 : 1e-4;
+    if (!(o.e0_tol > 0)) o.e0_tol = o.precision == RTE_FP64 ? 1e-12 : 1e-1;
+    if (!(o.coarse_tol > 0)) o.coarse_tol = o.precision == RTE_FP64 ? 1e-12 : 1e-2;
     HostSystem hs;
     RTE_TRY(build_host_system(*prob, o, hs));
     rte_handle* h = new rte_handle();
