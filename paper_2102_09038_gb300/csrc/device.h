@@ -74,7 +74,6 @@ struct DevSystem {
     DevLow lo;                 // mixed-precision copies (null in FP64 mode)
     // E_0 level-0 stencil coefficients per direction, ELL [7][nRp][nSp]
     const double* e0coef;
-    const float* e0coef_f;
     const double* ec_ell;      // E_c in ELL form [7][nRp][dP][dP], blocks transposed
     // digit slices of the constant second operands for the split FP64 GEMM
     int split_S;               // 0: FP64 GEMMs on the FP64 units

@@ -115,21 +115,37 @@ struct E0MG {
     int L, ncols, nSp, nu;
     bool dense;
     const float* cinv;     // [n_c][n_c][nSp]
-    const float* e0s;      // [nSp][6]
+    const float4* w8;      // [nSp][2]: gamma a11, gamma a12, gamma a22, om^x, om^y, m, 0, 0
     MGDeviceLevel lev[kMaxMGLevels];
 };
 
-// per-direction coefficient of stencil direction `dir` at node i
-__device__ __forceinline__ float e0_cf(const MGDeviceLevel& L, int nSp, int dir, int i, int k) {
-    return __ldg(L.cdir + ((size_t)dir * L.n + i) * nSp + k);
+// The E_0 block of direction k is sum_q w_q(k) S_q over the six spatial parts
+// S_q (K11, K12, K22, B_x, B_y, M_t on level 0, their Galerkin products below),
+// so its stencil coefficients are formed on the fly from the level's parts,
+// stored node-major as sv[i][dir][8] (six used), and the direction's weights:
+// the sweeps read 224 bytes per node instead of 28 bytes per (node,
+// direction) pair.
+__device__ __forceinline__ float e0_coef(const float4* sv, float4 wa, float4 wb, int i, int dir) {
+    const float4 a = __ldg(sv + ((size_t)i * 7 + dir) * 2);
+    const float4 b = __ldg(sv + ((size_t)i * 7 + dir) * 2 + 1);
+    return fmaf(wa.x, a.x, fmaf(wa.y, a.y, fmaf(wa.z, a.z, fmaf(wa.w, a.w,
+           fmaf(wb.x, b.x, wb.y * b.y)))));
 }
 
-__device__ __forceinline__ float e0_apply(const MGDeviceLevel& L, int nSp, int k, const float* x,
-                                          int i, int c, int nc, float& dg) {
+// diagonal coefficient of column k at node i
+__device__ __forceinline__ float e0_cf(const MGDeviceLevel& L, const float4* W, int i, int k) {
+    return e0_coef(reinterpret_cast<const float4*>(L.sv), __ldg(W + 2 * k), __ldg(W + 2 * k + 1),
+                   i, 0);
+}
+
+__device__ __forceinline__ float e0_apply(const MGDeviceLevel& L, const float4* W, int k,
+                                          const float* x, int i, int c, int nc, float& dg) {
+    const float4* sv = reinterpret_cast<const float4*>(L.sv);
+    const float4 wa = __ldg(W + 2 * k), wb = __ldg(W + 2 * k + 1);
     float y = 0.f;
 #pragma unroll
     for (int dir = 0; dir < 7; ++dir) {
-        const float cf = e0_cf(L, nSp, dir, i, k);
+        const float cf = e0_coef(sv, wa, wb, i, dir);
         y += cf * ldg2(x + (size_t)nbr(i, dir, L.m, L.n) * nc + c);
         if (dir == 0) dg = cf;
     }
@@ -149,10 +165,10 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
         float* xt = buf(l, cur[l] ^ 1);
         ITEMS2(Lv.n, nc)
             float dg0, dg1 = 1.f, y1 = 0.f, b1 = 0.f, x1 = 0.f;
-            const float y0 = e0_apply(Lv, mg.nSp, c0 & km, x, i0, c0, nc, dg0);
+            const float y0 = e0_apply(Lv, mg.w8, c0 & km, x, i0, c0, nc, dg0);
             const float b0 = ldg2(Lv.B + e0), x0 = ldg2(x + e0);
             if (v1) {
-                y1 = e0_apply(Lv, mg.nSp, c1 & km, x, i1, c1, nc, dg1);
+                y1 = e0_apply(Lv, mg.w8, c1 & km, x, i1, c1, nc, dg1);
                 b1 = ldg2(Lv.B + e1);
                 x1 = ldg2(x + e1);
             }
@@ -166,11 +182,11 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
         const MGDeviceLevel& Lv = mg.lev[l];
         float* x = buf(l, 0);
         ITEMS2(Lv.n, nc)
-            const float b0 = ldg2(Lv.B + e0), d0 = e0_cf(Lv, mg.nSp, 0, i0, c0 & km);
+            const float b0 = ldg2(Lv.B + e0), d0 = e0_cf(Lv, mg.w8, i0, c0 & km);
             float b1 = 0.f, d1 = 1.f;
             if (v1) {
                 b1 = ldg2(Lv.B + e1);
-                d1 = e0_cf(Lv, mg.nSp, 0, i1, c1 & km);
+                d1 = e0_cf(Lv, mg.w8, i1, c1 & km);
             }
             x[e0] = kOmega * __fdividef(b0, d0);
             if (v1) x[e1] = kOmega * __fdividef(b1, d1);
@@ -187,8 +203,8 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
         float* t = buf(l, cur[l] ^ 1);
         ITEMS2(Lv.n, nc)
             float dg, r1 = 0.f;
-            const float r0 = ldg2(Lv.B + e0) - e0_apply(Lv, mg.nSp, c0 & km, x, i0, c0, nc, dg);
-            if (v1) r1 = ldg2(Lv.B + e1) - e0_apply(Lv, mg.nSp, c1 & km, x, i1, c1, nc, dg);
+            const float r0 = ldg2(Lv.B + e0) - e0_apply(Lv, mg.w8, c0 & km, x, i0, c0, nc, dg);
+            if (v1) r1 = ldg2(Lv.B + e1) - e0_apply(Lv, mg.w8, c1 & km, x, i1, c1, nc, dg);
             t[e0] = r0;
             if (v1) t[e1] = r1;
         }}
@@ -277,7 +293,7 @@ template <typename T>
 struct E0Args {
     int nRp, m, nSp, nrhs, ncols, kTiles, chunks, units, maxit;
     double tol2;
-    const T* coef;      // level-0 coefficients [7][nRp][nSp] in the CG precision
+    const T* coef;      // FP64: level-0 coefficients [7][nRp][nSp]; FP32: unused
     const double* B;
     double* X;
     T* R;
@@ -311,6 +327,7 @@ __device__ void col_add(double v, double* sh, double* dst, int col, bool valid) 
 
 template <typename T>
 __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
+    constexpr bool kOnTheFly = sizeof(T) == sizeof(float);
     __shared__ double sh[256];
     __shared__ int s_stop;
     const int kx = threadIdx.x & 31, ny = threadIdx.x >> 5;
@@ -385,18 +402,29 @@ __global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
             double ppap = 0.0;
             if (act) {
                 const T* Pr = a.P + (size_t)r * a.nRp * a.nSp;
+                // FP32: coefficients formed on the fly from the level-0 parts;
+                // FP64: read from the precomputed FP64 stencil
+                float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
+                const float4* sv0 = reinterpret_cast<const float4*>(a.mg.lev[0].sv);
+                if (kOnTheFly) {
+                    wa = __ldg(a.mg.w8 + 2 * k);
+                    wb = __ldg(a.mg.w8 + 2 * k + 1);
+                }
+                auto cf = [&](int i, int dir) -> T {
+                    if (kOnTheFly) return static_cast<T>(e0_coef(sv0, wa, wb, i, dir));
+                    return __ldg(a.coef + ((size_t)dir * a.nRp + i) * a.nSp + k);
+                };
                 // nodes ia and ib = ia + kChunk / 2 together, loads before stores
                 NODE_PAIR_LOOP
                     T ya = 0, yb = 0, pb = 0;
 #pragma unroll
                     for (int dir = 0; dir < 7; ++dir)
-                        ya += __ldg(a.coef + ((size_t)dir * a.nRp + ia) * a.nSp + k) *
-                              ldg2(Pr + (size_t)nbr(ia, dir, a.m, a.nRp) * a.nSp + k);
+                        ya += cf(ia, dir) * ldg2(Pr + (size_t)nbr(ia, dir, a.m, a.nRp) * a.nSp + k);
                     const T pa = ldg2(a.P + ea);
                     if (vb) {
 #pragma unroll
                         for (int dir = 0; dir < 7; ++dir)
-                            yb += __ldg(a.coef + ((size_t)dir * a.nRp + ib) * a.nSp + k) *
+                            yb += cf(ib, dir) *
                                   ldg2(Pr + (size_t)nbr(ib, dir, a.m, a.nRp) * a.nSp + k);
                         pb = ldg2(a.P + eb);
                     }
@@ -919,7 +947,7 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     a.mg = view<E0MG>(d.e0mg);
     a.mg.ncols = ncols;
     a.mg.nSp = d.nSp;
-    a.mg.e0s = d.e0mg.e0s;
+    a.mg.w8 = reinterpret_cast<const float4*>(d.e0mg.w8);
     const void* fn = (const void*)k_e0_pcg<T>;
     const int grid = coop_grid(fn, 256);
     void* args[] = {&a};
@@ -951,7 +979,7 @@ int e0_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nr
 
 int e0_cg_lo(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nrhs,
              double tol, int maxit, void* work, size_t work_bytes, SolveStatus* status_dev) {
-    return e0_pcg_impl<float>(s, d, d.e0coef_f, B, X, nrhs, tol, maxit, work, work_bytes,
+    return e0_pcg_impl<float>(s, d, nullptr, B, X, nrhs, tol, maxit, work, work_bytes,
                               status_dev);
 }
 

@@ -13,9 +13,9 @@ constexpr int kMaxMGLevels = 14;
 
 struct MGDeviceLevel {
     int m = 0, n = 0;
-    const float* val = nullptr;    // E_0: [6][7][n]; E_c: [7][n][d][d], blocks transposed
+    const float* val = nullptr;    // E_c: [7][n][d][d], blocks transposed
     const float* dinv = nullptr;   // E_c: [n][d][d] inverse diagonal blocks, transposed
-    const float* cdir = nullptr;   // E_0: per-direction coefficients [7][n][nSp]
+    const float* sv = nullptr;     // E_0: the six spatial parts, node-major [n][7][8]
     float *X = nullptr, *Xt = nullptr, *B = nullptr;   // work vectors
 };
 
@@ -23,7 +23,7 @@ struct MGDevice {
     int L = 0, nu = 2, cap_cols = 0;
     bool dense = false;
     const float* cinv = nullptr;   // coarsest dense inverse(s)
-    const float* e0s = nullptr;    // E_0 only: per-direction weights [nSp][6]
+    const float* w8 = nullptr;     // E_0 only: per-direction weights [nSp][8], six used
     MGDeviceLevel lev[kMaxMGLevels];
 };
 

@@ -340,10 +340,12 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
         MGDeviceLevel& D = out.lev[l];
         D.m = L.m;
         D.n = (L.m + 1) * (L.m + 1);
-        std::vector<double> ell;
-        RTE_TRY(to_ell(L, mh.slots, bs, ell));
-        transpose_blocks(ell, bs);
-        RTE_TRY(upload(h, &D.val, std::vector<float>(ell.begin(), ell.end())));
+        if (bs > 1) {   // E_c blocks (the E_0 kernels use the node-major parts)
+            std::vector<double> ell;
+            RTE_TRY(to_ell(L, mh.slots, bs, ell));
+            transpose_blocks(ell, bs);
+            RTE_TRY(upload(h, &D.val, std::vector<float>(ell.begin(), ell.end())));
+        }
         if (block_dinv) {
             std::vector<float> di;
             RTE_TRY(block_diag_inverse(L, bs, di));
@@ -376,23 +378,25 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         MGHost mh;
         RTE_TRY(build_hierarchy(hs.m, hs.st, v, 6, 1, kDenseCoarseNodes, mh));
         RTE_TRY(upload_mg(h, mh, cap * hs.nSp, 1, false, d.e0mg));
-        // per-direction FP32 coefficients of every level: cdir[dir][i][k]
+        // the six spatial parts of every level, node-major sv[i][dir][8]
+        // (the kernels form each direction's coefficients from them)
         for (int l = 0; l < d.e0mg.L; ++l) {
             std::vector<double> ell;
             RTE_TRY(to_ell(mh.levels[l], 6, 1, ell));
             const size_t nl = (size_t)(mh.levels[l].m + 1) * (mh.levels[l].m + 1);
-            std::vector<float> cd((size_t)7 * nl * hs.nSp);
-            for (size_t di = 0; di < 7 * nl; ++di)
-                for (int k = 0; k < hs.nSp; ++k) {
-                    double c = 0.0;
-                    for (int q = 0; q < 6; ++q) c += hs.e0s[6 * k + q] * ell[(size_t)q * 7 * nl + di];
-                    cd[di * hs.nSp + k] = (float)c;
-                }
-            RTE_TRY(upload(h, &d.e0mg.lev[l].cdir, cd));
+            std::vector<float> sv(nl * 7 * 8, 0.f);
+            for (size_t i = 0; i < nl; ++i)
+                for (int dir = 0; dir < 7; ++dir)
+                    for (int q = 0; q < 6; ++q)
+                        sv[(i * 7 + dir) * 8 + q] = (float)ell[((size_t)q * 7 + dir) * nl + i];
+            RTE_TRY(upload(h, &d.e0mg.lev[l].sv, sv));
         }
-        const float* e0f = nullptr;
-        RTE_TRY(upload(h, &e0f, std::vector<float>(hs.e0s.begin(), hs.e0s.end())));
-        d.e0mg.e0s = e0f;
+        {
+            std::vector<float> w8((size_t)hs.nSp * 8, 0.f);
+            for (int k = 0; k < hs.nSp; ++k)
+                for (int q = 0; q < 6; ++q) w8[(size_t)k * 8 + q] = (float)hs.e0s[6 * k + q];
+            RTE_TRY(upload(h, &d.e0mg.w8, w8));
+        }
         if (d.e0mg.dense) {
             const int nc = (mh.levels.back().m + 1) * (mh.levels.back().m + 1);
             std::vector<double> all((size_t)nc * nc * hs.nSp), one;
@@ -416,12 +420,9 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         const double* dell = nullptr;
         RTE_TRY(upload(h, &dell, ell6));
         double* c = nullptr;
-        float* cf = nullptr;
         RTE_TRY(dalloc(h, &c, (size_t)7 * hs.nRp * hs.nSp));
-        if (h->mixed) RTE_TRY(dalloc(h, &cf, (size_t)7 * hs.nRp * hs.nSp));
-        e0_coefficients(h->stream, hs.nRp, hs.nSp, dell, d.e0s, c, cf);
+        e0_coefficients(h->stream, hs.nRp, hs.nSp, dell, d.e0s, c, nullptr);
         d.e0coef = c;
-        d.e0coef_f = cf;
     }
     // ------------------------------------------------------------ E_c
     if (d.dP > 0) {
