@@ -87,36 +87,14 @@ __device__ __forceinline__ void prolong_src(int i, int mf, int& c0, int& c1, flo
     for (; e < it_total__; e += it_stride__, i += it_sq__, c += it_sr__,         \
                            (c >= (int)it_nc__ ? (c -= it_nc__, ++i) : 0))
 
-// The same loop taking two items per trip, e0 and e1 = e0 + stride (v1 says
-// whether e1 exists), so that the loads of both are in flight together: a
-// store between two items would otherwise keep the second item's loads
-// behind the first item's store, one memory latency per item.
-#define ITEMS2(n, ncv)                                                          \
-    {                                                                            \
-    const int it_nc__ = (int)(ncv);                                              \
-    const unsigned it_total__ = (unsigned)(n) * (unsigned)it_nc__;               \
-    const unsigned it_stride__ = gridDim.x * blockDim.x;                         \
-    const int it_sq__ = (int)(it_stride__ / (unsigned)it_nc__);                  \
-    const int it_sr__ = (int)(it_stride__ % (unsigned)it_nc__);                  \
-    unsigned e0 = blockIdx.x * blockDim.x + threadIdx.x;                         \
-    int i0 = (int)(e0 / (unsigned)it_nc__), c0 = (int)(e0 % (unsigned)it_nc__);  \
-    int i1 = i0 + it_sq__, c1 = c0 + it_sr__;                                    \
-    if (c1 >= it_nc__) { c1 -= it_nc__; ++i1; }                                  \
-    for (; e0 < it_total__; e0 += 2 * it_stride__,                               \
-         i0 = i1 + it_sq__, c0 = c1 + it_sr__,                                   \
-         (c0 >= it_nc__ ? (c0 -= it_nc__, ++i0) : 0),                            \
-         i1 = i0 + it_sq__, c1 = c0 + it_sr__,                                   \
-         (c1 >= it_nc__ ? (c1 -= it_nc__, ++i1) : 0)) {                          \
-        const unsigned e1 = e0 + it_stride__;                                    \
-        const bool v1 = e1 < it_total__;
-
 // ================================================================ E_0 V-cycle
 struct E0MG {
     int L, ncols, nSp, nu;
     bool dense;
     const float* cinv;     // [n_c][n_c][nSp]
     const float4* w8;      // [nSp][2]: gamma a11, gamma a12, gamma a22, om^x, om^y, m, 0, 0
-    MGDeviceLevel lev[kMaxMGLevels];
+    const float4* wq;      // [6][nSp / 4]: the same weights, direction index fastest
+    const MGDeviceLevel* lev;   // [L], in device memory
 };
 
 // The E_0 block of direction k is sum_q w_q(k) S_q over the six spatial parts
@@ -132,159 +110,245 @@ __device__ __forceinline__ float e0_coef(const float4* sv, float4 wa, float4 wb,
            fmaf(wb.x, b.x, wb.y * b.y)))));
 }
 
-// diagonal coefficient of column k at node i
-__device__ __forceinline__ float e0_cf(const MGDeviceLevel& L, const float4* W, int i, int k) {
-    return e0_coef(reinterpret_cast<const float4*>(L.sv), __ldg(W + 2 * k), __ldg(W + 2 * k + 1),
-                   i, 0);
-}
+// The V-cycle works on quads: a thread takes four consecutive columns (four
+// directions) of one node, so the node's parts are read once for four
+// columns and every vector access is one 16-byte load or store.  The
+// columns of a level are ncols = nrhs n_S^+, a multiple of 4.
+struct Quad {
+    float4 w[6];   // weights of the quad's four directions, w[q].x for the first
+    int k4 = -1;   // which quad of directions w holds
+    __device__ void load(const float4* wq, int nq_dir, int k4new) {
+        if (k4new == k4) return;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) w[q] = __ldg(wq + (size_t)q * nq_dir + k4new);
+        k4 = k4new;
+    }
+    // the four coefficients of stencil direction dir at node i
+    __device__ __forceinline__ float4 coef(const float4* sv, int i, int dir) const {
+        const float4 a = __ldg(sv + ((size_t)i * 7 + dir) * 2);
+        const float2 b = __ldg(reinterpret_cast<const float2*>(sv + ((size_t)i * 7 + dir) * 2 + 1));
+        float4 c;
+        c.x = fmaf(w[0].x, a.x, fmaf(w[1].x, a.y, fmaf(w[2].x, a.z, fmaf(w[3].x, a.w,
+              fmaf(w[4].x, b.x, w[5].x * b.y)))));
+        c.y = fmaf(w[0].y, a.x, fmaf(w[1].y, a.y, fmaf(w[2].y, a.z, fmaf(w[3].y, a.w,
+              fmaf(w[4].y, b.x, w[5].y * b.y)))));
+        c.z = fmaf(w[0].z, a.x, fmaf(w[1].z, a.y, fmaf(w[2].z, a.z, fmaf(w[3].z, a.w,
+              fmaf(w[4].z, b.x, w[5].z * b.y)))));
+        c.w = fmaf(w[0].w, a.x, fmaf(w[1].w, a.y, fmaf(w[2].w, a.z, fmaf(w[3].w, a.w,
+              fmaf(w[4].w, b.x, w[5].w * b.y)))));
+        return c;
+    }
+};
 
-__device__ __forceinline__ float e0_apply(const MGDeviceLevel& L, const float4* W, int k,
-                                          const float* x, int i, int c, int nc, float& dg) {
+__device__ __forceinline__ float4 ld4(const float4* p) { return __ldcg(p); }
+
+// y = (E_0 block) x for the quad (i, p); dg = its diagonal
+__device__ __forceinline__ float4 e0_apply4(const MGDeviceLevel& L, const Quad& qd,
+                                            const float4* x4, int i, int p, int nq, float4& dg) {
     const float4* sv = reinterpret_cast<const float4*>(L.sv);
-    const float4 wa = __ldg(W + 2 * k), wb = __ldg(W + 2 * k + 1);
-    float y = 0.f;
+    // the seven neighbour loads first (long latency), then the coefficients
+    // one direction at a time (L1 hits), to bound the live registers
+    float4 xv[7];
+#pragma unroll
+    for (int dir = 0; dir < 7; ++dir) xv[dir] = ld4(x4 + (size_t)nbr(i, dir, L.m, L.n) * nq + p);
+    float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int dir = 0; dir < 7; ++dir) {
-        const float cf = e0_coef(sv, wa, wb, i, dir);
-        y += cf * ldg2(x + (size_t)nbr(i, dir, L.m, L.n) * nc + c);
+        asm volatile("" ::: "memory");
+        const float4 cf = qd.coef(sv, i, dir);
+        y.x = fmaf(cf.x, xv[dir].x, y.x);
+        y.y = fmaf(cf.y, xv[dir].y, y.y);
+        y.z = fmaf(cf.z, xv[dir].z, y.z);
+        y.w = fmaf(cf.w, xv[dir].w, y.w);
         if (dir == 0) dg = cf;
     }
     return y;
 }
 
+// Grid-stride loop over the quads (i, p) of an n-node level with nq quads
+// per node; o4 = the quad's float4 offset.  Needs nq, nqd (direction quads)
+// and wq in scope.
+#define QUADS(n, UNROLL)                                                        \
+    {                                                                            \
+    const int kq__ = nqd - 1;   /* n_S^+ is a power of two */                    \
+    const unsigned qd_total__ = (unsigned)(n) * (unsigned)nq;                    \
+    const unsigned qd_stride__ = gridDim.x * blockDim.x;                         \
+    const int qd_sq__ = (int)(qd_stride__ / (unsigned)nq);                       \
+    const int qd_sr__ = (int)(qd_stride__ % (unsigned)nq);                       \
+    unsigned qe__ = blockIdx.x * blockDim.x + threadIdx.x;                       \
+    int i = (int)(qe__ / (unsigned)nq), p = (int)(qe__ % (unsigned)nq);          \
+    _Pragma(UNROLL)                                                              \
+    for (; qe__ < qd_total__; qe__ += qd_stride__, i += qd_sq__, p += qd_sr__,   \
+         (p >= nq ? (p -= nq, ++i) : 0)) {                                       \
+        const size_t o4 = (size_t)i * nq + p;                                    \
+        Quad qd;                                                                 \
+        qd.load(wq, nqd, p & kq__);
+
+__device__ __forceinline__ float4 jac4(float4 x, float4 b, float4 y, float4 d) {
+    return make_float4(x.x + kOmega * __fdividef(b.x - y.x, d.x),
+                       x.y + kOmega * __fdividef(b.y - y.y, d.y),
+                       x.z + kOmega * __fdividef(b.z - y.z, d.z),
+                       x.w + kOmega * __fdividef(b.w - y.w, d.w));
+}
+
+// The V-cycle's phases, each compiled on its own (not inlined) so that its
+// registers are allocated for its own loop alone.
+__device__ __noinline__ void e0_first(const MGDeviceLevel Lv, const float4* __restrict__ wq,
+                                      int nq, int nqd, float4* __restrict__ x) {
+    const float4* __restrict__ B = reinterpret_cast<const float4*>(Lv.B);
+    const float4* __restrict__ sv = reinterpret_cast<const float4*>(Lv.sv);
+    QUADS(Lv.n, "unroll 2")
+        const float4 d = qd.coef(sv, i, 0), b = ld4(B + o4);
+        x[o4] = make_float4(kOmega * __fdividef(b.x, d.x), kOmega * __fdividef(b.y, d.y),
+                            kOmega * __fdividef(b.z, d.z), kOmega * __fdividef(b.w, d.w));
+    }}
+}
+
+__device__ __noinline__ void e0_jacobi(const MGDeviceLevel Lv, const float4* __restrict__ wq,
+                                       int nq, int nqd, const float4* __restrict__ x,
+                                       float4* __restrict__ xt) {
+    const float4* __restrict__ B = reinterpret_cast<const float4*>(Lv.B);
+    QUADS(Lv.n, "unroll 2")
+        float4 dg;
+        const float4 y = e0_apply4(Lv, qd, x, i, p, nq, dg);
+        xt[o4] = jac4(ld4(x + o4), ld4(B + o4), y, dg);
+    }}
+}
+
+__device__ __noinline__ void e0_residual(const MGDeviceLevel Lv, const float4* __restrict__ wq,
+                                         int nq, int nqd, const float4* __restrict__ x,
+                                         float4* __restrict__ t) {
+    const float4* __restrict__ B = reinterpret_cast<const float4*>(Lv.B);
+    QUADS(Lv.n, "unroll 2")
+        float4 dg;
+        const float4 y = e0_apply4(Lv, qd, x, i, p, nq, dg);
+        const float4 b = ld4(B + o4);
+        t[o4] = make_float4(b.x - y.x, b.y - y.y, b.z - y.z, b.w - y.w);
+    }}
+}
+
+__device__ __noinline__ void e0_restrict(const MGDeviceLevel Cv, int nq,
+                                         const float4* __restrict__ t) {
+    float4* __restrict__ CB = reinterpret_cast<float4*>(Cv.B);
+    const unsigned total = (unsigned)Cv.n * (unsigned)nq;
+#pragma unroll 2
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int i = (int)(e / (unsigned)nq), p = (int)(e % (unsigned)nq);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            float w;
+            const int f = restrict_src(i, Cv.m, q, w);
+            const float4 v = ld4(t + (size_t)f * nq + p);
+            acc.x = fmaf(w, v.x, acc.x);
+            acc.y = fmaf(w, v.y, acc.y);
+            acc.z = fmaf(w, v.z, acc.z);
+            acc.w = fmaf(w, v.w, acc.w);
+        }
+        CB[e] = acc;
+    }
+}
+
+__device__ __noinline__ void e0_prolong(const MGDeviceLevel Lv, int nq, float4* __restrict__ x,
+                                        const float4* __restrict__ xc) {
+    const unsigned total = (unsigned)Lv.n * (unsigned)nq;
+#pragma unroll 2
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += gridDim.x * blockDim.x) {
+        const int i = (int)(e / (unsigned)nq), p = (int)(e % (unsigned)nq);
+        int c0, c1;
+        float w0, w1;
+        prolong_src(i, Lv.m, c0, c1, w0, w1);
+        const float4 a = ld4(xc + (size_t)c0 * nq + p), b = ld4(xc + (size_t)c1 * nq + p);
+        const float4 v = ld4(x + e);
+        x[e] = make_float4(v.x + w0 * a.x + w1 * b.x, v.y + w0 * a.y + w1 * b.y,
+                           v.z + w0 * a.z + w1 * b.z, v.w + w0 * a.w + w1 * b.w);
+    }
+}
+
+// coarsest level: x = (dense inverse of each direction block) B
+__device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* cinv, int nSp, int nc,
+                                      float* x) {
+    const int km = nSp - 1;
+    ITEMS(Lv.n, nc) {
+        // cinv is [i][j][direction], so a warp's lanes (consecutive
+        // columns) read consecutive words
+        const int k = c & km;
+        const float* row = cinv + (size_t)i * Lv.n * nSp + k;
+        const float* bc = Lv.B + c;
+        // 16 independent load pairs in flight per trip
+        constexpr int U = 16;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        int j = 0;
+        for (; j + U <= Lv.n; j += U) {
+            float rv[U], bv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                rv[u] = __ldg(row + (size_t)(j + u) * nSp);
+                bv[u] = ldg2(bc + (size_t)(j + u) * nc);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc[u & 3] += rv[u] * bv[u];
+        }
+        for (; j < Lv.n; ++j) acc[0] += __ldg(row + (size_t)j * nSp) * ldg2(bc + (size_t)j * nc);
+        x[e] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+    }}
+}
+
 // One symmetric V-cycle on B_0; returns the buffer holding z on level 0.
 __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
-    const int nc = mg.ncols;
+    const int nc = mg.ncols, nq = nc >> 2, nqd = mg.nSp >> 2;
     int cur[kMaxMGLevels];
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
-    auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
-    const int km = mg.nSp - 1;   // n_S^+ is a power of two
-    auto jacobi = [&](int l) -> bool {
-        const MGDeviceLevel& Lv = mg.lev[l];
-        const float* x = buf(l, cur[l]);
-        float* xt = buf(l, cur[l] ^ 1);
-        ITEMS2(Lv.n, nc)
-            float dg0, dg1 = 1.f, y1 = 0.f, b1 = 0.f, x1 = 0.f;
-            const float y0 = e0_apply(Lv, mg.w8, c0 & km, x, i0, c0, nc, dg0);
-            const float b0 = ldg2(Lv.B + e0), x0 = ldg2(x + e0);
-            if (v1) {
-                y1 = e0_apply(Lv, mg.w8, c1 & km, x, i1, c1, nc, dg1);
-                b1 = ldg2(Lv.B + e1);
-                x1 = ldg2(x + e1);
-            }
-            xt[e0] = x0 + kOmega * __fdividef(b0 - y0, dg0);
-            if (v1) xt[e1] = x1 + kOmega * __fdividef(b1 - y1, dg1);
-        }}
-        cur[l] ^= 1;
-        return grid_sync(bar);
-    };
-    auto first = [&](int l) -> bool {
-        const MGDeviceLevel& Lv = mg.lev[l];
-        float* x = buf(l, 0);
-        ITEMS2(Lv.n, nc)
-            const float b0 = ldg2(Lv.B + e0), d0 = e0_cf(Lv, mg.w8, i0, c0 & km);
-            float b1 = 0.f, d1 = 1.f;
-            if (v1) {
-                b1 = ldg2(Lv.B + e1);
-                d1 = e0_cf(Lv, mg.w8, i1, c1 & km);
-            }
-            x[e0] = kOmega * __fdividef(b0, d0);
-            if (v1) x[e1] = kOmega * __fdividef(b1, d1);
-        }}
-        cur[l] = 0;
-        return grid_sync(bar);
+    auto buf4 = [&](int l, int which) {
+        return reinterpret_cast<float4*>(which ? mg.lev[l].Xt : mg.lev[l].X);
     };
     for (int l = 0; l + 1 < mg.L; ++l) {
-        const MGDeviceLevel& Lv = mg.lev[l];
-        if (!first(l)) return false;
-        for (int k = 1; k < mg.nu; ++k)
-            if (!jacobi(l)) return false;
-        const float* x = buf(l, cur[l]);
-        float* t = buf(l, cur[l] ^ 1);
-        ITEMS2(Lv.n, nc)
-            float dg, r1 = 0.f;
-            const float r0 = ldg2(Lv.B + e0) - e0_apply(Lv, mg.w8, c0 & km, x, i0, c0, nc, dg);
-            if (v1) r1 = ldg2(Lv.B + e1) - e0_apply(Lv, mg.w8, c1 & km, x, i1, c1, nc, dg);
-            t[e0] = r0;
-            if (v1) t[e1] = r1;
-        }}
+        const MGDeviceLevel Lv = mg.lev[l];
+        e0_first(Lv, mg.wq, nq, nqd, buf4(l, 0));
+        cur[l] = 0;
         if (!grid_sync(bar)) return false;
-        const MGDeviceLevel& Cv = mg.lev[l + 1];
-        ITEMS2(Cv.n, nc)
-            float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                float w;
-                const int f = restrict_src(i0, Cv.m, q, w);
-                a0 += w * ldg2(t + (size_t)f * nc + c0);
-            }
-            if (v1) {
-#pragma unroll
-                for (int q = 0; q < 7; ++q) {
-                    float w;
-                    const int f = restrict_src(i1, Cv.m, q, w);
-                    a1 += w * ldg2(t + (size_t)f * nc + c1);
-                }
-            }
-            Cv.B[e0] = a0;
-            if (v1) Cv.B[e1] = a1;
-        }}
+        for (int k = 1; k < mg.nu; ++k) {
+            e0_jacobi(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
+            cur[l] ^= 1;
+            if (!grid_sync(bar)) return false;
+        }
+        float4* t = buf4(l, cur[l] ^ 1);
+        e0_residual(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), t);
+        if (!grid_sync(bar)) return false;
+        e0_restrict(mg.lev[l + 1], nq, t);
         if (!grid_sync(bar)) return false;
     }
     {
         const int l = mg.L - 1;
-        const MGDeviceLevel& Lv = mg.lev[l];
+        const MGDeviceLevel Lv = mg.lev[l];
         if (mg.dense) {
-            float* x = buf(l, 0);
-            ITEMS(Lv.n, nc) {
-                // cinv is [i][j][direction], so a warp's lanes (consecutive
-                // columns) read consecutive words
-                const int k = c % mg.nSp;
-                const float* row = mg.cinv + (size_t)i * Lv.n * mg.nSp + k;
-                const float* bc = Lv.B + c;
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                int j = 0;
-                for (; j + 4 <= Lv.n; j += 4) {
-                    a0 += __ldg(row + (size_t)j * mg.nSp) * ldg2(bc + (size_t)j * nc);
-                    a1 += __ldg(row + (size_t)(j + 1) * mg.nSp) * ldg2(bc + (size_t)(j + 1) * nc);
-                    a2 += __ldg(row + (size_t)(j + 2) * mg.nSp) * ldg2(bc + (size_t)(j + 2) * nc);
-                    a3 += __ldg(row + (size_t)(j + 3) * mg.nSp) * ldg2(bc + (size_t)(j + 3) * nc);
-                }
-                for (; j < Lv.n; ++j) a0 += __ldg(row + (size_t)j * mg.nSp) * ldg2(bc + (size_t)j * nc);
-                x[e] = (a0 + a1) + (a2 + a3);
-            }}
+            e0_dense(Lv, mg.cinv, mg.nSp, nc, reinterpret_cast<float*>(buf4(l, 0)));
             cur[l] = 0;
             if (!grid_sync(bar)) return false;
         } else {
-            if (!first(l)) return false;
-            for (int k = 1; k < kCoarseSweeps; ++k)
-                if (!jacobi(l)) return false;
+            e0_first(Lv, mg.wq, nq, nqd, buf4(l, 0));
+            cur[l] = 0;
+            if (!grid_sync(bar)) return false;
+            for (int k = 1; k < kCoarseSweeps; ++k) {
+                e0_jacobi(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
+                cur[l] ^= 1;
+                if (!grid_sync(bar)) return false;
+            }
         }
     }
     for (int l = mg.L - 2; l >= 0; --l) {
-        const MGDeviceLevel& Lv = mg.lev[l];
-        float* x = buf(l, cur[l]);
-        const float* xc = buf(l + 1, cur[l + 1]);
-        ITEMS2(Lv.n, nc)
-            int p0, p1, q0 = 0, q1 = 0;
-            float w0, w1, u0 = 0.f, u1 = 0.f;
-            prolong_src(i0, Lv.m, p0, p1, w0, w1);
-            const float z0 = ldg2(x + e0) + w0 * ldg2(xc + (size_t)p0 * nc + c0) +
-                             w1 * ldg2(xc + (size_t)p1 * nc + c0);
-            float z1 = 0.f;
-            if (v1) {
-                prolong_src(i1, Lv.m, q0, q1, u0, u1);
-                z1 = ldg2(x + e1) + u0 * ldg2(xc + (size_t)q0 * nc + c1) +
-                     u1 * ldg2(xc + (size_t)q1 * nc + c1);
-            }
-            x[e0] = z0;
-            if (v1) x[e1] = z1;
-        }}
+        const MGDeviceLevel Lv = mg.lev[l];
+        e0_prolong(Lv, nq, buf4(l, cur[l]), buf4(l + 1, cur[l + 1]));
         if (!grid_sync(bar)) return false;
-        for (int k = 0; k < mg.nu; ++k)
-            if (!jacobi(l)) return false;
+        for (int k = 0; k < mg.nu; ++k) {
+            e0_jacobi(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
+            cur[l] ^= 1;
+            if (!grid_sync(bar)) return false;
+        }
     }
-    z = buf(0, cur[0]);
+    z = reinterpret_cast<float*>(buf4(0, cur[0]));
     return true;
 }
 
@@ -326,7 +390,7 @@ __device__ void col_add(double v, double* sh, double* dst, int col, bool valid) 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_e0_pcg(E0Args<T> a) {
+__global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
     constexpr bool kOnTheFly = sizeof(T) == sizeof(float);
     __shared__ double sh[256];
     __shared__ int s_stop;
@@ -527,7 +591,7 @@ struct EcMG {
     int L, nrhs, d, nu, G;
     bool dense;
     const float* cinv;     // [(n_c d)][(n_c d)]
-    MGDeviceLevel lev[kMaxMGLevels];
+    const MGDeviceLevel* lev;   // [L], in device memory
 };
 
 // Loop over the (rhs, node) items of an array of nn nodes.  All lanes of a
@@ -633,7 +697,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
     auto jacobi = [&](int l) -> bool {
-        const MGDeviceLevel& Lv = mg.lev[l];
+        const MGDeviceLevel Lv = mg.lev[l];
         const float* x = buf(l, cur[l]);
         float* xt = buf(l, cur[l] ^ 1);
         GROUP_LOOP(Lv.n)
@@ -647,7 +711,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         return grid_sync(bar);
     };
     auto first = [&](int l) -> bool {
-        const MGDeviceLevel& Lv = mg.lev[l];
+        const MGDeviceLevel Lv = mg.lev[l];
         float* x = buf(l, 0);
         GROUP_LOOP(Lv.n)
             const bool act = ok && gl < d;
@@ -659,7 +723,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         return grid_sync(bar);
     };
     for (int l = 0; l + 1 < mg.L; ++l) {
-        const MGDeviceLevel& Lv = mg.lev[l];
+        const MGDeviceLevel Lv = mg.lev[l];
         if (!first(l)) return false;
         for (int k = 1; k < mg.nu; ++k)
             if (!jacobi(l)) return false;
@@ -671,7 +735,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
             if (act) t[base + gl] = ldg2(Lv.B + base + gl) - y;
         }}
         if (!grid_sync(bar)) return false;
-        const MGDeviceLevel& Cv = mg.lev[l + 1];
+        const MGDeviceLevel Cv = mg.lev[l + 1];
         GROUP_LOOP(Cv.n)
             if (ok && gl < d) {
                 float acc = 0.f;
@@ -688,7 +752,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
     }
     {
         const int l = mg.L - 1;
-        const MGDeviceLevel& Lv = mg.lev[l];
+        const MGDeviceLevel Lv = mg.lev[l];
         if (mg.dense) {
             float* x = buf(l, 0);
             const int N = Lv.n * d;
@@ -699,14 +763,22 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
                 const int r = (int)(w / (unsigned)N), q = (int)(w % (unsigned)N);
                 const float* row = mg.cinv + (size_t)q * N;
                 const float* b = Lv.B + (size_t)r * N;
-                float acc = 0.f, acc2 = 0.f;
+                // 6 independent load pairs in flight per lane and trip
+                constexpr int U = 6;
+                float a4[4] = {0.f, 0.f, 0.f, 0.f};
                 int j = lane;
-                for (; j + 32 < N; j += 64) {
-                    acc += __ldg(row + j) * ldg2(b + j);
-                    acc2 += __ldg(row + j + 32) * ldg2(b + j + 32);
+                for (; j + 32 * (U - 1) < N; j += 32 * U) {
+                    float rv[U], bv[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        rv[u] = __ldg(row + j + 32 * u);
+                        bv[u] = ldg2(b + j + 32 * u);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) a4[u % 4] += rv[u] * bv[u];
                 }
-                if (j < N) acc += __ldg(row + j) * ldg2(b + j);
-                acc += acc2;
+                for (; j < N; j += 32) a4[0] += __ldg(row + j) * ldg2(b + j);
+                float acc = (a4[0] + a4[1]) + (a4[2] + a4[3]);
                 for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
                 if (lane == 0) x[(size_t)r * N + q] = acc;
             }
@@ -719,7 +791,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         }
     }
     for (int l = mg.L - 2; l >= 0; --l) {
-        const MGDeviceLevel& Lv = mg.lev[l];
+        const MGDeviceLevel Lv = mg.lev[l];
         float* x = buf(l, cur[l]);
         const float* xc = buf(l + 1, cur[l + 1]);
         const int ncn = mg.lev[l + 1].n;
@@ -892,7 +964,7 @@ V view(const MGDevice& m) {
     g.nu = m.nu;
     g.dense = m.dense;
     g.cinv = m.cinv;
-    for (int l = 0; l < m.L; ++l) g.lev[l] = m.lev[l];
+    g.lev = m.dev_lev;
     return g;
 }
 
@@ -948,6 +1020,7 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     a.mg.ncols = ncols;
     a.mg.nSp = d.nSp;
     a.mg.w8 = reinterpret_cast<const float4*>(d.e0mg.w8);
+    a.mg.wq = reinterpret_cast<const float4*>(d.e0mg.wq);
     const void* fn = (const void*)k_e0_pcg<T>;
     const int grid = coop_grid(fn, 256);
     void* args[] = {&a};

@@ -24,7 +24,9 @@ struct MGDevice {
     bool dense = false;
     const float* cinv = nullptr;   // coarsest dense inverse(s)
     const float* w8 = nullptr;     // E_0 only: per-direction weights [nSp][8], six used
+    const float* wq = nullptr;     // E_0 only: the same weights [6][nSp]
     MGDeviceLevel lev[kMaxMGLevels];
+    const MGDeviceLevel* dev_lev = nullptr;   // copy of lev[0 .. L) in device memory
 };
 
 }  // namespace rte

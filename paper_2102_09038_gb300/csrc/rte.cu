@@ -396,6 +396,10 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
             for (int k = 0; k < hs.nSp; ++k)
                 for (int q = 0; q < 6; ++q) w8[(size_t)k * 8 + q] = (float)hs.e0s[6 * k + q];
             RTE_TRY(upload(h, &d.e0mg.w8, w8));
+            std::vector<float> wq((size_t)6 * hs.nSp);
+            for (int q = 0; q < 6; ++q)
+                for (int k = 0; k < hs.nSp; ++k) wq[(size_t)q * hs.nSp + k] = (float)hs.e0s[6 * k + q];
+            RTE_TRY(upload(h, &d.e0mg.wq, wq));
         }
         if (d.e0mg.dense) {
             const int nc = (mh.levels.back().m + 1) * (mh.levels.back().m + 1);
@@ -442,6 +446,13 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         transpose_blocks(ell, d.dP);
         RTE_TRY(upload(h, &d.ec_ell, ell));
     }
+    // the kernels index the level descriptors at run time: keep them in
+    // device memory rather than in the (then locally copied) kernel argument
+    RTE_TRY(upload(h, &d.e0mg.dev_lev,
+                   std::vector<MGDeviceLevel>(d.e0mg.lev, d.e0mg.lev + d.e0mg.L)));
+    if (d.dP > 0)
+        RTE_TRY(upload(h, &d.ecmg.dev_lev,
+                       std::vector<MGDeviceLevel>(d.ecmg.lev, d.ecmg.lev + d.ecmg.L)));
     return RTE_OK;
 }
 
@@ -1280,6 +1291,22 @@ int rte_operator(rte_handle* h, int op, const double* in, double* out, int nrhs)
     }
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
+}
+
+int rte_odd(rte_handle* h, const double* u_plus, const double* l_minus, double* u_minus,
+            int nrhs) {
+    if (!h || !u_plus || !u_minus || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
+    RTE_TRY(ensure_workspace(h, nrhs));
+    const DevSystem& d = h->d;
+    cudaStream_t s = h->stream;
+    const size_t len = (size_t)d.nRm * d.nSm;
+    apply_A(s, d, u_plus, h->z1, nrhs);                                   // z1 = A u^+
+    axpby_per_rhs(s, l_minus, h->z1, len, nrhs, nullptr, 1.0, nullptr, -1.0);   // l^- - z1
+    RTE_TRY(mk_inv(h, h->z1, h->z2, nrhs));
+    RTE_CUDA_TRY(cudaMemcpyAsync(u_minus, h->z2, sizeof(double) * len * nrhs,
+                                 cudaMemcpyDeviceToDevice, s));
+    RTE_CUDA_TRY(cudaGetLastError());
+    return tc_gemm_error(s);
 }
 
 int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
