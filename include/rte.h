@@ -153,6 +153,16 @@ int rte_precond(rte_handle* h, const double* r, double* s, int nrhs,
 int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
               rte_stats* stats);
 
+/* The odd part of the solution from the even part: the second block row of
+ * the mixed system (eq. mixed_discrete), A u^+ + (M^- - K^-) u^- = l^-, so
+ * u^- = (M^- - K^-)^{-1} (l^- - A u^+) (Section 2.4).  u_plus: nrhs x n_R^+
+ * x n_S^+; l_minus: nrhs x n_R^- x n_S^- or NULL for l^- = 0 (isotropic
+ * source, vacuum inflow); u_minus: nrhs x n_R^- x n_S^-, odd index 3k + i.
+ * Device arrays owned by the caller.  FP64 in every mode (the FP64-accurate
+ * (M^- - K^-)^{-1} of the outer residual). */
+int rte_odd(rte_handle* h, const double* u_plus, const double* l_minus, double* u_minus,
+            int nrhs);
+
 /* Individual steps of the iteration, for testing and profiling (device
  * vectors, sizes as in the header comment):
  *  RTE_OP_A          odd  <- even : A x = sum_n A_n (x) D_n     (eq. AR)

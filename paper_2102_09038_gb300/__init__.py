@@ -92,6 +92,7 @@ def load(path=LIB_PATH):
     lib.rte_precond.argtypes = [P, P, P, I, I]
     lib.rte_solve.argtypes = [P, P, P, I, D, ctypes.POINTER(_Stats)]
     lib.rte_operator.argtypes = [P, I, P, P, I]
+    lib.rte_odd.argtypes = [P, P, P, P, I]
     lib.rte_export.argtypes = [P, I, ctypes.POINTER(D), ctypes.c_size_t]
     lib.rte_timing_enable.argtypes = [P, I]
     lib.rte_timing_read.argtypes = [P, ctypes.POINTER(ctypes.c_char_p),
@@ -370,6 +371,17 @@ class Solver:
     def operator(self, name, x, out):
         _check(_lib.rte_operator(self._h, OPS[name], self._vec(x),
                                  self._vec(out), x.shape[0]))
+        return out
+
+    def odd(self, u_plus, l_minus=None):
+        """u^- = (M^- - K^-)^{-1} (l^- - A u^+), the odd part of the solution
+        (rte_odd); l_minus None means l^- = 0."""
+        import torch
+        nrhs = u_plus.shape[0]
+        out = torch.empty((nrhs, self.n_cells, self.n_odd), dtype=torch.float64,
+                          device=u_plus.device)
+        lm = self._vec(l_minus) if l_minus is not None else None
+        _check(_lib.rte_odd(self._h, self._vec(u_plus), lm, self._vec(out), nrhs))
         return out
 
     def export(self, name):

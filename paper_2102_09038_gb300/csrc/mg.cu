@@ -370,7 +370,7 @@ struct E0Args {
     E0MG mg;
 };
 
-constexpr int kChunk = 64;   // nodes per work unit (8 rows x 8 passes)
+constexpr int kChunk = 128;  // nodes per work unit (8 rows x 16 passes)
 
 template <typename T>
 __device__ __forceinline__ double* slot(const E0Args<T>& a, int s, int q) {
@@ -419,19 +419,39 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
         if (ia >= a.nRp) break;                                     \
         const bool vb = ib < a.nRp;                                 \
         const size_t ea = ((size_t)r * a.nRp + ia) * a.nSp + k;     \
-        const size_t eb = ea + (size_t)(kChunk / 2) * a.nSp;        \
-        const size_t ema = (size_t)ia * nc + col;                   \
-        const size_t emb = ema + (size_t)(kChunk / 2) * nc;
+        const size_t eb = ea + (size_t)(kChunk / 2) * a.nSp;
+// Four nodes per trip (i0 + 0, 32, 64, 96 of the unit's rows): every load of
+// the four is issued before the first store.
+#define NODE4_LOOP                                                  \
+    for (int t = 0; t < kChunk / 32; ++t) {                         \
+        const int i0 = chunk * kChunk + ny + 8 * t;                 \
+        if (i0 >= a.nRp) break;                                     \
+        int iv[4];                                                  \
+        bool vv[4];                                                 \
+        size_t ev[4], emv[4];                                       \
+        _Pragma("unroll") for (int q = 0; q < 4; ++q) {             \
+            iv[q] = i0 + q * (kChunk / 4);                          \
+            vv[q] = iv[q] < a.nRp;                                  \
+            ev[q] = ((size_t)r * a.nRp + iv[q]) * a.nSp + k;        \
+            emv[q] = (size_t)iv[q] * nc + col;                      \
+        }
     // ------------------------------------------------------------ init
     UNIT_LOOP
         double pbb = 0.0;
         if (kv) {
-            NODE_LOOP
-                const T b = static_cast<T>(a.B[e]);
-                a.X[e] = 0.0;
-                a.R[e] = b;
-                B0[em] = static_cast<float>(b);
-                pbb += (double)b * (double)b;
+            NODE4_LOOP
+                T bv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vv[q]) bv[q] = static_cast<T>(a.B[ev[q]]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vv[q]) {
+                        a.X[ev[q]] = 0.0;
+                        a.R[ev[q]] = bv[q];
+                        B0[emv[q]] = static_cast<float>(bv[q]);
+                        pbb += (double)bv[q] * (double)bv[q];
+                    }
             }
         }
         col_add(pbb, sh, a.bb, col, kv);
@@ -442,10 +462,20 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
     UNIT_LOOP
         double prz = 0.0;
         if (kv) {
-            NODE_LOOP
-                const T zv = static_cast<T>(ldg2(z + em));
-                a.P[e] = zv;
-                prz += (double)ldg2(a.R + e) * (double)zv;
+            NODE4_LOOP
+                T zv[4], rv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vv[q]) {
+                        zv[q] = static_cast<T>(ldg2(z + emv[q]));
+                        rv[q] = ldg2(a.R + ev[q]);
+                    }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vv[q]) {
+                        a.P[ev[q]] = zv[q];
+                        prz += (double)rv[q] * (double)zv[q];
+                    }
             }
         }
         col_add(prz, sh, slot(a, 2, 1), col, kv);
@@ -510,15 +540,31 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
             if (kv) {
                 const double pap = ldg2(slot(a, cur, 0) + col);
                 const double alpha = (act && pap != 0.0) ? ldg2(slot(a, prev, 1) + col) / pap : 0.0;
-                NODE_LOOP
+                NODE4_LOOP
                     if (act) {
-                        a.X[e] += alpha * (double)ldg2(a.P + e);
-                        const T rv = ldg2(a.R + e) - static_cast<T>(alpha) * ldg2(a.AP + e);
-                        a.R[e] = rv;
-                        prr += (double)rv * (double)rv;
-                        B0[em] = static_cast<float>(rv);
+                        double xo[4];
+                        T pv[4], rv[4], apv[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (vv[q]) {
+                                xo[q] = ldg2(a.X + ev[q]);
+                                pv[q] = ldg2(a.P + ev[q]);
+                                rv[q] = ldg2(a.R + ev[q]);
+                                apv[q] = ldg2(a.AP + ev[q]);
+                            }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (vv[q]) {
+                                a.X[ev[q]] = xo[q] + alpha * (double)pv[q];
+                                const T rn = rv[q] - static_cast<T>(alpha) * apv[q];
+                                a.R[ev[q]] = rn;
+                                prr += (double)rn * (double)rn;
+                                B0[emv[q]] = static_cast<float>(rn);
+                            }
                     } else {
-                        B0[em] = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (vv[q]) B0[emv[q]] = 0.f;
                     }
                 }
             }
@@ -553,12 +599,16 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
             if (!(ldg2(slot(a, cur, 2) + col) > a.tol2 * ldg2(a.bb + col))) continue;
             const double rzo = ldg2(slot(a, prev, 1) + col);
             const double beta = rzo != 0.0 ? ldg2(slot(a, cur, 1) + col) / rzo : 0.0;
-            NODE_PAIR_LOOP
-                const T na = static_cast<T>(ldg2(z + ema)) + static_cast<T>(beta) * ldg2(a.P + ea);
-                T nb = 0;
-                if (vb) nb = static_cast<T>(ldg2(z + emb)) + static_cast<T>(beta) * ldg2(a.P + eb);
-                a.P[ea] = na;
-                if (vb) a.P[eb] = nb;
+            NODE4_LOOP
+                T nv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vv[q])
+                        nv[q] = static_cast<T>(ldg2(z + emv[q])) +
+                                static_cast<T>(beta) * ldg2(a.P + ev[q]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (vv[q]) a.P[ev[q]] = nv[q];
             }
         UNIT_END
         if (!grid_sync(a.bar)) return;
@@ -576,6 +626,7 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
 #undef UNIT_END
 #undef NODE_LOOP
 #undef NODE_PAIR_LOOP
+#undef NODE4_LOOP
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.status->iterations = it;
         a.status->converged = s_stop;

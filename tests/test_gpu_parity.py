@@ -233,3 +233,38 @@ def test_solve_warm_start_and_multi_rhs(pair):
     for r in range(3):
         res = np.linalg.norm(ops.apply_EK(u[r]) - qref[r]) / np.linalg.norm(qref[r])
         assert res < 1e-10
+
+
+def test_odd_part_recovery(pair):
+    # u^- = (M^- - K^-)^{-1}(l^- - A u^+), against the oracle's operators,
+    # with l^- = 0 and with a given l^-
+    ops = pair.ops
+    up = pair.even(2)
+    lm = pair.odd(2)
+    upt = torch.tensor(up, dtype=torch.float64, device='cuda')
+    got0 = pair.gpu.odd(upt).cpu().numpy()
+    got1 = pair.gpu.odd(upt, torch.tensor(lm, dtype=torch.float64, device='cuda')).cpu().numpy()
+    for r in range(2):
+        ref0 = ops.solve_MKminus(-ops.apply_A(up[r]))
+        ref1 = ops.solve_MKminus(lm[r] - ops.apply_A(up[r]))
+        assert relerr(got0[r], ref0) < 1e-11
+        assert relerr(got1[r], ref1) < 1e-11
+
+
+def test_odd_part_of_the_mixed_solution():
+    # the full pair (u^+, u^-) of the dense mixed system on a tiny mesh: the
+    # library's solve gives u^+, rte_odd must give the mixed system's u^-
+    import paper_2102_09038_gb300 as rte
+    from oracle.dense import mixed_solve
+    p = workloads.constant(3, 1, 0.6, 1.5, 1.2, 1.0)
+    disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+    lplus = disc.source(p.q_nodal[0])
+    up_ref, um_ref = mixed_solve(disc, lplus)
+    s = rte.Solver(p, n_plus=2, n_minus=3)
+    q = torch.tensor(lplus.reshape(1, disc.nRp, disc.nSp), dtype=torch.float64, device='cuda')
+    u, info = s.solve(q, tol=1e-12)
+    assert info['status'] == 0
+    um = s.odd(u).cpu().numpy()
+    assert relerr(u.cpu().numpy().ravel(), up_ref) < 1e-10
+    assert relerr(um.ravel(), um_ref) < 1e-10
+    s.close()
