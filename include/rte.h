@@ -99,6 +99,9 @@ typedef struct {
     int split_slices;       /* digit slices per operand for RTE_DGEMM_SPLIT  */
     int mg_sweeps;          /* smoothing sweeps before and after each coarse
                                correction in the multigrid preconditioners   */
+    int autotune;           /* 1: time the launch shapes of the SpMM kernels
+                               and tensor-core GEMMs at setup (cached per
+                               shape for the process); 0: fixed shapes       */
 } rte_options;
 
 typedef struct {
@@ -152,6 +155,22 @@ int rte_precond(rte_handle* h, const double* r, double* s, int nrhs,
  * RTE_ERR_DIVERGED on a NaN/Inf residual. */
 int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
               rte_stats* stats);
+
+/* Contraction estimates of Section 6.2 by power iteration on the handle's
+ * own operators (nrhs = 1):
+ *  rho = spectral radius of T = I - P_2 P_1^l (E - K^+) (Algorithm 3's
+ *        iteration matrix, = (I - P_G)(I - P_1^l (E - K^+)));
+ *  eta = its (E - K^+)-norm: eta^2 = largest eigenvalue of
+ *        (I - P_1^l A)(I - P_G)(I - P_1^l A), A = E - K^+, P_G the
+ *        A-orthogonal projection onto span W (needs n_plus >= 0).
+ * Starts from a seeded uniform vector; stops when two successive estimates
+ * differ by at most tol (relative) or after maxit steps (*iters = steps
+ * taken).  rho or eta may be NULL to skip it.  Use an FP64 handle: in the
+ * mixed modes the inner solves stop at loose tolerances and the operator is
+ * only approximately linear.  Uses the handle's workspace (not concurrently
+ * with rte_solve on the same handle). */
+int rte_rates(rte_handle* h, int maxit, double tol, unsigned long long seed, double* rho,
+              double* eta, int* iters);
 
 /* The odd part of the solution from the even part: the second block row of
  * the mixed system (eq. mixed_discrete), A u^+ + (M^- - K^-) u^- = l^-, so
@@ -208,6 +227,14 @@ int rte_operator(rte_handle* h, int op, const double* in, double* out,
  * Queued on stream (a cudaStream_t). */
 int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K,
                   int bf16, int out_bf16, void* stream);
+
+/* The launch shapes the autotuner chose so far in this process (one
+ * "key=choice (ms per candidate);" entry per tuned kernel shape; choice is
+ * the candidate index: block sizes 128/256/512 for the SpMM kernels, tile
+ * widths 128/256 for the tensor-core GEMMs).  Copies at most len - 1 bytes
+ * and a terminating zero into buf (buf may be NULL when len is 0); returns
+ * the length of the whole report. */
+size_t rte_autotune_report(char* buf, size_t len);
 
 /* The FP64 split GEMM of RTE_DGEMM_SPLIT, exposed for testing and
  * profiling: C[M x N] = A[M x K] * Bt[N x K]^T, all FP64 row-major device

@@ -49,7 +49,8 @@ class _Options(ctypes.Structure):
                 ('e0_maxit', ctypes.c_int), ('coarse_tol', ctypes.c_double),
                 ('coarse_maxit', ctypes.c_int), ('max_iter', ctypes.c_int),
                 ('max_rhs', ctypes.c_int), ('dgemm', ctypes.c_int),
-                ('split_slices', ctypes.c_int), ('mg_sweeps', ctypes.c_int)]
+                ('split_slices', ctypes.c_int), ('mg_sweeps', ctypes.c_int),
+                ('autotune', ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -93,6 +94,8 @@ def load(path=LIB_PATH):
     lib.rte_solve.argtypes = [P, P, P, I, D, ctypes.POINTER(_Stats)]
     lib.rte_operator.argtypes = [P, I, P, P, I]
     lib.rte_odd.argtypes = [P, P, P, P, I]
+    lib.rte_rates.argtypes = [P, I, D, ctypes.c_ulonglong, ctypes.POINTER(D), ctypes.POINTER(D),
+                              ctypes.POINTER(I)]
     lib.rte_export.argtypes = [P, I, ctypes.POINTER(D), ctypes.c_size_t]
     lib.rte_timing_enable.argtypes = [P, I]
     lib.rte_timing_read.argtypes = [P, ctypes.POINTER(ctypes.c_char_p),
@@ -101,6 +104,8 @@ def load(path=LIB_PATH):
                                     ctypes.POINTER(I)]
     lib.rte_gemm_lowp.argtypes = [P, P, P, I, I, I, I, I, P]
     lib.rte_dgemm_split.argtypes = [P, P, P, I, I, I, I, P]
+    lib.rte_autotune_report.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    lib.rte_autotune_report.restype = ctypes.c_size_t
     lib.rte_dgemm_split_static.argtypes = [P, P, P, I, I, I, I, P]
     lib.rte_estimate_bytes.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Options), I]
     lib.rte_estimate_bytes.restype = ctypes.c_size_t
@@ -165,6 +170,23 @@ def dgemm_split(A, Bt, slices=7, stream=None):
     _check(_lib.rte_dgemm_split(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, slices,
                                 ctypes.c_void_p(st.cuda_stream)))
     return C
+
+
+def autotune_report():
+    """{kernel shape: (chosen candidate, [ms per candidate])} of the launch
+    shapes the autotuner timed in this process."""
+    load()
+    n = _lib.rte_autotune_report(None, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    _lib.rte_autotune_report(buf, n + 1)
+    out = {}
+    for item in buf.value.decode().split(';'):
+        if ' (ms' not in item:
+            continue
+        head, ms = item.rsplit(' (ms', 1)
+        key, choice = head.rsplit('=', 1)
+        out[key] = (int(choice), [float(v) for v in ms.strip(' )').split()])
+    return out
 
 
 def dgemm_split_static(A, Bt, slices=7, out=None, stream=None):
@@ -383,6 +405,14 @@ class Solver:
         lm = self._vec(l_minus) if l_minus is not None else None
         _check(_lib.rte_odd(self._h, self._vec(u_plus), lm, self._vec(out), nrhs))
         return out
+
+    def rates(self, maxit=300, tol=1e-9, seed=1, rho=True, eta=True):
+        """(rho, eta, steps): power-iteration estimates of the spectral radius
+        and the energy norm of Algorithm 3's iteration matrix (rte_rates)."""
+        r, e, it = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int(0)
+        _check(_lib.rte_rates(self._h, maxit, tol, seed, ctypes.byref(r) if rho else None,
+                              ctypes.byref(e) if eta else None, ctypes.byref(it)))
+        return (r.value if rho else None), (e.value if eta else None), it.value
 
     def export(self, name):
         """Host copy of an assembled matrix (see rte_export in rte.h)."""

@@ -33,6 +33,8 @@ struct DevLow {
 // Raw device pointers of an assembled system (owned by rte_handle).
 struct DevSystem {
     int m;                     // mesh: m x m squares
+    int tpb_A = 256;           // threads per block of the transport apply (autotuned)
+    int tpb_even = 256;        // threads per block of the even gather (autotuned)
     int nRp, nRm, nSp, nSm, dP, dM, nnz;
     const double* ell4;        // M_t^+, M_s^+, B_x, B_y in ELL form [4][7][nRp]
     double g, c, gamma;
@@ -118,6 +120,8 @@ void dot_per_rhs(cudaStream_t s, const float* x, const float* y, size_t len, int
                  double* partial, double* out);
 void axpby_per_rhs(cudaStream_t s, const float* x, float* y, size_t len, int nrhs,
                    const double* a, double ca, const double* b, double cb);
+// x uniform in [-1, 1), a counter-based function of (seed, index)
+void fill_uniform(cudaStream_t s, double* x, size_t n, unsigned long long seed);
 void convert(cudaStream_t s, const double* x, float* y, size_t n);
 void convert(cudaStream_t s, const float* x, double* y, size_t n);
 void convert(cudaStream_t s, const float* x, __nv_bfloat16* y, size_t n);

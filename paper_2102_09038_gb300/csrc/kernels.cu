@@ -261,6 +261,19 @@ __device__ double block_sum(double v) {
     return v;  // valid in thread 0
 }
 
+// x[e] uniform in [-1, 1) from the SplitMix64 mix of (seed, e) (Steele,
+// Lea and Flood, "Fast splittable pseudorandom number generators", 2014).
+__global__ void k_fill_uniform(double* __restrict__ x, size_t n, unsigned long long seed) {
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+         e += (size_t)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (e + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[e] = (double)(z >> 11) * 0x1.0p-52 - 1.0;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_dot_partial(const T* __restrict__ x, const T* __restrict__ y,
@@ -574,7 +587,7 @@ void gemm_f64(cudaStream_t s, int M, int N, int K, const double* A, int lda,
 void apply_A(cudaStream_t s, const DevSystem& d, const double* U, double* Z, int nrhs) {
     const size_t total = (size_t)nrhs * d.nRm * d.nSp;
     count_launches(1);
-    k_apply_A_s<double, double, double><<<grid_for(total), kThreads, 0, s>>>(
+    k_apply_A_s<double, double, double><<<grid_for(total, d.tpb_A), d.tpb_A, 0, s>>>(
         d.m, d.nSp, nrhs, d.cell_D, d.ang_A1, d.ang_A2, U, Z);
 }
 
@@ -583,10 +596,10 @@ void apply_A_lo(cudaStream_t s, const DevSystem& d, const float* U, void* Z, boo
     const size_t total = (size_t)nrhs * d.nRm * d.nSp;
     count_launches(1);
     if (bf16)
-        k_apply_A_s<float, __nv_bfloat16, float><<<grid_for(total), kThreads, 0, s>>>(
+        k_apply_A_s<float, __nv_bfloat16, float><<<grid_for(total, d.tpb_A), d.tpb_A, 0, s>>>(
             d.m, d.nSp, nrhs, d.lo.cell_D, d.lo.A1, d.lo.A2, U, static_cast<__nv_bfloat16*>(Z));
     else
-        k_apply_A_s<float, float, float><<<grid_for(total), kThreads, 0, s>>>(
+        k_apply_A_s<float, float, float><<<grid_for(total, d.tpb_A), d.tpb_A, 0, s>>>(
             d.m, d.nSp, nrhs, d.lo.cell_D, d.lo.A1, d.lo.A2, U, static_cast<float*>(Z));
 }
 
@@ -594,7 +607,7 @@ void apply_even(cudaStream_t s, const DevSystem& d, const double* Zp, const doub
                 const double* V, double* Y, int nrhs, int flags) {
     const size_t total = (size_t)nrhs * d.nRp * d.nSp;
     count_launches(1);
-    k_apply_even_s<double><<<grid_for(total), kThreads, 0, s>>>(
+    k_apply_even_s<double><<<grid_for(total, d.tpb_even), d.tpb_even, 0, s>>>(
         d.m, d.nSp, nrhs, flags, d.cell_D, d.ang_A1, d.ang_A2, d.ell4, d.ang_m, d.ang_omx,
         d.ang_omy, Zp, X, V, Y);
 }
@@ -603,7 +616,7 @@ void apply_even_lo(cudaStream_t s, const DevSystem& d, const float* Zp, const fl
                    const float* V, float* Y, int nrhs, int flags) {
     const size_t total = (size_t)nrhs * d.nRp * d.nSp;
     count_launches(1);
-    k_apply_even_s<float><<<grid_for(total), kThreads, 0, s>>>(
+    k_apply_even_s<float><<<grid_for(total, d.tpb_even), d.tpb_even, 0, s>>>(
         d.m, d.nSp, nrhs, flags, d.lo.cell_D, d.lo.A1, d.lo.A2, d.lo.ell4, d.lo.m, d.lo.omx,
         d.lo.omy, Zp, X, V, Y);
 }
@@ -660,6 +673,11 @@ void axpby_per_rhs(cudaStream_t s, const float* x, float* y, size_t len, int nrh
                    const double* a, double ca, const double* b, double cb) {
     count_launches(1);
     k_axpby<float><<<grid_for(len * nrhs), kThreads, 0, s>>>(x, y, len, nrhs, a, ca, b, cb);
+}
+
+void fill_uniform(cudaStream_t s, double* x, size_t n, unsigned long long seed) {
+    count_launches(1);
+    k_fill_uniform<<<grid_for(n), kThreads, 0, s>>>(x, n, seed);
 }
 
 void convert(cudaStream_t s, const double* x, float* y, size_t n) {

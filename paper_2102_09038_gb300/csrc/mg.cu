@@ -633,6 +633,323 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg(E0Args<T> a) {
     }
 }
 
+__device__ __forceinline__ float4 ldf4q(const float* base, size_t o4) {
+    return __ldcg(reinterpret_cast<const float4*>(base) + o4);
+}
+
+// ------------------------------------------ E_0 PCG, FP32, quad phases
+// The FP32 CG runs as the V-cycle does: grid-stride loops over quads (four
+// consecutive columns of one node), each phase its own function.  The CG
+// vectors keep the even layout [rhs][node][direction]; the V-cycle arrays
+// are [node][column].  Per-column dot products: every thread sums its
+// quad's four columns; a block combines its threads in shared memory and
+// adds once per column.
+
+constexpr int kShCols = 1024;   // columns combined in shared memory per block
+
+struct ColSum {
+    double v[4];
+    int p;
+    __device__ ColSum() : v{0.0, 0.0, 0.0, 0.0}, p(-1) {}
+    __device__ void flush(double* dst) {
+        if (p >= 0)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (v[u] != 0.0) atomicAdd(dst + 4 * p + u, v[u]);
+        v[0] = v[1] = v[2] = v[3] = 0.0;
+    }
+    // the thread moves to quad pp (a change only when the grid stride is not
+    // a multiple of the quads per node)
+    __device__ void at(int pp, double* dst) {
+        if (pp != p) {
+            flush(dst);
+            p = pp;
+        }
+    }
+};
+
+// All threads of the block call this at the same point.
+__device__ void colsum_finish(ColSum& cs, double* dst, double* sh, int nc) {
+    if (nc > kShCols) {
+        cs.flush(dst);
+        return;
+    }
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) sh[c] = 0.0;
+    __syncthreads();
+    if (cs.p >= 0)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (cs.v[u] != 0.0) atomicAdd(sh + 4 * cs.p + u, cs.v[u]);
+    __syncthreads();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x)
+        if (sh[c] != 0.0) atomicAdd(dst + c, sh[c]);
+    __syncthreads();
+    cs = ColSum();
+}
+
+struct E0Q {   // what the quad phases need of E0Args<float>
+    int nRp, m, nSp, nc, nq, nqd;
+    double tol2;
+    const double* B;
+    double* X;
+    float *R, *P, *AP, *B0;
+    const double* bb;
+    MGDeviceLevel L0;
+    const float4* wq;
+};
+
+
+// Per-block table of the columns' CG scalars, built once per phase so that
+// the items read a byte and a float from shared memory instead of doing FP64
+// comparisons and divisions per item: act[c] = column c active (and, for the
+// direction update, still active), coef[c] = alpha or beta.
+enum TableKind { kActOnly, kAlpha, kBeta };
+
+__device__ void col_table(TableKind kind, int nc, double tol2, const double* bb,
+                          const double* rr_prev, const double* rz_prev, const double* x3,
+                          const double* rr_cur, unsigned char* act, float* coef) {
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        bool a = ldg2(rr_prev + c) > tol2 * ldg2(bb + c);
+        float f = 0.f;
+        if (kind == kAlpha && a) {
+            const double pap = ldg2(x3 + c);   // p.Ap
+            f = pap != 0.0 ? (float)(ldg2(rz_prev + c) / pap) : 0.f;
+        } else if (kind == kBeta) {
+            a = a && ldg2(rr_cur + c) > tol2 * ldg2(bb + c);
+            const double ro = ldg2(rz_prev + c);
+            f = a && ro != 0.0 ? (float)(ldg2(x3 + c) / ro) : 0.f;   // x3 = rz of this step
+        }
+        act[c] = a ? 1 : 0;
+        if (kind != kActOnly) coef[c] = f;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ unsigned quad_mask(const unsigned char* act, int col) {
+    const uchar4 m = *reinterpret_cast<const uchar4*>(act + col);
+    return (unsigned)m.x | ((unsigned)m.y << 1) | ((unsigned)m.z << 2) | ((unsigned)m.w << 3);
+}
+
+__device__ __forceinline__ float4 sel4(unsigned m, float4 a, float4 b) {
+    return make_float4((m & 1u) ? a.x : b.x, (m & 2u) ? a.y : b.y, (m & 4u) ? a.z : b.z,
+                       (m & 8u) ? a.w : b.w);
+}
+
+// Grid-stride loop over the (node i, quad p) items of the CG; e4 = float4
+// offset in the even layout, m4 = in the V-cycle layout.
+#define CGQ(q)                                                                   \
+    ColSum cs;                                                                   \
+    const unsigned total__ = (unsigned)q.nRp * (unsigned)q.nq;                   \
+    for (unsigned e__ = blockIdx.x * blockDim.x + threadIdx.x; e__ < total__;    \
+         e__ += gridDim.x * blockDim.x) {                                        \
+        const int i = (int)(e__ / (unsigned)q.nq), p = (int)(e__ % (unsigned)q.nq); \
+        const int r = p / q.nqd, k4 = p - r * q.nqd;                             \
+        const size_t e4 = ((size_t)r * q.nRp + i) * q.nqd + k4;                  \
+        const size_t m4 = (size_t)i * q.nq + p;                                  \
+        const int col = 4 * p;                                                   \
+        (void)m4;                                                                \
+        (void)col;
+
+__device__ __noinline__ void cgq_init(const E0Q& q, double* bbsum, double* sh) {
+    CGQ(q)
+        const double2* b2 = reinterpret_cast<const double2*>(q.B) + 2 * e4;
+        const double2 b01 = __ldcg(b2), b23 = __ldcg(b2 + 1);
+        const float4 bf = make_float4((float)b01.x, (float)b01.y, (float)b23.x, (float)b23.y);
+        double2* x2 = reinterpret_cast<double2*>(q.X) + 2 * e4;
+        x2[0] = make_double2(0.0, 0.0);
+        x2[1] = make_double2(0.0, 0.0);
+        reinterpret_cast<float4*>(q.R)[e4] = bf;
+        reinterpret_cast<float4*>(q.B0)[m4] = bf;
+        cs.at(p, bbsum);
+        cs.v[0] += (double)bf.x * bf.x;
+        cs.v[1] += (double)bf.y * bf.y;
+        cs.v[2] += (double)bf.z * bf.z;
+        cs.v[3] += (double)bf.w * bf.w;
+    }
+    colsum_finish(cs, bbsum, sh, q.nc);
+}
+
+// P = z, rz = r.z (first direction)
+__device__ __noinline__ void cgq_first_dir(const E0Q& q, const float* z, double* rz, double* sh) {
+    CGQ(q)
+        const float4 zv = ldf4q(z, m4), rv = ldf4q(q.R, e4);
+        reinterpret_cast<float4*>(q.P)[e4] = zv;
+        cs.at(p, rz);
+        cs.v[0] += (double)rv.x * zv.x;
+        cs.v[1] += (double)rv.y * zv.y;
+        cs.v[2] += (double)rv.z * zv.z;
+        cs.v[3] += (double)rv.w * zv.w;
+    }
+    colsum_finish(cs, rz, sh, q.nc);
+}
+
+// AP = E_0 P and p.Ap for the active columns
+__device__ __noinline__ void cgq_ap(const E0Q& q, const double* rr_prev, double* pap, double* sh,
+                                    unsigned char* s_act, float* s_coef) {
+    col_table(kActOnly, q.nc, q.tol2, q.bb, rr_prev, nullptr, nullptr, nullptr, s_act, s_coef);
+    CGQ(q)
+        const unsigned am = quad_mask(s_act, col);
+        if (!am) continue;
+        Quad qd;
+        qd.load(q.wq, q.nqd, k4);
+        const float4* Pr = reinterpret_cast<const float4*>(q.P) + (size_t)r * q.nRp * q.nqd;
+        float4 dg;
+        const float4 y = e0_apply4(q.L0, qd, Pr, i, k4, q.nqd, dg);
+        const float4 pv = ldf4q(q.P, e4);
+        reinterpret_cast<float4*>(q.AP)[e4] = y;
+        cs.at(p, pap);
+        if (am & 1u) cs.v[0] += (double)y.x * pv.x;
+        if (am & 2u) cs.v[1] += (double)y.y * pv.y;
+        if (am & 4u) cs.v[2] += (double)y.z * pv.z;
+        if (am & 8u) cs.v[3] += (double)y.w * pv.w;
+    }
+    colsum_finish(cs, pap, sh, q.nc);
+}
+
+// x += alpha p, r -= alpha Ap, V-cycle input = r (0 for finished columns)
+__device__ __noinline__ void cgq_update(const E0Q& q, const double* rr_prev, const double* rz_prev,
+                                        const double* pap, unsigned char* s_act, float* s_coef) {
+    col_table(kAlpha, q.nc, q.tol2, q.bb, rr_prev, rz_prev, pap, nullptr, s_act, s_coef);
+    CGQ(q)
+        const unsigned am = quad_mask(s_act, col);
+        float4* b0 = reinterpret_cast<float4*>(q.B0) + m4;
+        if (!am) {
+            *b0 = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
+        const float4 a4 = *reinterpret_cast<const float4*>(s_coef + col);
+        const float al[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float4 pv = ldf4q(q.P, e4), rv = ldf4q(q.R, e4), apv = ldf4q(q.AP, e4);
+        double2* x2 = reinterpret_cast<double2*>(q.X) + 2 * e4;
+        double2 x01 = __ldcg(x2), x23 = __ldcg(x2 + 1);
+        x01.x += (double)(al[0] * pv.x);
+        x01.y += (double)(al[1] * pv.y);
+        x23.x += (double)(al[2] * pv.z);
+        x23.y += (double)(al[3] * pv.w);
+        x2[0] = x01;
+        x2[1] = x23;
+        const float4 rn = make_float4(rv.x - al[0] * apv.x, rv.y - al[1] * apv.y,
+                                      rv.z - al[2] * apv.z, rv.w - al[3] * apv.w);
+        reinterpret_cast<float4*>(q.R)[e4] = rn;
+        *b0 = sel4(am, rn, make_float4(0.f, 0.f, 0.f, 0.f));
+    }
+}
+
+// rz = r.z and rr = r.r for the active columns; finished columns keep their
+// previous values
+__device__ __noinline__ void cgq_rz(const E0Q& q, const float* z, const double* rr_prev,
+                                    const double* rz_prev, double* rz, double* rr, double* sh,
+                                    unsigned char* s_act, float* s_coef) {
+    col_table(kActOnly, q.nc, q.tol2, q.bb, rr_prev, nullptr, nullptr, nullptr, s_act, s_coef);
+    ColSum c2;
+    {
+        CGQ(q)
+            const unsigned am = quad_mask(s_act, col);
+            if (!am) continue;
+            const float4 rv = ldf4q(q.R, e4), zv = ldf4q(z, m4);
+            cs.at(p, rz);
+            c2.at(p, rr);
+            const float r4[4] = {rv.x, rv.y, rv.z, rv.w}, z4[4] = {zv.x, zv.y, zv.z, zv.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if ((am >> u) & 1u) {
+                    cs.v[u] += (double)r4[u] * z4[u];
+                    c2.v[u] += (double)r4[u] * r4[u];
+                }
+        }
+        colsum_finish(cs, rz, sh, q.nc);
+    }
+    colsum_finish(c2, rr, sh, q.nc);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < q.nc; c += gridDim.x * blockDim.x)
+        if (!(ldg2(rr_prev + c) > q.tol2 * ldg2(q.bb + c))) {
+            rr[c] = ldg2(rr_prev + c);
+            rz[c] = ldg2(rz_prev + c);
+        }
+}
+
+// p = z + beta p for the columns still active
+__device__ __noinline__ void cgq_pupdate(const E0Q& q, const float* z, const double* rr_prev,
+                                         const double* rr, const double* rz_prev,
+                                         const double* rz, unsigned char* s_act, float* s_coef) {
+    col_table(kBeta, q.nc, q.tol2, q.bb, rr_prev, rz_prev, rz, rr, s_act, s_coef);
+    CGQ(q)
+        const unsigned um = quad_mask(s_act, col);
+        if (!um) continue;
+        const float4 b4 = *reinterpret_cast<const float4*>(s_coef + col);
+        const float be[4] = {b4.x, b4.y, b4.z, b4.w};
+        const float4 zv = ldf4q(z, m4), pv = ldf4q(q.P, e4);
+        const float4 np = make_float4(zv.x + be[0] * pv.x, zv.y + be[1] * pv.y,
+                                      zv.z + be[2] * pv.z, zv.w + be[3] * pv.w);
+        reinterpret_cast<float4*>(q.P)[e4] = sel4(um, np, pv);
+    }
+}
+#undef CGQ
+
+__global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
+    __shared__ double sh[kShCols];
+    __shared__ __align__(16) float s_coef[kShCols];
+    __shared__ __align__(16) unsigned char s_act[kShCols];
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) s_stop = 0;
+    E0Q q;
+    q.nRp = a.nRp;
+    q.m = a.m;
+    q.nSp = a.nSp;
+    q.nc = a.ncols;
+    q.nq = a.ncols >> 2;
+    q.nqd = a.nSp >> 2;
+    q.tol2 = a.tol2;
+    q.B = a.B;
+    q.X = a.X;
+    q.R = a.R;
+    q.P = a.P;
+    q.AP = a.AP;
+    q.L0 = a.mg.lev[0];
+    q.B0 = q.L0.B;
+    q.bb = a.bb;
+    q.wq = a.mg.wq;
+    const int nc = a.ncols;
+    cgq_init(q, a.bb, sh);
+    if (!grid_sync(a.bar)) return;
+    float* z = nullptr;
+    if (!e0_vcycle(a.mg, a.bar, z)) return;
+    cgq_first_dir(q, z, slot(a, 2, 1), sh);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += gridDim.x * blockDim.x)
+        slot(a, 2, 2)[c] = ldg2(a.bb + c);
+    if (!grid_sync(a.bar)) return;
+    int it = 0;
+    for (; it < a.maxit; ++it) {
+        const int cur = it % 3, prev = (it + 2) % 3, next = (it + 1) % 3;
+        if (blockIdx.x == 0)
+            for (int c = threadIdx.x; c < 3 * nc; c += blockDim.x)
+                a.acc[(size_t)next * 3 * nc + c] = 0.0;
+        cgq_ap(q, slot(a, prev, 2), slot(a, cur, 0), sh, s_act, s_coef);
+        if (!grid_sync(a.bar)) return;
+        cgq_update(q, slot(a, prev, 2), slot(a, prev, 1), slot(a, cur, 0), s_act, s_coef);
+        if (!grid_sync(a.bar)) return;
+        if (!e0_vcycle(a.mg, a.bar, z)) return;
+        cgq_rz(q, z, slot(a, prev, 2), slot(a, prev, 1), slot(a, cur, 1), slot(a, cur, 2), sh,
+               s_act, s_coef);
+        if (!grid_sync(a.bar)) return;
+        cgq_pupdate(q, z, slot(a, prev, 2), slot(a, cur, 2), slot(a, prev, 1), slot(a, cur, 1),
+                    s_act, s_coef);
+        if (!grid_sync(a.bar)) return;
+        if (threadIdx.x == 0) s_stop = 1;
+        __syncthreads();
+        for (int c = threadIdx.x; c < nc; c += blockDim.x)
+            if (ldg2(slot(a, cur, 2) + c) > a.tol2 * ldg2(a.bb + c)) s_stop = 0;
+        __syncthreads();
+        if (s_stop) {
+            ++it;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.status->iterations = it;
+        a.status->converged = s_stop;
+    }
+}
+
 // ============================================================ E_c V-cycle
 // E_c work is spread over lane groups: G lanes (8, 16 or 32, the smallest
 // power of two that holds d) per (rhs, node) item, 32 / G items per warp;
@@ -1072,7 +1389,9 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     a.mg.nSp = d.nSp;
     a.mg.w8 = reinterpret_cast<const float4*>(d.e0mg.w8);
     a.mg.wq = reinterpret_cast<const float4*>(d.e0mg.wq);
-    const void* fn = (const void*)k_e0_pcg<T>;
+    // FP32: the quad kernel when the columns fit its shared per-column tables
+    const void* fn = (sizeof(T) == sizeof(float) && ncols <= kShCols) ? (const void*)k_e0_pcg_f
+                                                                       : (const void*)k_e0_pcg<T>;
     const int grid = coop_grid(fn, 256);
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, s));

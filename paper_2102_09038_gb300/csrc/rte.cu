@@ -15,6 +15,7 @@
 #include "mg_host.h"
 #include "rte_internal.h"
 #include "tc_gemm.h"
+#include "tune.h"
 
 namespace rte {
 
@@ -68,6 +69,8 @@ struct rte_handle {
     size_t cobytes = 0;
     SolveStatus* status = nullptr;
     unsigned long long* trace = nullptr;   // phase trace buffer (profiling)
+    // autotuned tile widths of the low-precision GEMMs (0: by N)
+    int bn_mk1 = 0, bn_mk2 = 0, bn_kplus = 0;
     // statistics of the last inner solves
     int e0_iters = 0, co_iters = 0, mk_iters = 0;
     // timing
@@ -456,6 +459,64 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
     return RTE_OK;
 }
 
+// ------------------------------------------------------------ autotuning
+// Launch shapes chosen by measurement (tune.cpp) on this handle's workspace
+// at max_rhs: the block size of the two SpMM kernels and, in the mixed
+// modes, the tile width of each tensor-core contraction.  Results are
+// cached per shape for the process.
+int tune_launches(rte_handle* h) {
+    if (!h->opt.autotune) return RTE_OK;
+    DevSystem& d = h->d;
+    const int nr = h->cap_rhs;
+    cudaStream_t s = h->stream;
+    auto ok = [] { return cudaGetLastError() == cudaSuccess ? RTE_OK : RTE_ERR_CUDA; };
+    const int tpb[3] = {128, 256, 512};
+    char key[200];
+    int b = 1;
+    std::snprintf(key, sizeof key, "apply_A m=%d nS=%d rhs=%d", d.m, d.nSp, nr);
+    RTE_TRY(autotune(s, key, 3, [&](int c) {
+        d.tpb_A = tpb[c];
+        apply_A(s, d, h->e1, h->z1, nr);
+        return ok();
+    }, &b));
+    d.tpb_A = tpb[b];
+    std::snprintf(key, sizeof key, "apply_even m=%d nS=%d rhs=%d", d.m, d.nSp, nr);
+    RTE_TRY(autotune(s, key, 3, [&](int c) {
+        d.tpb_even = tpb[c];
+        apply_even(s, d, h->z2, h->e1, nullptr, h->e2, nr, 3);
+        return ok();
+    }, &b));
+    d.tpb_even = tpb[b];
+    if (!h->mixed) return RTE_OK;
+    const bool bf = d.lo.bf16;
+    const int bns[2] = {128, 256};
+    TcGemmArgs g{};
+    g.tf32 = !bf;
+    g.A = h->zl1; g.Bt = d.lo.VmT; g.C = h->zl2;
+    g.M = nr * d.nRm; g.N = d.nSm; g.K = d.nSm; g.ldc = d.nSm;
+    g.epi = 1; g.at = d.lo.cell_at; g.as = d.lo.cell_as; g.lam = d.lo.lamM; g.rows = d.nRm;
+    g.out_bf16 = bf;
+    std::snprintf(key, sizeof key, "tc_gemm %s M=%d N=%d K=%d epi=1", bf ? "bf16" : "tf32", g.M,
+                  g.N, g.K);
+    RTE_TRY(autotune(s, key, 2, [&](int c) { g.bn = bns[c]; return tc_gemm(s, g); }, &b));
+    h->bn_mk1 = bns[b];
+    g.A = h->zl2; g.Bt = d.lo.Vm; g.C = h->zf; g.epi = 0; g.out_bf16 = false;
+    std::snprintf(key, sizeof key, "tc_gemm %s M=%d N=%d K=%d epi=0", bf ? "bf16" : "tf32", g.M,
+                  g.N, g.K);
+    RTE_TRY(autotune(s, key, 2, [&](int c) { g.bn = bns[c]; return tc_gemm(s, g); }, &b));
+    h->bn_mk2 = bns[b];
+    TcGemmArgs k{};
+    k.tf32 = !bf;
+    k.A = bf ? static_cast<const void*>(h->xl) : static_cast<const void*>(h->f1);
+    k.Bt = d.lo.Sp; k.C = h->f3;
+    k.M = nr * d.nRp; k.N = d.nSp; k.K = d.nSp; k.ldc = d.nSp; k.rows = 1;
+    std::snprintf(key, sizeof key, "tc_gemm %s M=%d N=%d K=%d epi=0", bf ? "bf16" : "tf32", k.M,
+                  k.N, k.K);
+    RTE_TRY(autotune(s, key, 2, [&](int c) { k.bn = bns[c]; return tc_gemm(s, k); }, &b));
+    h->bn_kplus = bns[b];
+    return tc_gemm_error(s);
+}
+
 // ------------------------------------------------------------ workspace
 int ensure_workspace(rte_handle* h, int nrhs) {
     if (nrhs <= h->cap_rhs) return RTE_OK;
@@ -694,11 +755,13 @@ int apply_E_lo(rte_handle* h, const float* x, float* y, int nrhs, bool with_k) {
         g.M = nrhs * d.nRm; g.N = d.nSm; g.K = d.nSm; g.ldc = d.nSm;
         g.epi = 1; g.at = d.lo.cell_at; g.as = d.lo.cell_as; g.lam = d.lo.lamM; g.rows = d.nRm;
         g.out_bf16 = bf;
+        g.bn = h->bn_mk1;
         RTE_TRY(tc_gemm(h->stream, g));
     }
     {
         Scope sc(h, "tc_gemm_mk2");
         g.A = h->zl2; g.Bt = d.lo.Vm; g.C = h->zf; g.epi = 0; g.out_bf16 = false;
+        g.bn = h->bn_mk2;
         RTE_TRY(tc_gemm(h->stream, g));
     }
     float* V = nullptr;
@@ -714,6 +777,7 @@ int apply_E_lo(rte_handle* h, const float* x, float* y, int nrhs, bool with_k) {
         TcGemmArgs k{};
         k.tf32 = !bf; k.A = xop; k.Bt = d.lo.Sp; k.C = V;
         k.M = nrhs * d.nRp; k.N = d.nSp; k.K = d.nSp; k.ldc = d.nSp; k.rows = 1;
+        k.bn = h->bn_kplus;
         RTE_TRY(tc_gemm(h->stream, k));
     }
     Scope sc(h, "apply_even_lo");
@@ -855,6 +919,7 @@ int rte_default_options(rte_options* o) {
     o->dgemm = RTE_DGEMM_AUTO;
     o->split_slices = 7;
     o->mg_sweeps = 2;
+    o->autotune = 1;
     return RTE_OK;
 }
 
@@ -1208,6 +1273,8 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     if (rc) return bail(rc);
     rc = alloc_workspace(h, o.max_rhs);
     if (rc) return bail(rc);
+    rc = tune_launches(h);
+    if (rc) return bail(rc);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess)
         return bail(fail(RTE_ERR_CUDA, "setup synchronisation failed"));
     *out = h;
@@ -1291,6 +1358,101 @@ int rte_operator(rte_handle* h, int op, const double* in, double* out, int nrhs)
     }
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
+}
+
+namespace {
+
+// ||x||_2 of one even vector (device reduction, host result)
+int norm2(rte_handle* h, const double* x, double* out) {
+    const size_t len = (size_t)h->d.nRp * h->d.nSp;
+    dot_per_rhs(h->stream, x, x, len, 1, h->partial, h->sc);
+    double v = 0.0;
+    RTE_CUDA_TRY(cudaMemcpyAsync(&v, h->sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *out = std::sqrt(std::max(v, 0.0));
+    return RTE_OK;
+}
+
+// One power-iteration step: x <- y / ||y||; returns ||y|| / ||x|| (x is a
+// unit vector on entry).
+int power_step(rte_handle* h, double* x, const double* y, double* ratio) {
+    const size_t len = (size_t)h->d.nRp * h->d.nSp;
+    double ny = 0.0;
+    RTE_TRY(norm2(h, y, &ny));
+    *ratio = ny;
+    if (!(ny > 0.0)) return RTE_OK;
+    axpby_per_rhs(h->stream, y, x, len, 1, nullptr, 1.0 / ny, nullptr, 0.0);
+    return RTE_OK;
+}
+
+}  // namespace
+
+int rte_rates(rte_handle* h, int maxit, double tol, unsigned long long seed, double* rho,
+              double* eta, int* iters) {
+    if (!h || maxit < 1 || !(tol >= 0) || (!rho && !eta)) return fail(RTE_ERR_ARG, "bad argument");
+    const DevSystem& d = h->d;
+    cudaStream_t s = h->stream;
+    const size_t len = (size_t)d.nRp * d.nSp;
+    double* x = h->e1;
+    double* y = h->e2;
+    double* t = h->e3;
+    double* w = h->e4;
+    int used = 0;
+    auto start = [&](unsigned long long sd) -> int {
+        fill_uniform(s, x, len, sd);
+        double nx = 0.0;
+        RTE_TRY(norm2(h, x, &nx));
+        axpby_per_rhs(s, x, x, len, 1, nullptr, 1.0 / nx, nullptr, 0.0);
+        return RTE_OK;
+    };
+    if (rho) {
+        // T x = x - P_2 P_1 (E - K^+) x, the iteration matrix of Algorithm 3
+        RTE_TRY(start(seed));
+        double prev = 0.0, cur = 0.0;
+        int k = 0;
+        for (; k < maxit; ++k) {
+            RTE_TRY(apply_E(h, x, y, 1, true));
+            RTE_TRY(precond(h, y, t, 1, true));
+            axpby_per_rhs(s, x, t, len, 1, nullptr, 1.0, nullptr, -1.0);   // t = x - P y
+            RTE_TRY(power_step(h, x, t, &cur));
+            if (k > 0 && std::fabs(cur - prev) <= tol * cur) { ++k; break; }
+            prev = cur;
+        }
+        *rho = cur;
+        used = std::max(used, k);
+    }
+    if (eta && d.dP > 0) {
+        // eta^2 = largest eigenvalue of (I - P_1 A)(I - P_G)(I - P_1 A), A = E - K^+,
+        // P_G = W E_c^{-1} W^T A (the A-orthogonal projection onto span W)
+        RTE_TRY(start(seed ^ 0x5851F42D4C957F2Dull));
+        double prev = 0.0, cur = 0.0;
+        int k = 0;
+        auto one_minus_p1a = [&](const double* in, double* out) -> int {   // out = in - P_1 A in
+            RTE_TRY(apply_E(h, in, y, 1, true));
+            RTE_TRY(apply_P1(h, y, out, 1));
+            axpby_per_rhs(s, in, out, len, 1, nullptr, 1.0, nullptr, -1.0);
+            return RTE_OK;
+        };
+        for (; k < maxit; ++k) {
+            RTE_TRY(one_minus_p1a(x, t));                                   // t = (I - P_1 A) x
+            RTE_TRY(apply_E(h, t, y, 1, true));                             // y = A t
+            RTE_TRY(restrict_(h, y, h->c1, 1));
+            RTE_TRY(coarse_inv(h, h->c1, h->c2, 1));
+            axpby_per_rhs(s, nullptr, h->c2, (size_t)d.nRp * d.dP, 1, nullptr, 0.0, nullptr, -1.0);
+            RTE_TRY(prolong_add(h, h->c2, t, 1, 1.0));                     // t -= W E_c^{-1} W^T A t
+            RTE_TRY(one_minus_p1a(t, w));                                   // w = (I - P_1 A) t
+            RTE_TRY(power_step(h, x, w, &cur));
+            if (k > 0 && std::fabs(cur - prev) <= tol * cur) { ++k; break; }
+            prev = cur;
+        }
+        *eta = std::sqrt(std::max(cur, 0.0));
+        used = std::max(used, k);
+    } else if (eta) {
+        *eta = 0.0;
+    }
+    if (iters) *iters = used;
+    RTE_CUDA_TRY(cudaGetLastError());
+    return tc_gemm_error(s);
 }
 
 int rte_odd(rte_handle* h, const double* u_plus, const double* l_minus, double* u_minus,
@@ -1477,6 +1639,16 @@ int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, 
     cudaFreeAsync(pb, s);
     if (rc) return rc;
     return tc_gemm_error(s);
+}
+
+size_t rte_autotune_report(char* buf, size_t len) {
+    const std::string r = autotune_report();
+    if (buf && len > 0) {
+        const size_t n = std::min(len - 1, r.size());
+        std::memcpy(buf, r.data(), n);
+        buf[n] = 0;
+    }
+    return r.size();
 }
 
 int rte_gemm_lowp(const void* A, const void* Bt, void* C, int M, int N, int K, int bf16,

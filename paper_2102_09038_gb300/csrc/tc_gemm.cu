@@ -196,7 +196,8 @@ int launch(cudaStream_t s, const TcGemmArgs& g) {
 
 int tc_gemm(cudaStream_t s, const TcGemmArgs& g) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return RTE_OK;
-    const bool wide = g.N > 128;
+    if (g.bn != 0 && g.bn != 128 && g.bn != 256) return fail(RTE_ERR_ARG, "tile width 128 or 256");
+    const bool wide = g.bn ? g.bn == 256 : g.N > 128;
     if (g.tf32) {
         if (g.out_bf16) return fail(RTE_ERR_ARG, "TF32 GEMM writes FP32");
         return wide ? launch<256, true, float>(s, g) : launch<128, true, float>(s, g);

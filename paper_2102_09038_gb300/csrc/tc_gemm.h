@@ -18,6 +18,7 @@ struct TcGemmArgs {
     float beta;
     bool tf32;          // operands FP32 read as TF32 (else BF16)
     bool out_bf16;      // write C as BF16 (else FP32)
+    int bn = 0;         // tile width 128 or 256; 0: 256 when N > 128
 };
 
 int tc_gemm(cudaStream_t s, const TcGemmArgs& g);

@@ -1,0 +1,87 @@
+// Launch-configuration autotuner: a process-wide table from a kernel's key
+// (name and problem shape) to the fastest measured candidate.
+#include "tune.h"
+
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "rte_internal.h"
+
+namespace rte {
+
+namespace {
+
+struct Entry {
+    int best = 0;
+    std::vector<float> ms;
+};
+
+std::mutex g_mu;
+std::map<std::string, Entry> g_table;
+
+}  // namespace
+
+int autotune(cudaStream_t s, const std::string& key, int ncand,
+             const std::function<int(int)>& run, int* best, int reps) {
+    if (ncand < 1 || !best) return fail(RTE_ERR_ARG, "autotune: no candidates");
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_table.find(key);
+        if (it != g_table.end()) {
+            *best = it->second.best;
+            return RTE_OK;
+        }
+    }
+    cudaEvent_t a = nullptr, b = nullptr;
+    RTE_CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return fail(RTE_ERR_CUDA, "autotune: cudaEventCreate");
+    }
+    Entry e;
+    e.ms.assign(ncand, -1.f);
+    float best_ms = 0.f;
+    int pick = -1;
+    for (int c = 0; c < ncand; ++c) {
+        if (run(c) != RTE_OK) continue;   // warm-up; a refused candidate is skipped
+        cudaEventRecord(a, s);
+        int rc = RTE_OK;
+        for (int r = 0; r < reps && rc == RTE_OK; ++r) rc = run(c);
+        cudaEventRecord(b, s);
+        if (rc != RTE_OK || cudaEventSynchronize(b) != cudaSuccess) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        e.ms[c] = ms / reps;
+        if (pick < 0 || e.ms[c] < best_ms) {
+            pick = c;
+            best_ms = e.ms[c];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (pick < 0) return fail(RTE_ERR_CUDA, "autotune: no candidate of " + key + " ran");
+    e.best = pick;
+    *best = pick;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_table.emplace(key, e);
+    return RTE_OK;
+}
+
+std::string autotune_report() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::string out;
+    char buf[64];
+    for (const auto& kv : g_table) {
+        out += kv.first + "=" + std::to_string(kv.second.best) + " (ms";
+        for (float m : kv.second.ms) {
+            std::snprintf(buf, sizeof(buf), " %.4f", m);
+            out += buf;
+        }
+        out += ");";
+    }
+    return out;
+}
+
+}  // namespace rte

@@ -108,3 +108,32 @@ def test_mixed_solve_reaches_fp64_residual(mixed):
     # iterative refinement costs only a few more outer iterations
     _, io = oracle.richardson(ops, qref[0], tol=1e-11, l=4, N=2)
     assert info['iterations'] <= io['iterations'] + 6, (info['iterations'], io['iterations'])
+
+
+@pytest.mark.parametrize('prec', [1, 2])
+def test_autotuned_launch_shapes(prec):
+    # the tuner picks one candidate per kernel shape, and the picked shapes
+    # give the same result as the fixed ones: each output is summed in the
+    # same order whatever the block size or tile width
+    import paper_2102_09038_gb300 as rte
+    p = workloads.checkerboard(m=12, levels=2, g=0.8, ratio=0.9, blocks=2, nrhs=1)
+    tuned = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, autotune=1)
+    fixed = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, autotune=0)
+    rep = rte.autotune_report()
+    keys = [k for k in rep if 'm=12 ' in k or 'M=%d ' % (2 * 12 * 12) in k]
+    assert any(k.startswith('apply_A') for k in keys)
+    assert any(k.startswith('apply_even') for k in keys)
+    assert any(k.startswith('tc_gemm %s' % ('bf16' if prec == 2 else 'tf32')) for k in rep)
+    for choice, ms in rep.values():
+        assert 0 <= choice < len(ms) and ms[choice] > 0 and ms[choice] == min(v for v in ms if v > 0)
+    x = torch.tensor(np.random.default_rng(5).standard_normal((1, tuned.n_nodes, tuned.n_dirs)),
+                     dtype=torch.float64, device='cuda')
+    for op in ('EK_LO', 'A'):
+        shape = x.shape if op == 'EK_LO' else (1, tuned.n_cells, tuned.n_odd)
+        a = torch.zeros(shape, dtype=torch.float64, device='cuda')
+        b = torch.zeros_like(a)
+        tuned.operator(op, x, a)
+        fixed.operator(op, x, b)
+        assert torch.equal(a, b), op
+    tuned.close()
+    fixed.close()

@@ -268,3 +268,38 @@ def test_odd_part_of_the_mixed_solution():
     assert relerr(u.cpu().numpy().ravel(), up_ref) < 1e-10
     assert relerr(um.ravel(), um_ref) < 1e-10
     s.close()
+
+
+def test_contraction_rates_match_dense_iteration_matrix():
+    # rho and eta of Algorithm 3's iteration matrix by power iteration on the
+    # library's operators, against the dense matrix built from the oracle's
+    # operators column by column (tiny mesh, FP64 handle)
+    import scipy.linalg as sla
+    import paper_2102_09038_gb300 as rte
+    p = workloads.constant(3, 1, 0.6, 1.0, 0.9, 1.0)
+    disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+    ops = oracle.Operators(disc, n_plus=2, n_minus=3)
+    co = Coarse(ops, 2)
+    n = disc.nRp * disc.nSp
+    A = np.zeros((n, n))
+    T = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        ej = e.reshape(disc.nRp, disc.nSp)
+        r = ops.apply_EK(ej)
+        A[:, j] = r.ravel()
+        s1 = ops.apply_P1(r, 4)
+        s = s1 + co.prolong(co.solve(co.restrict(r - ops.apply_EK(s1))))
+        T[:, j] = (ej - s).ravel()
+    A = 0.5 * (A + A.T)
+    rho_ref = np.abs(np.linalg.eigvals(T)).max()
+    eta_ref = np.sqrt(sla.eigh(T.T @ A @ T, A, eigvals_only=True).max())
+    s = rte.Solver(p, n_plus=2, n_minus=3)
+    rho, eta, steps = s.rates(maxit=1000, tol=1e-12)
+    s.close()
+    assert steps > 1
+    assert abs(rho - rho_ref) <= 2e-3 * rho_ref, (rho, rho_ref)
+    assert abs(eta - eta_ref) <= 2e-3 * eta_ref, (eta, eta_ref)
+    # the paper's bound eta <= c (Section 5.3) holds for the computed operators
+    assert eta <= 0.9 + 1e-9
