@@ -168,17 +168,29 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel group as last captured with ncu on the default workload (the summary
+# and command are in profiles/); a kernel changed since its capture has no
+# entry.  k_e0_pcg_f: mean of two captured launches of 13 PCG iterations.
+PROFILED_DRAM_BYTES = {'e0_cg_lo': 4.885e9}
+
+
 def kernel_work(name, d, nrhs, info):
     """Algorithmic work of one launch of a named kernel group: (amount, unit,
     bound).  Contractions count 2 M N K flops.  Memory-bound kernels count
     the bytes they must move once per launch:
       * transport A: read U^+ (FP64), write Z (FP64);
       * A^T + M^+ + R - K^+ gather: read Z, U^+ and U S^+, write Y;
-      * E_0 PCG (persistent): per CG iteration and (node, column) the level-0
-        CG traffic (7 stencil coefficients, P, AP write, X/R/P/AP updates,
-        z, V-cycle input: 18 words of the CG precision plus 16 B of FP64 X)
-        and the V-cycle's 18 FP32 array passes on every level (4^-l of the
-        level-0 size), times the iterations the launch took;
+      * E_0 PCG (persistent): per CG iteration the coarsest level's dense
+        per-direction inverses (read once per V-cycle) and, per (node, column), the level-0
+        CG vector traffic (P read and AP written by the apply; P, R, AP read,
+        R and V-cycle input written by the update; R, z read for r.z and
+        r.r; z, P read and P written by the direction update: 12 words of
+        the CG precision, plus 16 B of FP64 X) and the V-cycle's 17 FP32 array
+        passes per level (4^-l of the level-0 size), times the iterations the
+        launch took.  The FP32 kernel forms the stencil coefficients on chip
+        (224 B per node per pass, not counted); the FP64 kernel also reads 7
+        FP64 coefficients per item;
       * E_c PCG: per iteration the FP64 level-0 blocks (7 d^2 per node) and
         ~12 FP64 vector passes, plus the FP32 V-cycle (7 d^2 + 18 d words
         per node per sweep-equivalent, 4/3 for the coarser levels)."""
@@ -196,8 +208,11 @@ def kernel_work(name, d, nrhs, info):
     if name in ('e0_cg', 'e0_cg_lo'):
         ts = 8 if name == 'e0_cg' else 4
         cols = nrhs * nS
-        cg = nRp * cols * (18 * ts + 16)
-        vc = sum(nRp / 4 ** l * cols * 4 * 18 for l in range(d['e0_levels']))
+        cg = nRp * cols * (12 * ts + 16 + (7 * 8 if name == 'e0_cg' else 0))
+        vc = sum(nRp / 4 ** l * cols * 4 * 17 for l in range(d['e0_levels']))
+        # the coarsest level's dense per-direction inverses, read once per V-cycle
+        mc = d['mesh'] >> (d['e0_levels'] - 1)
+        vc += ((mc + 1) ** 2) ** 2 * nS * 4
         return (cg + vc) * max(info.get('e0_iters', 1), 1), 'byte', 'hbm'
     if name == 'coarse_cg':
         dp = d['dP']
@@ -284,11 +299,13 @@ def run_ours(args):
     top = max(tim.items(), key=lambda kv: kv[1][0])
     peaks, src = load_peaks()
     d['e0_levels'] = levels_of(args.mesh)
+    d['mesh'] = args.mesh
     d['dP'] = solver.d_plus
     work = kernel_work(top[0], d, p.nrhs, last_info)
     avg_ms = top[1][0] / max(top[1][1], 1)
     roof = dict(kernel=top[0], bound=None, achieved=None, peak=None, unit=None,
-                frac=None, traffic=None, launches=top[1][1], avg_ms=avg_ms)
+                frac=None, traffic=PROFILED_DRAM_BYTES.get(top[0]), launches=top[1][1],
+                avg_ms=avg_ms)
     if work is not None:
         amount, unit, bound = work
         if unit == 'flop' and bound == 'fp64':
