@@ -223,10 +223,10 @@ def kernel_work(name, d, nrhs, info):
 
 
 def levels_of(m, max_nodes=300):
-    """Multigrid levels the library builds for an m x m mesh (halving while
-    m is even, m >= 4 and the level has more than max_nodes nodes)."""
+    """Multigrid levels the library builds for an m x m mesh (m -> m // 2
+    while m >= 4 and the level has more than max_nodes nodes)."""
     lv = 1
-    while m % 2 == 0 and m >= 4 and (m + 1) ** 2 > max_nodes:
+    while m >= 4 and (m + 1) ** 2 > max_nodes:
         m //= 2
         lv += 1
     return lv

@@ -35,25 +35,21 @@ __device__ __forceinline__ int nbr(int i, int dir, int m, int n) {
     return j < 0 ? 0 : (j >= n ? n - 1 : j);
 }
 
-// restriction P^T: the (up to) 7 fine nodes that interpolate from coarse node
-// (X, Y); fine mesh mf = 2 mc
-__device__ __forceinline__ int restrict_src(int I, int mc, int q, float& w) {
-    const int dx[7] = {0, 1, -1, 0, 0, 1, -1};
-    const int dy[7] = {0, 0, 0, 1, -1, 1, -1};
-    const int X = I % (mc + 1), Y = I / (mc + 1), mf = 2 * mc;
-    const int x = 2 * X + dx[q], y = 2 * Y + dy[q];
-    if (x < 0 || y < 0 || x > mf || y > mf) {
-        w = 0.f;
-        return 0;
-    }
-    w = q == 0 ? 1.f : 0.5f;
-    return y * (mf + 1) + x;
+// restriction P^T: fine node q of coarse node I's list (the fine nodes that
+// interpolate from I, with their weights; width Cv.rwid, zero-weight padding)
+__device__ __forceinline__ int restrict_src(const MGDeviceLevel& Cv, int I, int q, float& w) {
+    const size_t k = (size_t)I * Cv.rwid + q;
+    w = __ldg(Cv.rw + k);
+    return __ldg(Cv.ridx + k);
 }
 
-// prolongation: coarse nodes (and weights) interpolating fine node i
+// prolongation: coarse nodes (and weights) interpolating fine node i; the
+// coarse mesh is the floor(mf/2)-mesh, and for odd mf the last fine column
+// and row take the values of the ones before them
 __device__ __forceinline__ void prolong_src(int i, int mf, int& c0, int& c1, float& w0,
                                             float& w1) {
-    const int mc = mf / 2, x = i % (mf + 1), y = i / (mf + 1);
+    const int mc = mf / 2;
+    const int x = min(i % (mf + 1), 2 * mc), y = min(i / (mf + 1), 2 * mc);
     if (!(x & 1) && !(y & 1)) {
         c0 = c1 = (y / 2) * (mc + 1) + x / 2;
         w0 = 1.f;
@@ -236,10 +232,9 @@ __device__ __noinline__ void e0_restrict(const MGDeviceLevel Cv, int nq,
          e += gridDim.x * blockDim.x) {
         const int i = (int)(e / (unsigned)nq), p = (int)(e % (unsigned)nq);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < 7; ++q) {
+        for (int q = 0; q < Cv.rwid; ++q) {
             float w;
-            const int f = restrict_src(i, Cv.m, q, w);
+            const int f = restrict_src(Cv, i, q, w);
             const float4 v = ld4(t + (size_t)f * nq + p);
             acc.x = fmaf(w, v.x, acc.x);
             acc.y = fmaf(w, v.y, acc.y);
@@ -1107,10 +1102,9 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         GROUP_LOOP(Cv.n)
             if (ok && gl < d) {
                 float acc = 0.f;
-#pragma unroll
-                for (int q = 0; q < 7; ++q) {
+                for (int q = 0; q < Cv.rwid; ++q) {
                     float w;
-                    const int f = restrict_src(i, Cv.m, q, w);
+                    const int f = restrict_src(Cv, i, q, w);
                     acc += w * ldg2(t + ((size_t)r * Lv.n + f) * d + gl);
                 }
                 Cv.B[base + gl] = acc;

@@ -1,6 +1,7 @@
 // Device-side multigrid hierarchy shared by the E_0 and E_c solvers.
 //
-// Every level is the uniform (m+1) x (m+1) node grid of an m x m "/"-mesh.
+// Every level is the uniform (m+1) x (m+1) node grid of an m x m "/"-mesh;
+// level l+1 is the floor(m/2)-mesh of level l.
 // Operators are stored in ELL form over the 7 stencil directions
 //   0: self, 1: +x, 2: -x, 3: +y, 4: -y, 5: +x+y, 6: -x-y
 // (zero coefficients where a neighbour does not exist), so neighbour,
@@ -17,6 +18,11 @@ struct MGDeviceLevel {
     const float* dinv = nullptr;   // E_c: [n][d][d] inverse diagonal blocks, transposed
     const float* sv = nullptr;     // E_0: the six spatial parts, node-major [n][7][8]
     float *X = nullptr, *Xt = nullptr, *B = nullptr;   // work vectors
+    // restriction from the next finer level: for each node of this level,
+    // rwid fine nodes and weights (zero-weight padding); unset on level 0
+    const int* ridx = nullptr;
+    const float* rw = nullptr;
+    int rwid = 0;
 };
 
 struct MGDevice {

@@ -1,14 +1,18 @@
-// Geometric multigrid hierarchy on the nested "/"-triangulations of the unit
+// Geometric multigrid hierarchy on the "/"-triangulations of the unit
 // square, used to precondition the conjugate-gradient solves of the E_0
 // direction blocks and of the coarse Galerkin system E_c.
 //
-// Refining the m/2 x m/2 "/"-mesh by edge midpoints gives exactly the m x m
-// "/"-mesh, so the coarse P1 space is a subspace of the fine one and the
+// Coarse level of an m-mesh: the floor(m/2)-mesh.  For even m, refining the
+// coarse mesh by edge midpoints gives exactly the fine mesh, and the
 // prolongation is linear interpolation: a fine node that is also a coarse
 // node keeps its value, a fine node at the midpoint of a coarse edge
 // (horizontal, vertical or the "/" diagonal) takes the mean of the edge's two
-// ends.  Coarse operators are Galerkin products P^T A P of the fine ones,
-// which keep the 7-point pattern of the coarse mesh.
+// ends.  For odd m the fine nodes of the last column (and row) take the
+// values of the column (row) before them, x -> min(x, m - 1): the coarse
+// space is then the interpolants on [0, (m-1)/m]^2 extended constantly over
+// the last fine cell, and every fine coupling still lands inside the coarse
+// 7-point pattern.  Coarse operators are Galerkin products P^T A P of the
+// fine ones.
 #include <algorithm>
 #include <cmath>
 #include <set>
@@ -39,16 +43,17 @@ Stencil stencil_of_square(int m) {
     return st;
 }
 
-// Prolongation from the (m/2)-mesh to the m-mesh: up to two coarse nodes per
-// fine node with weights.
+// Prolongation from the floor(m/2)-mesh to the m-mesh: up to two coarse
+// nodes per fine node with weights.
 static void prolongation(int mf, std::vector<int>& p0, std::vector<int>& p1,
                          std::vector<float>& w0, std::vector<float>& w1) {
     const int mc = mf / 2, nf = (mf + 1) * (mf + 1);
     p0.assign(nf, 0); p1.assign(nf, -1); w0.assign(nf, 0.f); w1.assign(nf, 0.f);
     auto cid = [&](int x, int y) { return y * (mc + 1) + x; };
-    for (int y = 0; y <= mf; ++y)
-        for (int x = 0; x <= mf; ++x) {
-            const int f = y * (mf + 1) + x;
+    for (int yf = 0; yf <= mf; ++yf)
+        for (int xf = 0; xf <= mf; ++xf) {
+            const int f = yf * (mf + 1) + xf;
+            const int x = std::min(xf, 2 * mc), y = std::min(yf, 2 * mc);
             if (x % 2 == 0 && y % 2 == 0) {
                 p0[f] = cid(x / 2, y / 2); w0[f] = 1.f;
             } else if (x % 2 == 1 && y % 2 == 0) {        // horizontal edge
@@ -148,11 +153,11 @@ int build_hierarchy(int m, const Stencil& fine, const std::vector<double>& vals0
     L0.st = fine;
     L0.vals = vals0;
     out.levels.push_back(std::move(L0));
-    // coarsen while the mesh halves exactly and the level is not yet small
+    // coarsen while the level is not yet small
     while (true) {
         MGHostLevel& f = out.levels.back();
         const int nf = (f.m + 1) * (f.m + 1);
-        if (f.m % 2 != 0 || f.m < 4 || nf <= max_coarse_nodes) break;
+        if (f.m < 4 || nf <= max_coarse_nodes) break;
         MGHostLevel c;
         c.m = f.m / 2;
         c.st = stencil_of_square(c.m);

@@ -18,8 +18,14 @@ struct GridBar {
     int pad;
 };
 
-// Spins of ~128 ns before a barrier gives up (about 2 s).
-constexpr unsigned long long kSpinLimit = 1ull << 24;
+// A barrier wait gives up after this many nanoseconds (2 s).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // All blocks of the (co-resident) grid meet here.  A wait that runs out sets
 // gb->err, and every later barrier returns false at once, so the kernel can
@@ -37,13 +43,17 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb) {
             __threadfence();
             atomicAdd(&gb->gen, 1u);
         } else {
-            unsigned long long spins = 0;
+            // plain polling (a sleep between polls costs more than it saves
+            // at these barrier rates); the limit is checked every 256 polls
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
             while (*vgen == g) {
-                __nanosleep(128);
-                if (*verr) break;
-                if (++spins > kSpinLimit) {
-                    atomicExch(&gb->err, 1);
-                    break;
+                if ((++spins & 255u) == 0) {
+                    if (*verr) break;
+                    if (global_ns() - t0 > kWaitLimitNs) {
+                        atomicExch(&gb->err, 1);
+                        break;
+                    }
                 }
             }
         }

@@ -329,6 +329,24 @@ void transpose_blocks(std::vector<V>& a, int bs) {
             for (int y = x + 1; y < bs; ++y) std::swap(a[o + x * bs + y], a[o + y * bs + x]);
 }
 
+// Restriction lists of level D from its finer level F (ELL over D's nodes:
+// the fine nodes that interpolate from each coarse node, with weights).
+int upload_restriction(rte_handle* h, const MGHostLevel& F, MGDeviceLevel& D) {
+    int w = 0;
+    for (int I = 0; I < D.n; ++I) w = std::max(w, F.rptr[I + 1] - F.rptr[I]);
+    std::vector<int> ri((size_t)D.n * w, 0);
+    std::vector<float> rwv((size_t)D.n * w, 0.f);
+    for (int I = 0; I < D.n; ++I)
+        for (int k = F.rptr[I]; k < F.rptr[I + 1]; ++k) {
+            ri[(size_t)I * w + (k - F.rptr[I])] = F.ridx[k];
+            rwv[(size_t)I * w + (k - F.rptr[I])] = F.rw[k];
+        }
+    RTE_TRY(upload(h, &D.ridx, ri));
+    RTE_TRY(upload(h, &D.rw, rwv));
+    D.rwid = w;
+    return RTE_OK;
+}
+
 // Uploads a host multigrid hierarchy in ELL form; work vectors hold cols
 // columns of bs values per node.
 int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv,
@@ -355,6 +373,7 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
             transpose_blocks(di, bs);
             RTE_TRY(upload(h, &D.dinv, di));
         }
+        if (l > 0) RTE_TRY(upload_restriction(h, mh.levels[l - 1], D));
         const size_t nv = (size_t)D.n * cols * bs;
         RTE_TRY(dalloc(h, &D.X, nv));
         RTE_TRY(dalloc(h, &D.Xt, nv));
@@ -470,6 +489,17 @@ int tune_launches(rte_handle* h) {
     const int nr = h->cap_rhs;
     cudaStream_t s = h->stream;
     auto ok = [] { return cudaGetLastError() == cudaSuccess ? RTE_OK : RTE_ERR_CUDA; };
+    // defined operands (zeros) for the timing runs, sizes as in alloc_workspace
+    const size_t ne = (size_t)nr * d.nRp * d.nSp, no = (size_t)nr * d.nRm * d.nSm;
+    RTE_CUDA_TRY(cudaMemsetAsync(h->e1, 0, ne * sizeof(double), s));
+    RTE_CUDA_TRY(cudaMemsetAsync(h->z2, 0, no * sizeof(double), s));
+    if (h->mixed) {
+        const size_t lo = d.lo.bf16 ? 2 : 4;
+        RTE_CUDA_TRY(cudaMemsetAsync(h->zl1, 0, no * lo, s));
+        RTE_CUDA_TRY(cudaMemsetAsync(h->zl2, 0, no * lo, s));
+        RTE_CUDA_TRY(cudaMemsetAsync(h->f1, 0, ne * sizeof(float), s));
+        RTE_CUDA_TRY(cudaMemsetAsync(h->xl, 0, ne * lo, s));
+    }
     const int tpb[3] = {128, 256, 512};
     char key[200];
     int b = 1;
@@ -478,14 +508,14 @@ int tune_launches(rte_handle* h) {
         d.tpb_A = tpb[c];
         apply_A(s, d, h->e1, h->z1, nr);
         return ok();
-    }, &b));
+    }, &b, 1));
     d.tpb_A = tpb[b];
     std::snprintf(key, sizeof key, "apply_even m=%d nS=%d rhs=%d", d.m, d.nSp, nr);
     RTE_TRY(autotune(s, key, 3, [&](int c) {
         d.tpb_even = tpb[c];
         apply_even(s, d, h->z2, h->e1, nullptr, h->e2, nr, 3);
         return ok();
-    }, &b));
+    }, &b, 1));
     d.tpb_even = tpb[b];
     if (!h->mixed) return RTE_OK;
     const bool bf = d.lo.bf16;
@@ -498,12 +528,14 @@ int tune_launches(rte_handle* h) {
     g.out_bf16 = bf;
     std::snprintf(key, sizeof key, "tc_gemm %s M=%d N=%d K=%d epi=1", bf ? "bf16" : "tf32", g.M,
                   g.N, g.K);
-    RTE_TRY(autotune(s, key, 2, [&](int c) { g.bn = bns[c]; return tc_gemm(s, g); }, &b));
+    RTE_TRY(autotune(s, key, 2, [&](int c) { g.bn = bns[c]; return tc_gemm(s, g); }, &b,
+                     g.N > 128 ? 1 : 0));
     h->bn_mk1 = bns[b];
     g.A = h->zl2; g.Bt = d.lo.Vm; g.C = h->zf; g.epi = 0; g.out_bf16 = false;
     std::snprintf(key, sizeof key, "tc_gemm %s M=%d N=%d K=%d epi=0", bf ? "bf16" : "tf32", g.M,
                   g.N, g.K);
-    RTE_TRY(autotune(s, key, 2, [&](int c) { g.bn = bns[c]; return tc_gemm(s, g); }, &b));
+    RTE_TRY(autotune(s, key, 2, [&](int c) { g.bn = bns[c]; return tc_gemm(s, g); }, &b,
+                     g.N > 128 ? 1 : 0));
     h->bn_mk2 = bns[b];
     TcGemmArgs k{};
     k.tf32 = !bf;
@@ -512,7 +544,8 @@ int tune_launches(rte_handle* h) {
     k.M = nr * d.nRp; k.N = d.nSp; k.K = d.nSp; k.ldc = d.nSp; k.rows = 1;
     std::snprintf(key, sizeof key, "tc_gemm %s M=%d N=%d K=%d epi=0", bf ? "bf16" : "tf32", k.M,
                   k.N, k.K);
-    RTE_TRY(autotune(s, key, 2, [&](int c) { k.bn = bns[c]; return tc_gemm(s, k); }, &b));
+    RTE_TRY(autotune(s, key, 2, [&](int c) { k.bn = bns[c]; return tc_gemm(s, k); }, &b,
+                     k.N > 128 ? 1 : 0));
     h->bn_kplus = bns[b];
     return tc_gemm_error(s);
 }

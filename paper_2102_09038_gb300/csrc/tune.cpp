@@ -24,7 +24,7 @@ std::map<std::string, Entry> g_table;
 }  // namespace
 
 int autotune(cudaStream_t s, const std::string& key, int ncand,
-             const std::function<int(int)>& run, int* best, int reps) {
+             const std::function<int(int)>& run, int* best, int def, int reps) {
     if (ncand < 1 || !best) return fail(RTE_ERR_ARG, "autotune: no candidates");
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -42,23 +42,34 @@ int autotune(cudaStream_t s, const std::string& key, int ncand,
     }
     Entry e;
     e.ms.assign(ncand, -1.f);
-    float best_ms = 0.f;
-    int pick = -1;
-    for (int c = 0; c < ncand; ++c) {
-        if (run(c) != RTE_OK) continue;   // warm-up; a refused candidate is skipped
-        cudaEventRecord(a, s);
-        int rc = RTE_OK;
-        for (int r = 0; r < reps && rc == RTE_OK; ++r) rc = run(c);
-        cudaEventRecord(b, s);
-        if (rc != RTE_OK || cudaEventSynchronize(b) != cudaSuccess) continue;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, a, b);
-        e.ms[c] = ms / reps;
-        if (pick < 0 || e.ms[c] < best_ms) {
-            pick = c;
-            best_ms = e.ms[c];
+    std::vector<bool> bad(ncand, false);
+    for (int c = 0; c < ncand; ++c) bad[c] = run(c) != RTE_OK;   // warm-up
+    // three rounds over the candidates in turn, the best round of each counts
+    // (clock ramps and other work on the GPU affect all candidates alike)
+    for (int round = 0; round < 3; ++round)
+        for (int c = 0; c < ncand; ++c) {
+            if (bad[c]) continue;
+            cudaEventRecord(a, s);
+            int rc = RTE_OK;
+            for (int r = 0; r < reps && rc == RTE_OK; ++r) rc = run(c);
+            cudaEventRecord(b, s);
+            if (rc != RTE_OK || cudaEventSynchronize(b) != cudaSuccess) {
+                bad[c] = true;
+                continue;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            ms /= reps;
+            if (e.ms[c] < 0.f || ms < e.ms[c]) e.ms[c] = ms;
         }
-    }
+    int pick = -1;
+    for (int c = 0; c < ncand; ++c)
+        if (!bad[c] && e.ms[c] >= 0.f && (pick < 0 || e.ms[c] < e.ms[pick])) pick = c;
+    // keep the default shape unless another one is clearly (3 %) faster:
+    // differences below that are within the timing noise of a setup-time run
+    if (pick >= 0 && def >= 0 && def < ncand && !bad[def] && e.ms[def] >= 0.f &&
+        e.ms[pick] > 0.97f * e.ms[def])
+        pick = def;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (pick < 0) return fail(RTE_ERR_CUDA, "autotune: no candidate of " + key + " ran");

@@ -1,0 +1,101 @@
+"""The workload configurations at full size, through the C ABI.
+
+Each solution's residual is measured in the oracle's exact FP64 operator
+(assembled on the CPU, independently of the library): the configurations
+are too large for the oracle to solve, but the residual of a given vector
+takes it seconds.  Mixed-precision solutions are compared with the FP64 GPU
+solution of the same problem (the stated solution errors), and batched
+solves of uneven instances (odd meshes included) are checked per result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip('torch')
+
+
+def gpu_solve(p, tol, **opts):
+    import paper_2102_09038_gb300 as rte
+    s = rte.Solver(p, max_rhs=p.nrhs, **opts)
+    q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
+    u, info = s.solve(q, tol=tol)
+    out = u.cpu().numpy()
+    s.close()
+    assert info['status'] == 0, info
+    return out, info
+
+
+def oracle_residual(p, u):
+    disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+    ops = oracle.Operators(disc)
+    out = []
+    for r in range(p.nrhs):
+        q = disc.source(p.q_nodal[r])
+        out.append(np.linalg.norm(ops.apply_EK(u[r]) - q) / np.linalg.norm(q))
+    return max(out)
+
+
+def relerr(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_config1_plain_fp64():
+    # 32x32 mesh, 128 triangles, g = 0.5, sigma_s = 0.5: FP64 to 1e-10
+    p = workloads.plain_fp64()
+    u, info = gpu_solve(p, 1e-10, precision=0)
+    assert info['rel_residual'] <= 1e-10
+    assert oracle_residual(p, u) <= 1.05e-10
+
+
+def test_config2_checkerboard_modes():
+    # 128x128, 512 triangles, g = 0.9, c = 0.99, checkerboard sigma_t:
+    # (1) the benchmark's mode and tolerance, judged by the oracle;
+    # (2) the mixed modes against FP64 at a tight tolerance
+    p = workloads.checkerboard(m=128, levels=3, g=0.9, ratio=0.99, seed=0)
+    ub, info = gpu_solve(p, 1e-6, precision=2)
+    assert info['iterations'] <= 30
+    assert oracle_residual(p, ub) <= 1.05e-6
+    u64, _ = gpu_solve(p, 1e-10, precision=0)
+    u32, _ = gpu_solve(p, 1e-10, precision=1)
+    u16, _ = gpu_solve(p, 1e-10, precision=2)
+    assert relerr(u32, u64) <= 1e-6
+    assert relerr(u16, u64) <= 1e-4
+    assert oracle_residual(p, u16) <= 1.05e-10
+
+
+def test_config3_precision_2048_triangles():
+    # 96x96, 2048 triangles (1024 even directions), g = 0.8, c = 0.999:
+    # BF16/FP32 scattering with FP64 residual and coarse solve, against the
+    # FP64 path (split FP64 GEMMs) at 1e-8
+    import paper_2102_09038_gb300 as rte
+    p = workloads.precision_case(g=0.8)
+    u64, _ = gpu_solve(p, 1e-8, precision=0, dgemm=rte.DGEMM_SPLIT)
+    u16, _ = gpu_solve(p, 1e-8, precision=2)
+    u32, _ = gpu_solve(p, 1e-8, precision=1)
+    assert relerr(u32, u64) <= 1e-6
+    assert relerr(u16, u64) <= 1e-4
+    assert oracle_residual(p, u16) <= 1.05e-8
+
+
+def test_config4_uneven_batch_with_odd_meshes():
+    # instances of the batching configuration (meshes 32..128, odd ones
+    # included, 128/512 triangles, 1-8 right-hand sides), solved together by
+    # the server; every result reaches its tolerance, two are checked by the
+    # oracle
+    import paper_2102_09038_gb300 as rte
+    insts = workloads.batch_instances(64, seed=0)
+    picked = [insts[i] for i in (0, 1, 3, 4, 5, 7)]
+    assert any(p.m % 2 for p in picked)
+    sv = rte.Server(hbm_budget_bytes=64 << 30, slots=3, precision=2)
+    ids = [sv.submit(p, p.q_nodal, tol=1e-6) for p in picked]
+    results = [sv.wait(rid) for rid in ids]
+    sv.close()
+    for p, (u, info) in zip(picked, results):
+        assert info['rel_residual'] <= 1e-6, (p.m, info)
+        assert info['iterations'] <= 40, (p.m, info)
+    for k in (1, 3):   # m = 110 and m = 101 (odd coarse levels)
+        p, (u, _) = picked[k], results[k]
+        assert oracle_residual(p, u) <= 1.05e-6

@@ -112,7 +112,8 @@ def test_mixed_solve_reaches_fp64_residual(mixed):
 
 @pytest.mark.parametrize('prec', [1, 2])
 def test_autotuned_launch_shapes(prec):
-    # the tuner picks one candidate per kernel shape, and the picked shapes
+    # the tuner picks one candidate per kernel shape (the fastest, unless the
+    # default is within 3 % of it), and the picked shapes
     # give the same result as the fixed ones: each output is summed in the
     # same order whatever the block size or tile width
     import paper_2102_09038_gb300 as rte
@@ -125,7 +126,9 @@ def test_autotuned_launch_shapes(prec):
     assert any(k.startswith('apply_even') for k in keys)
     assert any(k.startswith('tc_gemm %s' % ('bf16' if prec == 2 else 'tf32')) for k in rep)
     for choice, ms in rep.values():
-        assert 0 <= choice < len(ms) and ms[choice] > 0 and ms[choice] == min(v for v in ms if v > 0)
+        # the fastest, or the default shape within 3 % of the fastest
+        assert 0 <= choice < len(ms) and ms[choice] > 0
+        assert ms[choice] <= min(v for v in ms if v > 0) / 0.97 * (1 + 1e-6)
     x = torch.tensor(np.random.default_rng(5).standard_normal((1, tuned.n_nodes, tuned.n_dirs)),
                      dtype=torch.float64, device='cuda')
     for op in ('EK_LO', 'A'):

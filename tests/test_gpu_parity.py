@@ -36,6 +36,9 @@ CASES = {
     'g0': lambda: workloads.constant(4, 1, 0.0, 2.0, 1.5, 1.0),
     # no scattering: K = 0, c = 0
     'nosc': lambda: workloads.constant(4, 1, 0.6, 2.0, 0.0, 1.0),
+    # odd meshes on two multigrid levels (35 -> 17 -> 8, the last dense)
+    'odd35': lambda: workloads.checkerboard(m=35, levels=2, g=0.8, ratio=0.97, blocks=5,
+                                            nrhs=1),
 }
 
 
