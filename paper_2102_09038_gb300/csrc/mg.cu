@@ -952,8 +952,10 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
 // transposed, [dir][n][b][a], so the lanes of a group read consecutive words.
 struct EcMG {
     int L, nrhs, d, nu, G;
+    int Q;                 // Kronecker terms of the levels (0: explicit blocks)
     bool dense;
     const float* cinv;     // [(n_c d)][(n_c d)]
+    const float* Gq;       // angular blocks of the terms [Q][d][d] (Q > 0)
     const MGDeviceLevel* lev;   // [L], in device memory
 };
 
@@ -988,6 +990,45 @@ __device__ __forceinline__ float ec_apply(const MGDeviceLevel& L, const float* x
         for (int b = 0; b < d; ++b) y += __ldg(blk + (size_t)b * d) * ldg2(xv + b);
     }
     return y;
+}
+
+// The same product with the level in Kronecker form, sum_q S_q (x) G_q:
+// t_q = sum_dir S_q(i, nbr) x_nbr (lane a holds component a), then
+// y_a = sum_q sum_b G_q[a][b] t_q[b] with t_q[b] from lane b of the group.
+// The stencils are node-major [n][7][Qp]; sG holds the G_q in shared memory.
+// Every lane of the warp must call this (shuffles).
+constexpr int kEcMaxQ = 16;
+__device__ __forceinline__ float ec_apply_kron(const MGDeviceLevel& L, const float* sG, int Q,
+                                               const float* x, int r, int i, int d, int G,
+                                               int gl, bool act) {
+    const int qp4 = (Q + 3) >> 2;
+    const float4* sk = reinterpret_cast<const float4*>(L.sv) + (size_t)i * 7 * qp4;
+    const float* xr = x + (size_t)r * L.n * d;
+    float t[kEcMaxQ];
+#pragma unroll
+    for (int q = 0; q < kEcMaxQ; ++q) t[q] = 0.f;
+#pragma unroll
+    for (int dir = 0; dir < 7; ++dir) {
+        const float xv = act ? ldg2(xr + (size_t)nbr(i, dir, L.m, L.n) * d + gl) : 0.f;
+#pragma unroll
+        for (int q4 = 0; q4 < kEcMaxQ / 4; ++q4) {
+            if (q4 >= qp4) break;
+            const float4 s4 = __ldg(sk + dir * qp4 + q4);
+            t[4 * q4 + 0] = fmaf(s4.x, xv, t[4 * q4 + 0]);
+            t[4 * q4 + 1] = fmaf(s4.y, xv, t[4 * q4 + 1]);
+            t[4 * q4 + 2] = fmaf(s4.z, xv, t[4 * q4 + 2]);
+            t[4 * q4 + 3] = fmaf(s4.w, xv, t[4 * q4 + 3]);
+        }
+    }
+    float y = 0.f;
+    const int row = act ? gl : 0;
+#pragma unroll
+    for (int q = 0; q < kEcMaxQ; ++q) {
+        if (q >= Q) break;
+        const float* g = sG + ((size_t)q * d + row) * d;
+        for (int b = 0; b < d; ++b) y = fmaf(g[b], __shfl_sync(0xffffffffu, t[q], b, G), y);
+    }
+    return act ? y : 0.f;
 }
 
 // (D v)_a for the group's vector v (value b held by group lane b)
@@ -1053,9 +1094,13 @@ __device__ void rhs_flush(RhsSum& s, double* dst, double* sh_v, int* sh_r) {
     s.r = -1;
 }
 
-__device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
+__device__ bool ec_vcycle(const EcMG& mg, const float* sG, GridBar* bar, float*& z) {
     const int d = mg.d, G = mg.G, gpw = 32 / G;
     const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
+    auto apply = [&](const MGDeviceLevel& Lv, const float* x, int r, int i, bool act) {
+        return mg.Q ? ec_apply_kron(Lv, sG, mg.Q, x, r, i, d, G, gl, act)
+                    : ec_apply(Lv, x, r, i, d, gl, act);
+    };
     int cur[kMaxMGLevels];
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf = [&](int l, int which) { return which ? mg.lev[l].Xt : mg.lev[l].X; };
@@ -1065,7 +1110,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         float* xt = buf(l, cur[l] ^ 1);
         GROUP_LOOP(Lv.n)
             const bool act = ok && gl < d;
-            const float y = ec_apply(Lv, x, r, i, d, gl, act);
+            const float y = apply(Lv, x, r, i, act);
             const float res = act ? ldg2(Lv.B + base + gl) - y : 0.f;
             const float dx = ec_dmul(Lv.dinv + (size_t)i * d * d, d, G, res, gl, act);
             if (act) xt[base + gl] = ldg2(x + base + gl) + kOmega * dx;
@@ -1094,7 +1139,7 @@ __device__ bool ec_vcycle(const EcMG& mg, GridBar* bar, float*& z) {
         float* t = buf(l, cur[l] ^ 1);
         GROUP_LOOP(Lv.n)
             const bool act = ok && gl < d;
-            const float y = ec_apply(Lv, x, r, i, d, gl, act);
+            const float y = apply(Lv, x, r, i, act);
             if (act) t[base + gl] = ldg2(Lv.B + base + gl) - y;
         }}
         if (!grid_sync(bar)) return false;
@@ -1196,7 +1241,10 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     __shared__ int s_stop;
     __shared__ double sh_v[32];
     __shared__ int sh_r[32];
+    __shared__ float sG[kEcMaxQ * 16 * 16];   // angular blocks of the Kronecker terms
     if (threadIdx.x == 0) s_stop = 0;
+    for (int t = threadIdx.x; t < a.mg.Q * a.d * a.d; t += blockDim.x) sG[t] = __ldg(a.mg.Gq + t);
+    __syncthreads();
     const EcMG& mg = a.mg;
     const int d = a.d, G = mg.G, gpw = 32 / G;
     const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
@@ -1215,7 +1263,7 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     rhs_flush(sum, a.bb, sh_v, sh_r);
     if (!grid_sync(a.bar)) return;
     float* z = nullptr;
-    if (!ec_vcycle(mg, a.bar, z)) return;
+    if (!ec_vcycle(mg, sG, a.bar, z)) return;
     GROUP_LOOP(a.nRp)
         if (ok && gl < d) {
             const double zv = ldg2(z + base + gl);
@@ -1268,7 +1316,7 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
         }}
         rhs_flush(sum, sl(cur, 2), sh_v, sh_r);
         if (!grid_sync(a.bar)) return;
-        if (!ec_vcycle(mg, a.bar, z)) return;
+        if (!ec_vcycle(mg, sG, a.bar, z)) return;
         GROUP_LOOP(a.nRp)
             if (ok && gl < d && ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r))
                 sum.add(ldg2(a.R + base + gl) * (double)ldg2(z + base + gl), r, sl(cur, 1));
@@ -1459,6 +1507,10 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     a.mg.nrhs = nrhs;
     a.mg.d = d.dP;
     a.mg.G = d.dP <= 8 ? 8 : (d.dP <= 16 ? 16 : 32);
+    a.mg.Q = d.ecmg.Q;
+    a.mg.Gq = d.ecmg.G;
+    if (a.mg.Q > kEcMaxQ || (a.mg.Q > 0 && d.dP > 16))
+        return fail(RTE_ERR_ARG, "Kronecker coarse multigrid: at most 16 terms of d <= 16");
     const void* fn = (const void*)k_ec_pcg;
     const int grid = coop_grid(fn, 256);
     void* args[] = {&a};

@@ -16,7 +16,7 @@ struct MGDeviceLevel {
     int m = 0, n = 0;
     const float* val = nullptr;    // E_c: [7][n][d][d], blocks transposed
     const float* dinv = nullptr;   // E_c: [n][d][d] inverse diagonal blocks, transposed
-    const float* sv = nullptr;     // E_0: the six spatial parts, node-major [n][7][8]
+    const float* sv = nullptr;     // E_0: six spatial parts [n][7][8]; E_c: Q terms [n][7][Qp]
     float *X = nullptr, *Xt = nullptr, *B = nullptr;   // work vectors
     // restriction from the next finer level: for each node of this level,
     // rwid fine nodes and weights (zero-weight padding); unset on level 0
@@ -29,6 +29,8 @@ struct MGDevice {
     int L = 0, nu = 2, cap_cols = 0;
     bool dense = false;
     const float* cinv = nullptr;   // coarsest dense inverse(s)
+    int Q = 0;                     // E_c only: number of Kronecker terms (0: blocks)
+    const float* G = nullptr;      // E_c only: angular blocks of the terms [Q][d][d]
     const float* w8 = nullptr;     // E_0 only: per-direction weights [nSp][8], six used
     const float* wq = nullptr;     // E_0 only: the same weights [6][nSp]
     MGDeviceLevel lev[kMaxMGLevels];

@@ -49,6 +49,10 @@ struct rte_handle {
     // host copies kept for rte_export
     std::vector<double> h_Sp, h_Sm, h_m, h_MSm, h_A1, h_A2, h_omx, h_omy, h_lamP,
         h_lamM, h_WpN, h_ec;
+    // E_c = sum_q S_q (x) G_q: Q scalar stencils [Q][nnz] and Q angular
+    // d x d blocks (Q = 0: no Kronecker form, the explicit blocks are used)
+    int ec_Q = 0;
+    std::vector<double> h_ecS, h_ecG;
     // workspace
     int cap_rhs = 0;
     double *z1 = nullptr, *z2 = nullptr, *z3 = nullptr, *z4 = nullptr;   // odd
@@ -347,6 +351,60 @@ int upload_restriction(rte_handle* h, const MGHostLevel& F, MGDeviceLevel& D) {
     return RTE_OK;
 }
 
+// Uploads the multigrid hierarchy of E_c in Kronecker form: per level the Q
+// scalar stencils node-major [n][7][Qp] (Qp = Q rounded up to 4), the
+// inverted diagonal blocks sum_q S_q(i,i) G_q, and the work vectors of d
+// values per node; the angular blocks G_q (Q x d x d) are shared by all
+// levels.
+int upload_mg_kron(rte_handle* h, const MGHost& mh, int cols, int d, int Q,
+                   const std::vector<double>& G, MGDevice& out) {
+    out.L = (int)mh.levels.size();
+    if (out.L > kMaxMGLevels) return fail(RTE_ERR_ARG, "too many multigrid levels");
+    out.nu = std::max(1, std::min(h->opt.mg_sweeps, 16));
+    out.cap_cols = cols;
+    out.dense = mh.dense_coarse;
+    out.Q = Q;
+    const int Qp = (Q + 3) / 4 * 4;
+    const size_t dd = (size_t)d * d;
+    for (int l = 0; l < out.L; ++l) {
+        const MGHostLevel& L = mh.levels[l];
+        MGDeviceLevel& D = out.lev[l];
+        D.m = L.m;
+        D.n = (L.m + 1) * (L.m + 1);
+        std::vector<double> ell;
+        RTE_TRY(to_ell(L, Q, 1, ell));   // [Q][7][n]
+        std::vector<float> sk((size_t)D.n * 7 * Qp, 0.f);
+        for (int i = 0; i < D.n; ++i)
+            for (int dir = 0; dir < 7; ++dir)
+                for (int q = 0; q < Q; ++q)
+                    sk[((size_t)i * 7 + dir) * Qp + q] = (float)ell[((size_t)q * 7 + dir) * D.n + i];
+        RTE_TRY(upload(h, &D.sv, sk));
+        std::vector<float> di((size_t)D.n * dd);
+        std::vector<double> blk(dd), inv(dd);
+        for (int i = 0; i < D.n; ++i) {
+            std::fill(blk.begin(), blk.end(), 0.0);
+            for (int q = 0; q < Q; ++q) {
+                const double sq = ell[((size_t)q * 7 + 0) * D.n + i];
+                if (sq == 0.0) continue;
+                for (size_t t = 0; t < dd; ++t) blk[t] += sq * G[(size_t)q * dd + t];
+            }
+            if (!chol_inv_sym(d, blk.data(), inv.data()))
+                return fail(RTE_ERR_ARG, "singular coarse multigrid diagonal block");
+            for (size_t t = 0; t < dd; ++t) di[(size_t)i * dd + t] = (float)inv[t];
+        }
+        transpose_blocks(di, d);
+        RTE_TRY(upload(h, &D.dinv, di));
+        if (l > 0) RTE_TRY(upload_restriction(h, mh.levels[l - 1], D));
+        const size_t nv = (size_t)D.n * cols * d;
+        RTE_TRY(dalloc(h, &D.X, nv));
+        RTE_TRY(dalloc(h, &D.Xt, nv));
+        RTE_TRY(dalloc(h, &D.B, nv));
+    }
+    std::vector<float> gf(G.begin(), G.end());
+    RTE_TRY(upload(h, &out.G, gf));
+    return RTE_OK;
+}
+
 // Uploads a host multigrid hierarchy in ELL form; work vectors hold cols
 // columns of bs values per node.
 int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv,
@@ -381,6 +439,10 @@ int upload_mg(rte_handle* h, const MGHost& mh, int cols, int bs, bool block_dinv
     }
     return RTE_OK;
 }
+
+// The multigrid of E_c uses its Kronecker form when it has at most this many
+// terms (4 + 4 per sigma class) and d^+ <= 16, else the explicit d x d blocks.
+constexpr int kEcMaxTerms = 16;
 
 // Coarsening stops at a level of at most this many nodes, which is then
 // solved with a dense inverse.
@@ -453,18 +515,51 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
     // ------------------------------------------------------------ E_c
     if (d.dP > 0) {
         MGHost mh;
-        RTE_TRY(build_hierarchy(hs.m, hs.st, h->h_ec, 1, d.dP, kDenseCoarseNodes, mh));
-        RTE_TRY(upload_mg(h, mh, cap, d.dP, true, d.ecmg));
-        if (d.ecmg.dense) {
-            std::vector<double> A;
-            coarse_dense_matrix(mh.levels.back(), {}, 1, d.dP, A);
-            std::vector<float> inv;
-            const int N = (mh.levels.back().m + 1) * (mh.levels.back().m + 1) * d.dP;
-            RTE_TRY(spd_inverse_batch(h, N, 1, A, inv));
-            RTE_TRY(upload(h, &d.ecmg.cinv, inv));
+        const int dP = d.dP;
+        if (h->ec_Q > 0) {   // Kronecker form: Galerkin products of Q scalar stencils
+            const int Q = h->ec_Q;
+            RTE_TRY(build_hierarchy(hs.m, hs.st, h->h_ecS, Q, 1, kDenseCoarseNodes, mh));
+            RTE_TRY(upload_mg_kron(h, mh, cap, dP, Q, h->h_ecG, d.ecmg));
+            if (d.ecmg.dense) {
+                const MGHostLevel& L = mh.levels.back();
+                const int n = (L.m + 1) * (L.m + 1), N = n * dP;
+                const size_t nnz = L.st.col.size(), dd = (size_t)dP * dP;
+                std::vector<double> A((size_t)N * N, 0.0);
+                for (int i = 0; i < n; ++i)
+                    for (int k = L.st.ptr[i]; k < L.st.ptr[i + 1]; ++k) {
+                        const int j = L.st.col[k];
+                        for (int q = 0; q < Q; ++q) {
+                            const double sq = L.vals[(size_t)q * nnz + k];
+                            if (sq == 0.0) continue;
+                            const double* g = &h->h_ecG[(size_t)q * dd];
+                            for (int a = 0; a < dP; ++a)
+                                for (int b = 0; b < dP; ++b)
+                                    A[(size_t)(i * dP + a) * N + j * dP + b] += sq * g[a * dP + b];
+                        }
+                    }
+                std::vector<float> inv;
+                RTE_TRY(spd_inverse_batch(h, N, 1, A, inv));
+                RTE_TRY(upload(h, &d.ecmg.cinv, inv));
+            }
+        } else {
+            RTE_TRY(build_hierarchy(hs.m, hs.st, h->h_ec, 1, dP, kDenseCoarseNodes, mh));
+            RTE_TRY(upload_mg(h, mh, cap, dP, true, d.ecmg));
+            if (d.ecmg.dense) {
+                std::vector<double> A;
+                coarse_dense_matrix(mh.levels.back(), {}, 1, dP, A);
+                std::vector<float> inv;
+                const int N = (mh.levels.back().m + 1) * (mh.levels.back().m + 1) * dP;
+                RTE_TRY(spd_inverse_batch(h, N, 1, A, inv));
+                RTE_TRY(upload(h, &d.ecmg.cinv, inv));
+            }
         }
+        // FP64 level-0 blocks of the CG's own apply
+        MGHostLevel L0;
+        L0.m = hs.m;
+        L0.st = hs.st;
+        L0.vals = h->h_ec;
         std::vector<double> ell;
-        RTE_TRY(to_ell(mh.levels[0], 1, d.dP, ell));
+        RTE_TRY(to_ell(L0, 1, d.dP, ell));
         transpose_blocks(ell, d.dP);
         RTE_TRY(upload(h, &d.ec_ell, ell));
     }
@@ -1236,6 +1331,67 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
                 return bail(fail(RTE_ERR_ARG, "singular coarse diagonal block"));
         UP(ec_val, h->h_ec);
         UP(ec_dinv, dinv);
+        // Kronecker form of the same E_c for the multigrid levels: the mass,
+        // scattering and boundary terms and, per sigma class, the four
+        // transport terms D_n^T X D_m (x) H_c[n][m]
+        const int nclass = (int)Hc.size();
+        const int Q = 4 + 4 * nclass;
+        if (Q <= kEcMaxTerms && dP <= 16) {
+            std::map<std::pair<double, double>, int> cls;
+            for (const auto& kv : Hc) cls.emplace(kv.first, (int)cls.size());
+            std::vector<double> S((size_t)Q * nnz, 0.0), Gq((size_t)Q * dd, 0.0);
+            std::copy(Mt, Mt + nnz, S.begin());
+            std::copy(Ms, Ms + nnz, S.begin() + nnz);
+            std::copy(Bx, Bx + nnz, S.begin() + 2 * (size_t)nnz);
+            std::copy(By, By + nnz, S.begin() + 3 * (size_t)nnz);
+            for (int a = 0; a < dP; ++a) {
+                Gq[(size_t)a * dP + a] = 1.0;
+                Gq[dd + (size_t)a * dP + a] = -h->h_lamP[a];
+            }
+            std::copy(Ox.begin(), Ox.end(), Gq.begin() + 2 * (size_t)dd);
+            std::copy(Oy.begin(), Oy.end(), Gq.begin() + 3 * (size_t)dd);
+            for (const auto& kv : Hc) {
+                const int c = cls[kv.first];
+                for (int nn = 0; nn < 2; ++nn)
+                    for (int mm = 0; mm < 2; ++mm)
+                        for (int a = 0; a < dP; ++a)
+                            for (int b = 0; b < dP; ++b)
+                                Gq[(size_t)(4 + 4 * c + 2 * nn + mm) * dd + a * dP + b] =
+                                    kv.second[(size_t)(nn * dP + a) * d2 + mm * dP + b];
+            }
+            for (int j = 0; j < hs.nRm; ++j) {
+                const int c = cls[std::make_pair(prob->sigma_t[j], prob->sigma_s[j])];
+                const double A = hs.mesh.area[j];
+                const int* nd = &hs.mesh.cell_nodes[3 * j];
+                for (int al = 0; al < 3; ++al)
+                    for (int be = 0; be < 3; ++be) {
+                        const int row = nd[al], col = nd[be];
+                        const int* bgn = hs.st.col.data() + hs.st.ptr[row];
+                        const int* end = hs.st.col.data() + hs.st.ptr[row + 1];
+                        const int pos = (int)(std::lower_bound(bgn, end, col) - hs.st.col.data());
+                        const double D[2][2] = {{hs.cell_D[6 * j + al], hs.cell_D[6 * j + 3 + al]},
+                                                {hs.cell_D[6 * j + be], hs.cell_D[6 * j + 3 + be]}};
+                        for (int nn = 0; nn < 2; ++nn)
+                            for (int mm = 0; mm < 2; ++mm)
+                                S[(size_t)(4 + 4 * c + 2 * nn + mm) * nnz + pos] +=
+                                    D[0][nn] * D[1][mm] / A;
+                    }
+            }
+            // the two forms must agree: sum_q S_q G_q against the blocks
+            double diff = 0.0, scale = 0.0;
+            for (int p = 0; p < nnz; ++p)
+                for (int t = 0; t < dd; ++t) {
+                    double v = 0.0;
+                    for (int q = 0; q < Q; ++q) v += S[(size_t)q * nnz + p] * Gq[(size_t)q * dd + t];
+                    diff = std::max(diff, std::fabs(v - h->h_ec[(size_t)p * dd + t]));
+                    scale = std::max(scale, std::fabs(h->h_ec[(size_t)p * dd + t]));
+                }
+            if (diff <= 1e-10 * scale) {
+                h->ec_Q = Q;
+                h->h_ecS.swap(S);
+                h->h_ecG.swap(Gq);
+            }
+        }
     }
     if (o.precision != RTE_FP64) {
         h->mixed = true;
