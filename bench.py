@@ -56,6 +56,10 @@ def parse():
     ap.add_argument('--no-serving', action='store_true',
                     help='skip the serving (continuous batching) measurement')
     ap.add_argument('--serve-requests', type=int, default=48)
+    ap.add_argument('--serve-sweep', action='store_true',
+                    help='also sweep the arrival rate of the serving stream (minutes)')
+    ap.add_argument('--batch', action='store_true',
+                    help='also time the 64 uneven instances of the batching workload')
     return ap.parse_args()
 
 
@@ -172,7 +176,7 @@ def fp64_peak_tflops(torch):
 # kernel group as last captured with ncu on the default workload (the summary
 # and command are in profiles/); a kernel changed since its capture has no
 # entry.  k_e0_pcg_f: mean of two captured launches of 13 PCG iterations.
-PROFILED_DRAM_BYTES = {'e0_cg_lo': 4.885e9}
+PROFILED_DRAM_BYTES = {'e0_cg_lo': 4.94e9}
 
 
 def kernel_work(name, d, nrhs, info):
@@ -375,6 +379,12 @@ def run_ours(args):
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_bench(args, torch, rte)
+        if args.serve_sweep:
+            serving['rate_sweep'] = serving_sweep(args, torch, rte,
+                                                  serving['sequential_fp64_solves_per_s'])
+    batch = None
+    if rank == 0 and world == 1 and args.batch:
+        batch = batch_bench(torch, rte)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(p)
@@ -395,6 +405,8 @@ def run_ours(args):
                    e2e=e2e, gpu_launches=launches, roofline=roof,
                    kernel_share=share, clocks=clk.summary(), cpu_baseline=cpu,
                    fp64_compare=fp64, serving=serving)
+        if batch is not None:
+            out['batch'] = batch
         print(json.dumps(out))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -468,6 +480,70 @@ def serving_bench(args, torch, rte):
                 p99_latency_s=float(np.percentile(lat, 99)), solves_per_s=len(reqs) / wall,
                 sequential_fp64_solves_per_s=seq_rate,
                 sequential_fp64_sample=len(sample), mean_iterations=float(np.mean(iters)))
+
+
+def serving_sweep(args, torch, rte, seq_rate):
+    """The serving stream at several arrival rates (multiples of the
+    sequential FP64 rate): p50/p99 latency and served solves/s per rate,
+    to show where latency saturates."""
+    import numpy as np
+    reqs = serving_requests(args.serve_requests, seed=3)
+    free, _ = torch.cuda.mem_get_info()
+    out = []
+    for mult in (0.5, 1.0, 2.0, 4.0, 8.0):
+        sv = rte.Server(int(free * 0.6), slots=8, precision=rte.MIXED_BF16)
+        sv.wait(sv.submit(reqs[0], reqs[0].q_nodal, tol=1e-6))
+        rate = mult * seq_rate
+        arrivals = np.cumsum(np.random.default_rng(4).exponential(1.0 / rate, len(reqs)))
+        t0 = time.perf_counter()
+        ids = []
+        for p, ta in zip(reqs, arrivals):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(sv.submit(p, p.q_nodal, tol=1e-6))
+        lat = np.array([sv.wait(rid)[1]['latency'] for rid in ids])
+        wall = time.perf_counter() - t0
+        sv.close()
+        out.append(dict(rate_per_s=rate, rate_over_sequential_fp64=mult,
+                        p50_latency_s=float(np.percentile(lat, 50)),
+                        p99_latency_s=float(np.percentile(lat, 99)),
+                        solves_per_s=len(reqs) / wall))
+    return out
+
+
+def batch_bench(torch, rte):
+    """The batching workload: 64 uneven instances (meshes 32..128, 128 or
+    512 triangles, 1-8 right-hand sides) submitted at once to the server
+    (8 slots, mixed BF16, tol 1e-6); DOF*iter/s summed over all right-hand
+    sides, against plain FP64 solves of a sample one after another."""
+    import workloads
+    insts = workloads.batch_instances(64, seed=0)
+    free, _ = torch.cuda.mem_get_info()
+    sv = rte.Server(int(free * 0.6), slots=8, precision=rte.MIXED_BF16)
+    sv.wait(sv.submit(insts[0], insts[0].q_nodal, tol=1e-6))
+    t0 = time.perf_counter()
+    ids = [sv.submit(p, p.q_nodal, tol=1e-6) for p in insts]
+    work = 0.0
+    for p, rid in zip(insts, ids):
+        _, info = sv.wait(rid)
+        work += (p.m + 1) ** 2 * 4 ** (p.levels + 1) * p.nrhs * info['iterations']
+    wall = time.perf_counter() - t0
+    sv.close()
+    sample = insts[:4]
+    swork, t0 = 0.0, time.perf_counter()
+    for p in sample:
+        s = rte.Solver(p, max_rhs=p.nrhs)
+        q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
+        _, info = s.solve(q, tol=1e-6)
+        torch.cuda.synchronize()
+        s.close()
+        swork += (p.m + 1) ** 2 * 4 ** (p.levels + 1) * p.nrhs * info['iterations']
+    swall = time.perf_counter() - t0
+    return dict(instances=len(insts), slots=8, precision='mixed_bf16', wall_s=wall,
+                value=work / wall, unit='DOF*iter/s',
+                sequential_fp64=dict(sample=len(sample), value=swork / swall,
+                                     note='setup included, one solve after another'))
 
 
 def cpu_baseline(p, budget_s=30.0):
