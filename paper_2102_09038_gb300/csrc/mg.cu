@@ -1360,11 +1360,16 @@ __global__ void k_copy_err(const GridBar* bar, SolveStatus* st) { st->timed_out 
 
 // Blocks per SM of a persistent kernel: as many as fit (the grid barrier
 // requires them all to be resident), at most 4.
-int coop_grid(const void* fn, int threads) {
+// A problem with less work takes fewer blocks (one per `per_block` of its
+// `units`): its grid barriers are cheaper, and the persistent kernels of
+// small solves on other streams (the server's slots) can run beside it.
+int coop_grid(const void* fn, int threads, size_t units, size_t per_block) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
     per_sm = std::max(1, std::min(per_sm, 4));
-    return per_sm * device_sm_count();
+    const size_t full = (size_t)per_sm * device_sm_count();
+    const size_t want = (units + per_block - 1) / per_block;
+    return (int)std::max<size_t>(1, std::min(full, want));
 }
 
 template <typename V>
@@ -1434,7 +1439,8 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     // FP32: the quad kernel when the columns fit its shared per-column tables
     const void* fn = (sizeof(T) == sizeof(float) && ncols <= kShCols) ? (const void*)k_e0_pcg_f
                                                                        : (const void*)k_e0_pcg<T>;
-    const int grid = coop_grid(fn, 256);
+    // level-0 work: (node, column) items, four per thread and sweep (quads)
+    const int grid = coop_grid(fn, 256, (size_t)d.nRp * ncols, 256 * 16);
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, s));
     k_copy_err<<<1, 1, 0, s>>>(a.bar, status_dev);
@@ -1512,7 +1518,8 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     if (a.mg.Q > kEcMaxQ || (a.mg.Q > 0 && d.dP > 16))
         return fail(RTE_ERR_ARG, "Kronecker coarse multigrid: at most 16 terms of d <= 16");
     const void* fn = (const void*)k_ec_pcg;
-    const int grid = coop_grid(fn, 256);
+    // level-0 work: (rhs, node) items, one per lane group (16 per block)
+    const int grid = coop_grid(fn, 256, (size_t)nrhs * d.nRp, 8 * (32 / a.mg.G));
     void* args[] = {&a};
     RTE_CUDA_TRY(cudaLaunchCooperativeKernel(fn, grid, 256, args, 0, s));
     k_copy_err<<<1, 1, 0, s>>>(a.bar, status_dev);
