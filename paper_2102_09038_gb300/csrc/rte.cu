@@ -87,16 +87,56 @@ struct rte_handle {
 
 namespace {
 
+// Device memory of a handle is stream-ordered (cudaMallocAsync on the
+// handle's stream, freed the same way by rte_destroy): unlike cudaMalloc and
+// cudaFree, neither waits for the work of other streams, so the server's
+// slots set up and tear down solves while the others compute.  The device's
+// default pool keeps up to kPoolKeep bytes of freed memory for reuse.
+constexpr uint64_t kPoolKeep = 8ull << 30;
+
+void keep_pool_memory() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return;
+    uint64_t cur = 0;
+    cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &cur);
+    if (cur < kPoolKeep) {
+        uint64_t v = kPoolKeep;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &v);
+    }
+}
+
 template <typename T>
 int dalloc(rte_handle* h, T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void**)p, n * sizeof(T), h->stream);
     if (e != cudaSuccess) {
         *p = nullptr;
-        return fail(RTE_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return fail(RTE_ERR_NOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     }
     h->allocs.push_back((void*)*p);
+    return RTE_OK;
+}
+
+// One cuSOLVER handle per host thread, kept for the thread's life (creating
+// and destroying one per call allocates and frees device memory each time).
+struct SolverHandle {
+    cusolverDnHandle_t h = nullptr;
+    ~SolverHandle() {
+        if (h) cusolverDnDestroy(h);
+    }
+};
+
+int solver_handle(cudaStream_t s, cusolverDnHandle_t* out) {
+    thread_local SolverHandle sh;
+    if (!sh.h && cusolverDnCreate(&sh.h) != CUSOLVER_STATUS_SUCCESS) {
+        sh.h = nullptr;
+        return fail(RTE_ERR_CUDA, "cusolverDnCreate failed");
+    }
+    cusolverDnSetStream(sh.h, s);
+    *out = sh.h;
     return RTE_OK;
 }
 
@@ -159,16 +199,15 @@ void flush_timers(rte_handle* h) {
 // eigenvalues.
 int sym_eig(rte_handle* h, std::vector<double>& C, std::vector<double>& w, int n) {
     cusolverDnHandle_t cs = nullptr;
-    if (cusolverDnCreate(&cs) != CUSOLVER_STATUS_SUCCESS)
-        return fail(RTE_ERR_CUDA, "cusolverDnCreate failed");
-    cusolverDnSetStream(cs, h->stream);
+    RTE_TRY(solver_handle(h->stream, &cs));
+    const cudaStream_t st = h->stream;
     double *dA = nullptr, *dW = nullptr, *dWork = nullptr;
     int* dInfo = nullptr;
     int rc = RTE_OK;
     int lwork = 0;
-    if (cudaMalloc(&dA, sizeof(double) * (size_t)n * n) != cudaSuccess ||
-        cudaMalloc(&dW, sizeof(double) * n) != cudaSuccess ||
-        cudaMalloc(&dInfo, sizeof(int)) != cudaSuccess) {
+    if (cudaMallocAsync(&dA, sizeof(double) * (size_t)n * n, st) != cudaSuccess ||
+        cudaMallocAsync(&dW, sizeof(double) * n, st) != cudaSuccess ||
+        cudaMallocAsync(&dInfo, sizeof(int), st) != cudaSuccess) {
         rc = fail(RTE_ERR_NOMEM, "eigensolver allocation failed");
     }
     if (rc == RTE_OK) {
@@ -178,7 +217,7 @@ int sym_eig(rte_handle* h, std::vector<double>& C, std::vector<double>& w, int n
                                         n, dA, n, dW, &lwork) != CUSOLVER_STATUS_SUCCESS)
             rc = fail(RTE_ERR_CUDA, "syevd_bufferSize failed");
     }
-    if (rc == RTE_OK && cudaMalloc(&dWork, sizeof(double) * (size_t)std::max(lwork, 1)) != cudaSuccess)
+    if (rc == RTE_OK && cudaMallocAsync(&dWork, sizeof(double) * (size_t)std::max(lwork, 1), st) != cudaSuccess)
         rc = fail(RTE_ERR_NOMEM, "eigensolver workspace allocation failed");
     if (rc == RTE_OK &&
         cusolverDnDsyevd(cs, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dW,
@@ -196,11 +235,10 @@ int sym_eig(rte_handle* h, std::vector<double>& C, std::vector<double>& w, int n
         else if (info != 0)
             rc = fail(RTE_ERR_CUDA, "syevd did not converge");
     }
-    cudaFree(dA);
-    cudaFree(dW);
-    cudaFree(dWork);
-    cudaFree(dInfo);
-    cusolverDnDestroy(cs);
+    if (dA) cudaFreeAsync(dA, st);
+    if (dW) cudaFreeAsync(dW, st);
+    if (dWork) cudaFreeAsync(dWork, st);
+    if (dInfo) cudaFreeAsync(dInfo, st);
     return rc;
 }
 
@@ -210,9 +248,8 @@ int sym_eig(rte_handle* h, std::vector<double>& C, std::vector<double>& w, int n
 int spd_inverse_batch(rte_handle* h, int n, int count, const std::vector<double>& A,
                       std::vector<float>& inv) {
     cusolverDnHandle_t cs = nullptr;
-    if (cusolverDnCreate(&cs) != CUSOLVER_STATUS_SUCCESS)
-        return fail(RTE_ERR_CUDA, "cusolverDnCreate failed");
-    cusolverDnSetStream(cs, h->stream);
+    RTE_TRY(solver_handle(h->stream, &cs));
+    const cudaStream_t st = h->stream;
     const size_t nn = (size_t)n * n;
     double *dA = nullptr, *dB = nullptr, *dWork = nullptr;
     int* dInfo = nullptr;
@@ -220,14 +257,14 @@ int spd_inverse_batch(rte_handle* h, int n, int count, const std::vector<double>
     std::vector<double> I(nn, 0.0), out(nn);
     for (int i = 0; i < n; ++i) I[(size_t)i * n + i] = 1.0;
     inv.resize(nn * count);
-    if (cudaMalloc(&dA, nn * 8) != cudaSuccess || cudaMalloc(&dB, nn * 8) != cudaSuccess ||
-        cudaMalloc(&dInfo, sizeof(int)) != cudaSuccess)
+    if (cudaMallocAsync(&dA, nn * 8, st) != cudaSuccess || cudaMallocAsync(&dB, nn * 8, st) != cudaSuccess ||
+        cudaMallocAsync(&dInfo, sizeof(int), st) != cudaSuccess)
         rc = fail(RTE_ERR_NOMEM, "coarse inverse allocation failed");
     if (rc == RTE_OK &&
         cusolverDnDpotrf_bufferSize(cs, CUBLAS_FILL_MODE_LOWER, n, dA, n, &lwork) !=
             CUSOLVER_STATUS_SUCCESS)
         rc = fail(RTE_ERR_CUDA, "potrf_bufferSize failed");
-    if (rc == RTE_OK && cudaMalloc(&dWork, sizeof(double) * std::max(lwork, 1)) != cudaSuccess)
+    if (rc == RTE_OK && cudaMallocAsync(&dWork, sizeof(double) * std::max(lwork, 1), st) != cudaSuccess)
         rc = fail(RTE_ERR_NOMEM, "coarse inverse workspace allocation failed");
     for (int b = 0; b < count && rc == RTE_OK; ++b) {
         // symmetric: the row-major matrix is its own column-major transpose
@@ -254,11 +291,10 @@ int spd_inverse_batch(rte_handle* h, int n, int count, const std::vector<double>
         }
         for (size_t t = 0; t < nn; ++t) inv[nn * b + t] = (float)out[t];
     }
-    cudaFree(dA);
-    cudaFree(dB);
-    cudaFree(dWork);
-    cudaFree(dInfo);
-    cusolverDnDestroy(cs);
+    if (dA) cudaFreeAsync(dA, st);
+    if (dB) cudaFreeAsync(dB, st);
+    if (dWork) cudaFreeAsync(dWork, st);
+    if (dInfo) cudaFreeAsync(dInfo, st);
     return rc;
 }
 
@@ -1076,6 +1112,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     rte_handle* h = new rte_handle();
     h->opt = o;
     h->stream = (cudaStream_t)stream;
+    keep_pool_memory();
     auto bail = [&](int rc) {
         rte_destroy(h);
         return rc;
@@ -1857,7 +1894,8 @@ void rte_destroy(rte_handle* h) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
-    for (void* p : h->allocs) cudaFree(p);
+    for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
+    cudaStreamSynchronize(h->stream);
     delete h;
 }
 

@@ -87,7 +87,7 @@ std::string autotune_report() {
     for (const auto& kv : g_table) {
         out += kv.first + "=" + std::to_string(kv.second.best) + " (ms";
         for (float m : kv.second.ms) {
-            std::snprintf(buf, sizeof(buf), " %.4f", m);
+            std::snprintf(buf, sizeof(buf), " %.6g", m);
             out += buf;
         }
         out += ");";
