@@ -176,7 +176,7 @@ def fp64_peak_tflops(torch):
 # kernel group as last captured with ncu on the default workload (the summary
 # and command are in profiles/); a kernel changed since its capture has no
 # entry.  k_e0_pcg_f: mean of two captured launches of 13 PCG iterations.
-PROFILED_DRAM_BYTES = {'e0_cg_lo': 4.94e9}
+PROFILED_DRAM_BYTES = {}
 
 
 def kernel_work(name, d, nrhs, info):
@@ -191,8 +191,10 @@ def kernel_work(name, d, nrhs, info):
         R and V-cycle input written by the update; R, z read for r.z and
         r.r; z, P read and P written by the direction update: 12 words of
         the CG precision, plus 16 B of FP64 X) and the V-cycle's 17 FP32 array
-        passes per level (4^-l of the level-0 size), times the iterations the
-        launch took.  The FP32 kernel forms the stencil coefficients on chip
+        passes per level (4^-l of the level-0 size), times the V-cycles of
+        the launch (the mean over the solve's launches), each weighted by the
+        fraction of direction quads with a column not yet converged: the
+        mixed-mode kernel visits only those.  The FP32 kernel forms the stencil coefficients on chip
         (224 B per node per pass, not counted); the FP64 kernel also reads 7
         FP64 coefficients per item;
       * E_c PCG: per iteration the FP64 level-0 blocks (7 d^2 per node) and
@@ -217,7 +219,11 @@ def kernel_work(name, d, nrhs, info):
         # the coarsest level's dense per-direction inverses, read once per V-cycle
         mc = d['mesh'] >> (d['e0_levels'] - 1)
         vc += ((mc + 1) ** 2) ** 2 * nS * 4
-        return (cg + vc) * max(info.get('e0_iters', 1), 1), 'byte', 'hbm'
+        # V-cycles per launch, each weighted by the fraction of direction
+        # quads still active (converged columns are not visited again)
+        n = info.get('e0_launches', 0)
+        per = info['e0_active_vcycles'] / n if n else max(info.get('e0_iters', 1), 1)
+        return (cg + vc) * per, 'byte', 'hbm'
     if name == 'coarse_cg':
         dp = d['dP']
         cg = nRp * nrhs * (7 * dp * dp + 12 * dp) * 8

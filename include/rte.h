@@ -114,6 +114,12 @@ typedef struct {
     double* history;            /* optional host array: rel. residual per it */
     int history_cap;            /* its capacity                              */
     double seconds;             /* wall time of the solve                    */
+    int e0_launches;            /* E_0^{-1} applications in the solve        */
+    double e0_vcycles;          /* their multigrid V-cycles, summed          */
+    double e0_active_vcycles;   /* the same, each weighted by the fraction of
+                                   direction columns (in groups of four) not
+                                   yet converged, which are the only ones the
+                                   mixed-mode kernel visits                  */
 } rte_stats;
 
 /* Fills *opts with the defaults above (FP64, eigen route, tolerances

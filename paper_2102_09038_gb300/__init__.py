@@ -60,7 +60,9 @@ class _Stats(ctypes.Structure):
                 ('coarse_iters_last', ctypes.c_int),
                 ('mk_iters_last', ctypes.c_int),
                 ('history', ctypes.POINTER(ctypes.c_double)),
-                ('history_cap', ctypes.c_int), ('seconds', ctypes.c_double)]
+                ('history_cap', ctypes.c_int), ('seconds', ctypes.c_double),
+                ('e0_launches', ctypes.c_int), ('e0_vcycles', ctypes.c_double),
+                ('e0_active_vcycles', ctypes.c_double)]
 
 
 _lib = None
@@ -384,6 +386,8 @@ class Solver:
                     e0_iters=st.e0_iters_last,
                     coarse_iters=st.coarse_iters_last,
                     mk_iters=st.mk_iters_last, seconds=st.seconds,
+                    e0_launches=st.e0_launches, e0_vcycles=st.e0_vcycles,
+                    e0_active_vcycles=st.e0_active_vcycles,
                     history=list(hist[:min(history, st.iterations + 1)]),
                     status=rc)
         if rc not in (0, 4):

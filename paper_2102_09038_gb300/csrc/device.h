@@ -95,6 +95,7 @@ struct SolveStatus {
     int timed_out;
     int converged;
     int pad;
+    long long active_quads;   // E_0 quad kernel: active quads summed over its V-cycles
 };
 
 // ------------------------------------------------------------- launchers

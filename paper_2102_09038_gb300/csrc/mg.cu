@@ -161,24 +161,33 @@ __device__ __forceinline__ float4 e0_apply4(const MGDeviceLevel& L, const Quad& 
     return y;
 }
 
-// Grid-stride loop over the quads (i, p) of an n-node level with nq quads
-// per node; o4 = the quad's float4 offset.  Needs nq, nqd (direction quads)
-// and wq in scope.
+// The V-cycle visits only the active quads of the iteration: ql lists them
+// (increasing, na of them; ql == nullptr: all nq quads).  A quad whose four
+// columns have converged is left alone on every level, since nothing reads
+// its values again.
+__device__ __forceinline__ int quad_at(const unsigned short* ql, int k) {
+    return ql ? (int)ql[k] : k;
+}
+
+// Loop over the active quads (i, p) of an n-node level with nq quads per
+// node; o4 = the quad's float4 offset.  Thread t keeps active quad t % na
+// for all its nodes (t / na, stepping by the grid's threads / na; the last
+// threads / na * na .. threads - 1 idle), so its four directions' weights
+// are loaded once.  Needs nq, nqd (direction quads), ql, na and wq in scope.
 #define QUADS(n, UNROLL)                                                        \
     {                                                                            \
     const int kq__ = nqd - 1;   /* n_S^+ is a power of two */                    \
-    const unsigned qd_total__ = (unsigned)(n) * (unsigned)nq;                    \
-    const unsigned qd_stride__ = gridDim.x * blockDim.x;                         \
-    const int qd_sq__ = (int)(qd_stride__ / (unsigned)nq);                       \
-    const int qd_sr__ = (int)(qd_stride__ % (unsigned)nq);                       \
-    unsigned qe__ = blockIdx.x * blockDim.x + threadIdx.x;                       \
-    int i = (int)(qe__ / (unsigned)nq), p = (int)(qe__ % (unsigned)nq);          \
+    const unsigned qd_na__ = na > 0 ? (unsigned)na : 1u;                         \
+    const unsigned qd_rows__ = gridDim.x * blockDim.x / qd_na__;                 \
+    const unsigned qd_t__ = blockIdx.x * blockDim.x + threadIdx.x;               \
+    const bool qd_on__ = na > 0 && qd_t__ < qd_rows__ * qd_na__;                 \
+    const int p = qd_on__ ? quad_at(ql, (int)(qd_t__ % qd_na__)) : 0;            \
+    Quad qd;                                                                     \
+    if (qd_on__) qd.load(wq, nqd, p & kq__);                                     \
     _Pragma(UNROLL)                                                              \
-    for (; qe__ < qd_total__; qe__ += qd_stride__, i += qd_sq__, p += qd_sr__,   \
-         (p >= nq ? (p -= nq, ++i) : 0)) {                                       \
-        const size_t o4 = (size_t)i * nq + p;                                    \
-        Quad qd;                                                                 \
-        qd.load(wq, nqd, p & kq__);
+    for (int i = (int)(qd_t__ / qd_na__); qd_on__ && i < (int)(n);               \
+         i += (int)qd_rows__) {                                                  \
+        const size_t o4 = (size_t)i * nq + p;
 
 __device__ __forceinline__ float4 jac4(float4 x, float4 b, float4 y, float4 d) {
     return make_float4(x.x + kOmega * __fdividef(b.x - y.x, d.x),
@@ -190,7 +199,8 @@ __device__ __forceinline__ float4 jac4(float4 x, float4 b, float4 y, float4 d) {
 // The V-cycle's phases, each compiled on its own (not inlined) so that its
 // registers are allocated for its own loop alone.
 __device__ __noinline__ void e0_first(const MGDeviceLevel Lv, const float4* __restrict__ wq,
-                                      int nq, int nqd, float4* __restrict__ x) {
+                                      int nq, int nqd, const unsigned short* __restrict__ ql,
+                                      int na, float4* __restrict__ x) {
     const float4* __restrict__ B = reinterpret_cast<const float4*>(Lv.B);
     const float4* __restrict__ sv = reinterpret_cast<const float4*>(Lv.sv);
     QUADS(Lv.n, "unroll 2")
@@ -201,7 +211,8 @@ __device__ __noinline__ void e0_first(const MGDeviceLevel Lv, const float4* __re
 }
 
 __device__ __noinline__ void e0_jacobi(const MGDeviceLevel Lv, const float4* __restrict__ wq,
-                                       int nq, int nqd, const float4* __restrict__ x,
+                                       int nq, int nqd, const unsigned short* __restrict__ ql,
+                                       int na, const float4* __restrict__ x,
                                        float4* __restrict__ xt) {
     const float4* __restrict__ B = reinterpret_cast<const float4*>(Lv.B);
     QUADS(Lv.n, "unroll 2")
@@ -212,7 +223,8 @@ __device__ __noinline__ void e0_jacobi(const MGDeviceLevel Lv, const float4* __r
 }
 
 __device__ __noinline__ void e0_residual(const MGDeviceLevel Lv, const float4* __restrict__ wq,
-                                         int nq, int nqd, const float4* __restrict__ x,
+                                         int nq, int nqd, const unsigned short* __restrict__ ql,
+                                         int na, const float4* __restrict__ x,
                                          float4* __restrict__ t) {
     const float4* __restrict__ B = reinterpret_cast<const float4*>(Lv.B);
     QUADS(Lv.n, "unroll 2")
@@ -224,13 +236,14 @@ __device__ __noinline__ void e0_residual(const MGDeviceLevel Lv, const float4* _
 }
 
 __device__ __noinline__ void e0_restrict(const MGDeviceLevel Cv, int nq,
+                                         const unsigned short* __restrict__ ql, int na,
                                          const float4* __restrict__ t) {
     float4* __restrict__ CB = reinterpret_cast<float4*>(Cv.B);
-    const unsigned total = (unsigned)Cv.n * (unsigned)nq;
+    const unsigned total = (unsigned)Cv.n * (unsigned)na;
 #pragma unroll 2
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += gridDim.x * blockDim.x) {
-        const int i = (int)(e / (unsigned)nq), p = (int)(e % (unsigned)nq);
+        const int i = (int)(e / (unsigned)na), p = quad_at(ql, (int)(e % (unsigned)na));
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int q = 0; q < Cv.rwid; ++q) {
             float w;
@@ -241,37 +254,40 @@ __device__ __noinline__ void e0_restrict(const MGDeviceLevel Cv, int nq,
             acc.z = fmaf(w, v.z, acc.z);
             acc.w = fmaf(w, v.w, acc.w);
         }
-        CB[e] = acc;
+        CB[(size_t)i * nq + p] = acc;
     }
 }
 
-__device__ __noinline__ void e0_prolong(const MGDeviceLevel Lv, int nq, float4* __restrict__ x,
-                                        const float4* __restrict__ xc) {
-    const unsigned total = (unsigned)Lv.n * (unsigned)nq;
+__device__ __noinline__ void e0_prolong(const MGDeviceLevel Lv, int nq,
+                                        const unsigned short* __restrict__ ql, int na,
+                                        float4* __restrict__ x, const float4* __restrict__ xc) {
+    const unsigned total = (unsigned)Lv.n * (unsigned)na;
 #pragma unroll 2
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += gridDim.x * blockDim.x) {
-        const int i = (int)(e / (unsigned)nq), p = (int)(e % (unsigned)nq);
+        const int i = (int)(e / (unsigned)na), p = quad_at(ql, (int)(e % (unsigned)na));
+        const size_t o4 = (size_t)i * nq + p;
         int c0, c1;
         float w0, w1;
         prolong_src(i, Lv.m, c0, c1, w0, w1);
         const float4 a = ld4(xc + (size_t)c0 * nq + p), b = ld4(xc + (size_t)c1 * nq + p);
-        const float4 v = ld4(x + e);
-        x[e] = make_float4(v.x + w0 * a.x + w1 * b.x, v.y + w0 * a.y + w1 * b.y,
+        const float4 v = ld4(x + o4);
+        x[o4] = make_float4(v.x + w0 * a.x + w1 * b.x, v.y + w0 * a.y + w1 * b.y,
                            v.z + w0 * a.z + w1 * b.z, v.w + w0 * a.w + w1 * b.w);
     }
 }
 
 // coarsest level: x = (dense inverse of each direction block) B
 __device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* cinv, int nSp, int nc,
-                                      float* x) {
+                                      const unsigned short* __restrict__ ql, int na, float* x) {
     const int km = nSp - 1;
-    ITEMS(Lv.n, nc) {
+    ITEMS(Lv.n, 4 * na) {
+        const int col = 4 * quad_at(ql, c >> 2) + (c & 3);
         // cinv is [i][j][direction], so a warp's lanes (consecutive
         // columns) read consecutive words
-        const int k = c & km;
+        const int k = col & km;
         const float* row = cinv + (size_t)i * Lv.n * nSp + k;
-        const float* bc = Lv.B + c;
+        const float* bc = Lv.B + col;
         // 16 independent load pairs in flight per trip
         constexpr int U = 16;
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -287,13 +303,18 @@ __device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* cinv,
             for (int u = 0; u < U; ++u) acc[u & 3] += rv[u] * bv[u];
         }
         for (; j < Lv.n; ++j) acc[0] += __ldg(row + (size_t)j * nSp) * ldg2(bc + (size_t)j * nc);
-        x[e] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        x[(size_t)i * nc + col] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }}
 }
 
-// One symmetric V-cycle on B_0; returns the buffer holding z on level 0.
-__device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
+// One symmetric V-cycle on B_0 over the quads ql lists (na of them; all
+// quads when ql is null); returns the buffer holding z on level 0.
+__device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z,
+                          const unsigned short* ql = nullptr, int na = -1) {
     const int nc = mg.ncols, nq = nc >> 2, nqd = mg.nSp >> 2;
+    if (!ql) na = nq;
+    z = mg.lev[0].X;
+    if (na <= 0) return true;
     int cur[kMaxMGLevels];
     for (int l = 0; l < mg.L; ++l) cur[l] = 0;
     auto buf4 = [&](int l, int which) {
@@ -301,33 +322,33 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
     };
     for (int l = 0; l + 1 < mg.L; ++l) {
         const MGDeviceLevel Lv = mg.lev[l];
-        e0_first(Lv, mg.wq, nq, nqd, buf4(l, 0));
+        e0_first(Lv, mg.wq, nq, nqd, ql, na, buf4(l, 0));
         cur[l] = 0;
         if (!grid_sync(bar)) return false;
         for (int k = 1; k < mg.nu; ++k) {
-            e0_jacobi(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
+            e0_jacobi(Lv, mg.wq, nq, nqd, ql, na, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
             cur[l] ^= 1;
             if (!grid_sync(bar)) return false;
         }
         float4* t = buf4(l, cur[l] ^ 1);
-        e0_residual(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), t);
+        e0_residual(Lv, mg.wq, nq, nqd, ql, na, buf4(l, cur[l]), t);
         if (!grid_sync(bar)) return false;
-        e0_restrict(mg.lev[l + 1], nq, t);
+        e0_restrict(mg.lev[l + 1], nq, ql, na, t);
         if (!grid_sync(bar)) return false;
     }
     {
         const int l = mg.L - 1;
         const MGDeviceLevel Lv = mg.lev[l];
         if (mg.dense) {
-            e0_dense(Lv, mg.cinv, mg.nSp, nc, reinterpret_cast<float*>(buf4(l, 0)));
+            e0_dense(Lv, mg.cinv, mg.nSp, nc, ql, na, reinterpret_cast<float*>(buf4(l, 0)));
             cur[l] = 0;
             if (!grid_sync(bar)) return false;
         } else {
-            e0_first(Lv, mg.wq, nq, nqd, buf4(l, 0));
+            e0_first(Lv, mg.wq, nq, nqd, ql, na, buf4(l, 0));
             cur[l] = 0;
             if (!grid_sync(bar)) return false;
             for (int k = 1; k < kCoarseSweeps; ++k) {
-                e0_jacobi(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
+                e0_jacobi(Lv, mg.wq, nq, nqd, ql, na, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
                 cur[l] ^= 1;
                 if (!grid_sync(bar)) return false;
             }
@@ -335,10 +356,10 @@ __device__ bool e0_vcycle(const E0MG& mg, GridBar* bar, float*& z) {
     }
     for (int l = mg.L - 2; l >= 0; --l) {
         const MGDeviceLevel Lv = mg.lev[l];
-        e0_prolong(Lv, nq, buf4(l, cur[l]), buf4(l + 1, cur[l + 1]));
+        e0_prolong(Lv, nq, ql, na, buf4(l, cur[l]), buf4(l + 1, cur[l + 1]));
         if (!grid_sync(bar)) return false;
         for (int k = 0; k < mg.nu; ++k) {
-            e0_jacobi(Lv, mg.wq, nq, nqd, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
+            e0_jacobi(Lv, mg.wq, nq, nqd, ql, na, buf4(l, cur[l]), buf4(l, cur[l] ^ 1));
             cur[l] ^= 1;
             if (!grid_sync(bar)) return false;
         }
@@ -691,7 +712,35 @@ struct E0Q {   // what the quad phases need of E0Args<float>
     const double* bb;
     MGDeviceLevel L0;
     const float4* wq;
+    const unsigned short* ql;   // the iteration's active quads (null: all)
+    int na;                     // how many
 };
+
+// Lists, in increasing order, the quads that hold a column whose residual is
+// still above the tolerance (rr > tol2 bb, the test the per-column tables
+// make); every block builds the same list from the same global values.  One
+// quad per thread: nq <= blockDim.x.
+__device__ int quad_list(int nq, double tol2, const double* bb, const double* rr,
+                         unsigned short* ql, int* s_cnt) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    bool on = false;
+    if (t < nq)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            on = on || ldg2(rr + 4 * t + u) > tol2 * ldg2(bb + 4 * t + u);
+    const unsigned bal = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) s_cnt[w] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int v = 0; v < nw; ++v) {
+        const int cv = s_cnt[v];
+        if (v < w) off += cv;
+        tot += cv;
+    }
+    if (on) ql[off + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)t;
+    __syncthreads();
+    return tot;
+}
 
 
 // Per-block table of the columns' CG scalars, built once per phase so that
@@ -730,20 +779,23 @@ __device__ __forceinline__ float4 sel4(unsigned m, float4 a, float4 b) {
                        (m & 8u) ? a.w : b.w);
 }
 
-// Grid-stride loop over the (node i, quad p) items of the CG; e4 = float4
+// Loop over the (node i, active quad p) items of the CG, each thread on one
+// quad as in QUADS (so its per-column sums stay in registers); e4 = float4
 // offset in the even layout, m4 = in the V-cycle layout.
 #define CGQ(q)                                                                   \
     ColSum cs;                                                                   \
-    const unsigned total__ = (unsigned)q.nRp * (unsigned)q.nq;                   \
-    for (unsigned e__ = blockIdx.x * blockDim.x + threadIdx.x; e__ < total__;    \
-         e__ += gridDim.x * blockDim.x) {                                        \
-        const int i = (int)(e__ / (unsigned)q.nq), p = (int)(e__ % (unsigned)q.nq); \
-        const int r = p / q.nqd, k4 = p - r * q.nqd;                             \
+    const unsigned na__ = q.na > 0 ? (unsigned)q.na : 1u;                        \
+    const unsigned rows__ = gridDim.x * blockDim.x / na__;                       \
+    const unsigned t__ = blockIdx.x * blockDim.x + threadIdx.x;                  \
+    const bool on__ = q.na > 0 && t__ < rows__ * na__;                           \
+    const int p = on__ ? quad_at(q.ql, (int)(t__ % na__)) : 0;                   \
+    const int r = p / q.nqd, k4 = p - r * q.nqd;                                 \
+    const int col = 4 * p;                                                       \
+    (void)col;                                                                   \
+    for (int i = (int)(t__ / na__); on__ && i < q.nRp; i += (int)rows__) {       \
         const size_t e4 = ((size_t)r * q.nRp + i) * q.nqd + k4;                  \
         const size_t m4 = (size_t)i * q.nq + p;                                  \
-        const int col = 4 * p;                                                   \
-        (void)m4;                                                                \
-        (void)col;
+        (void)m4;
 
 __device__ __noinline__ void cgq_init(const E0Q& q, double* bbsum, double* sh) {
     CGQ(q)
@@ -782,10 +834,10 @@ __device__ __noinline__ void cgq_first_dir(const E0Q& q, const float* z, double*
 __device__ __noinline__ void cgq_ap(const E0Q& q, const double* rr_prev, double* pap, double* sh,
                                     unsigned char* s_act, float* s_coef) {
     col_table(kActOnly, q.nc, q.tol2, q.bb, rr_prev, nullptr, nullptr, nullptr, s_act, s_coef);
+    Quad qd;   // loaded on the thread's first item (its quad is fixed)
     CGQ(q)
         const unsigned am = quad_mask(s_act, col);
         if (!am) continue;
-        Quad qd;
         qd.load(q.wq, q.nqd, k4);
         const float4* Pr = reinterpret_cast<const float4*>(q.P) + (size_t)r * q.nRp * q.nqd;
         float4 dg;
@@ -884,6 +936,8 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
     __shared__ double sh[kShCols];
     __shared__ __align__(16) float s_coef[kShCols];
     __shared__ __align__(16) unsigned char s_act[kShCols];
+    __shared__ unsigned short s_ql[kShCols / 4];
+    __shared__ int s_cnt[32];
     __shared__ int s_stop;
     if (threadIdx.x == 0) s_stop = 0;
     E0Q q;
@@ -903,6 +957,9 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
     q.B0 = q.L0.B;
     q.bb = a.bb;
     q.wq = a.mg.wq;
+    q.ql = nullptr;
+    q.na = q.nq;
+    long long quads_done = q.nq;   // active quads summed over the V-cycles
     const int nc = a.ncols;
     cgq_init(q, a.bb, sh);
     if (!grid_sync(a.bar)) return;
@@ -918,11 +975,16 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
         if (blockIdx.x == 0)
             for (int c = threadIdx.x; c < 3 * nc; c += blockDim.x)
                 a.acc[(size_t)next * 3 * nc + c] = 0.0;
+        // every phase of this iteration, the V-cycle included, visits only
+        // the quads with an unconverged column
+        q.na = quad_list(q.nq, q.tol2, q.bb, slot(a, prev, 2), s_ql, s_cnt);
+        q.ql = s_ql;
+        quads_done += q.na;
         cgq_ap(q, slot(a, prev, 2), slot(a, cur, 0), sh, s_act, s_coef);
         if (!grid_sync(a.bar)) return;
         cgq_update(q, slot(a, prev, 2), slot(a, prev, 1), slot(a, cur, 0), s_act, s_coef);
         if (!grid_sync(a.bar)) return;
-        if (!e0_vcycle(a.mg, a.bar, z)) return;
+        if (!e0_vcycle(a.mg, a.bar, z, q.ql, q.na)) return;
         cgq_rz(q, z, slot(a, prev, 2), slot(a, prev, 1), slot(a, cur, 1), slot(a, cur, 2), sh,
                s_act, s_coef);
         if (!grid_sync(a.bar)) return;
@@ -942,6 +1004,7 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.status->iterations = it;
         a.status->converged = s_stop;
+        a.status->active_quads = quads_done;
     }
 }
 

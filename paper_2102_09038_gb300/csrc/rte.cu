@@ -77,6 +77,10 @@ struct rte_handle {
     int bn_mk1 = 0, bn_mk2 = 0, bn_kplus = 0;
     // statistics of the last inner solves
     int e0_iters = 0, co_iters = 0, mk_iters = 0;
+    // E_0^{-1} work of the current solve: launches, V-cycles, and V-cycles
+    // weighted by the fraction of quads (direction columns) still active
+    int e0_launches = 0;
+    double e0_vcycles = 0.0, e0_active_vcycles = 0.0;
     // timing
     bool timing = false;
     std::vector<std::string> tnames;
@@ -974,6 +978,10 @@ int e0_inv(rte_handle* h, const double* b, double* x, int nrhs) {
     SolveStatus st;
     RTE_TRY(read_status(h, st));
     h->e0_iters = st.iterations;
+    const double vc = st.iterations + 1.0, nq = nrhs * h->d.nSp / 4.0;
+    h->e0_launches += 1;
+    h->e0_vcycles += vc;
+    h->e0_active_vcycles += st.active_quads > 0 ? st.active_quads / nq : vc;
     return RTE_OK;
 }
 
@@ -1705,6 +1713,8 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
     const DevSystem& d = h->d;
     cudaStream_t s = h->stream;
     const size_t len = (size_t)d.nRp * d.nSp;
+    h->e0_launches = 0;
+    h->e0_vcycles = h->e0_active_vcycles = 0.0;
     double* r = h->e1;       // residual r_n
     double* sv = h->e2;      // s = P_2 P_1 r
     double* rprev = h->e3;
@@ -1767,6 +1777,9 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
         stats->e0_iters_last = h->e0_iters;
         stats->coarse_iters_last = h->co_iters;
         stats->mk_iters_last = h->mk_iters;
+        stats->e0_launches = h->e0_launches;
+        stats->e0_vcycles = h->e0_vcycles;
+        stats->e0_active_vcycles = h->e0_active_vcycles;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
     return rc;

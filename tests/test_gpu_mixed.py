@@ -100,6 +100,11 @@ def test_mixed_solve_reaches_fp64_residual(mixed):
     q = s.rhs(qn)
     u, info = s.solve(q, tol=1e-11)
     assert info['status'] == 0, info
+    # every E_0^{-1} of P_1^l is counted; the active-column weighting lies
+    # between one full V-cycle per launch (the first one visits every column)
+    # and all of them
+    assert info['e0_launches'] == 4 * info['iterations'], info
+    assert info['e0_launches'] <= info['e0_active_vcycles'] <= info['e0_vcycles'], info
     qref = np.stack([disc.source(v) for v in p.q_nodal])
     u = u.cpu().numpy()
     for r in range(p.nrhs):
