@@ -379,6 +379,7 @@ struct E0Args {
     T* R;
     T* P;
     T* AP;
+    float* X32;         // FP32 kernel: the iterate (X written at the end)
     double* acc;        // [3 slots][3][ncols]: pAp, rz, rr
     double* bb;
     GridBar* bar;
@@ -658,21 +659,23 @@ __device__ __forceinline__ float4 ldf4q(const float* base, size_t o4) {
 // consecutive columns of one node), each phase its own function.  The CG
 // vectors keep the even layout [rhs][node][direction]; the V-cycle arrays
 // are [node][column].  Per-column dot products: every thread sums its
-// quad's four columns; a block combines its threads in shared memory and
-// adds once per column.
+// quad's four columns over its nodes in FP32 (a few dozen products at most
+// at level 0); a block combines its threads in shared memory (FP32) and adds
+// once per column to the FP64 total.  No FP64 arithmetic per item: the FP64
+// pipe of the GB300 SM is a small fraction of its FP32 rate.
 
 constexpr int kShCols = 1024;   // columns combined in shared memory per block
 
 struct ColSum {
-    double v[4];
+    float v[4];
     int p;
-    __device__ ColSum() : v{0.0, 0.0, 0.0, 0.0}, p(-1) {}
+    __device__ ColSum() : v{0.f, 0.f, 0.f, 0.f}, p(-1) {}
     __device__ void flush(double* dst) {
         if (p >= 0)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-                if (v[u] != 0.0) atomicAdd(dst + 4 * p + u, v[u]);
-        v[0] = v[1] = v[2] = v[3] = 0.0;
+                if (v[u] != 0.f) atomicAdd(dst + 4 * p + u, (double)v[u]);
+        v[0] = v[1] = v[2] = v[3] = 0.f;
     }
     // the thread moves to quad pp (a change only when the grid stride is not
     // a multiple of the quads per node)
@@ -690,15 +693,16 @@ __device__ void colsum_finish(ColSum& cs, double* dst, double* sh, int nc) {
         cs.flush(dst);
         return;
     }
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) sh[c] = 0.0;
+    float* shf = reinterpret_cast<float*>(sh);
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) shf[c] = 0.f;
     __syncthreads();
     if (cs.p >= 0)
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            if (cs.v[u] != 0.0) atomicAdd(sh + 4 * cs.p + u, cs.v[u]);
+            if (cs.v[u] != 0.f) atomicAdd(shf + 4 * cs.p + u, cs.v[u]);
     __syncthreads();
     for (int c = threadIdx.x; c < nc; c += blockDim.x)
-        if (sh[c] != 0.0) atomicAdd(dst + c, sh[c]);
+        if (shf[c] != 0.f) atomicAdd(dst + c, (double)shf[c]);
     __syncthreads();
     cs = ColSum();
 }
@@ -709,6 +713,7 @@ struct E0Q {   // what the quad phases need of E0Args<float>
     const double* B;
     double* X;
     float *R, *P, *AP, *B0;
+    float* X32;                 // the iterate, FP32 (X written once at the end)
     const double* bb;
     MGDeviceLevel L0;
     const float4* wq;
@@ -792,6 +797,7 @@ __device__ __forceinline__ float4 sel4(unsigned m, float4 a, float4 b) {
     const int r = p / q.nqd, k4 = p - r * q.nqd;                                 \
     const int col = 4 * p;                                                       \
     (void)col;                                                                   \
+    _Pragma("unroll 1")                                                          \
     for (int i = (int)(t__ / na__); on__ && i < q.nRp; i += (int)rows__) {       \
         const size_t e4 = ((size_t)r * q.nRp + i) * q.nqd + k4;                  \
         const size_t m4 = (size_t)i * q.nq + p;                                  \
@@ -802,16 +808,14 @@ __device__ __noinline__ void cgq_init(const E0Q& q, double* bbsum, double* sh) {
         const double2* b2 = reinterpret_cast<const double2*>(q.B) + 2 * e4;
         const double2 b01 = __ldcg(b2), b23 = __ldcg(b2 + 1);
         const float4 bf = make_float4((float)b01.x, (float)b01.y, (float)b23.x, (float)b23.y);
-        double2* x2 = reinterpret_cast<double2*>(q.X) + 2 * e4;
-        x2[0] = make_double2(0.0, 0.0);
-        x2[1] = make_double2(0.0, 0.0);
+        reinterpret_cast<float4*>(q.X32)[e4] = make_float4(0.f, 0.f, 0.f, 0.f);
         reinterpret_cast<float4*>(q.R)[e4] = bf;
         reinterpret_cast<float4*>(q.B0)[m4] = bf;
         cs.at(p, bbsum);
-        cs.v[0] += (double)bf.x * bf.x;
-        cs.v[1] += (double)bf.y * bf.y;
-        cs.v[2] += (double)bf.z * bf.z;
-        cs.v[3] += (double)bf.w * bf.w;
+        cs.v[0] = fmaf(bf.x, bf.x, cs.v[0]);
+        cs.v[1] = fmaf(bf.y, bf.y, cs.v[1]);
+        cs.v[2] = fmaf(bf.z, bf.z, cs.v[2]);
+        cs.v[3] = fmaf(bf.w, bf.w, cs.v[3]);
     }
     colsum_finish(cs, bbsum, sh, q.nc);
 }
@@ -822,33 +826,59 @@ __device__ __noinline__ void cgq_first_dir(const E0Q& q, const float* z, double*
         const float4 zv = ldf4q(z, m4), rv = ldf4q(q.R, e4);
         reinterpret_cast<float4*>(q.P)[e4] = zv;
         cs.at(p, rz);
-        cs.v[0] += (double)rv.x * zv.x;
-        cs.v[1] += (double)rv.y * zv.y;
-        cs.v[2] += (double)rv.z * zv.z;
-        cs.v[3] += (double)rv.w * zv.w;
+        cs.v[0] = fmaf(rv.x, zv.x, cs.v[0]);
+        cs.v[1] = fmaf(rv.y, zv.y, cs.v[1]);
+        cs.v[2] = fmaf(rv.z, zv.z, cs.v[2]);
+        cs.v[3] = fmaf(rv.w, zv.w, cs.v[3]);
     }
     colsum_finish(cs, rz, sh, q.nc);
 }
 
 // AP = E_0 P and p.Ap for the active columns
+// The apply loop of one thread's quad (r, k4) over nodes i0, i0 + step, ...:
+// AP = E_0 P and the quad's four sums of p.Ap (masked by am).
+__device__ __noinline__ float4 ap_quad(const MGDeviceLevel L0, const float4* __restrict__ wq,
+                                       int nqd, int k4, unsigned am, int i0, int step, int n,
+                                       const float4* __restrict__ Pr, float4* __restrict__ APr) {
+    Quad qd;
+    qd.load(wq, nqd, k4);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int i = i0; i < n; i += step) {
+        float4 dg;
+        const float4 y = e0_apply4(L0, qd, Pr, i, k4, nqd, dg);
+        const float4 pv = ld4(Pr + (size_t)i * nqd + k4);
+        APr[(size_t)i * nqd + k4] = y;
+        if (am & 1u) s.x = fmaf(y.x, pv.x, s.x);
+        if (am & 2u) s.y = fmaf(y.y, pv.y, s.y);
+        if (am & 4u) s.z = fmaf(y.z, pv.z, s.z);
+        if (am & 8u) s.w = fmaf(y.w, pv.w, s.w);
+    }
+    return s;
+}
+
+// AP = E_0 P and p.Ap for the active columns (each thread on one quad, as in
+// CGQ)
 __device__ __noinline__ void cgq_ap(const E0Q& q, const double* rr_prev, double* pap, double* sh,
                                     unsigned char* s_act, float* s_coef) {
     col_table(kActOnly, q.nc, q.tol2, q.bb, rr_prev, nullptr, nullptr, nullptr, s_act, s_coef);
-    Quad qd;   // loaded on the thread's first item (its quad is fixed)
-    CGQ(q)
-        const unsigned am = quad_mask(s_act, col);
-        if (!am) continue;
-        qd.load(q.wq, q.nqd, k4);
-        const float4* Pr = reinterpret_cast<const float4*>(q.P) + (size_t)r * q.nRp * q.nqd;
-        float4 dg;
-        const float4 y = e0_apply4(q.L0, qd, Pr, i, k4, q.nqd, dg);
-        const float4 pv = ldf4q(q.P, e4);
-        reinterpret_cast<float4*>(q.AP)[e4] = y;
+    ColSum cs;
+    const unsigned na = q.na > 0 ? (unsigned)q.na : 1u;
+    const unsigned rows = gridDim.x * blockDim.x / na;
+    const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = q.na > 0 && t < rows * na ? quad_at(q.ql, (int)(t % na)) : -1;
+    const unsigned am = p >= 0 ? quad_mask(s_act, 4 * p) : 0u;
+    if (am) {
+        const int r = p / q.nqd, k4 = p - r * q.nqd;
+        const size_t off = (size_t)r * q.nRp * q.nqd;
+        const float4 v = ap_quad(q.L0, q.wq, q.nqd, k4, am, (int)(t / na), (int)rows, q.nRp,
+                                 reinterpret_cast<const float4*>(q.P) + off,
+                                 reinterpret_cast<float4*>(q.AP) + off);
         cs.at(p, pap);
-        if (am & 1u) cs.v[0] += (double)y.x * pv.x;
-        if (am & 2u) cs.v[1] += (double)y.y * pv.y;
-        if (am & 4u) cs.v[2] += (double)y.z * pv.z;
-        if (am & 8u) cs.v[3] += (double)y.w * pv.w;
+        cs.v[0] = v.x;
+        cs.v[1] = v.y;
+        cs.v[2] = v.z;
+        cs.v[3] = v.w;
     }
     colsum_finish(cs, pap, sh, q.nc);
 }
@@ -867,14 +897,10 @@ __device__ __noinline__ void cgq_update(const E0Q& q, const double* rr_prev, con
         const float4 a4 = *reinterpret_cast<const float4*>(s_coef + col);
         const float al[4] = {a4.x, a4.y, a4.z, a4.w};
         const float4 pv = ldf4q(q.P, e4), rv = ldf4q(q.R, e4), apv = ldf4q(q.AP, e4);
-        double2* x2 = reinterpret_cast<double2*>(q.X) + 2 * e4;
-        double2 x01 = __ldcg(x2), x23 = __ldcg(x2 + 1);
-        x01.x += (double)(al[0] * pv.x);
-        x01.y += (double)(al[1] * pv.y);
-        x23.x += (double)(al[2] * pv.z);
-        x23.y += (double)(al[3] * pv.w);
-        x2[0] = x01;
-        x2[1] = x23;
+        const float4 xv = ldf4q(q.X32, e4);
+        reinterpret_cast<float4*>(q.X32)[e4] =
+            make_float4(fmaf(al[0], pv.x, xv.x), fmaf(al[1], pv.y, xv.y),
+                        fmaf(al[2], pv.z, xv.z), fmaf(al[3], pv.w, xv.w));
         const float4 rn = make_float4(rv.x - al[0] * apv.x, rv.y - al[1] * apv.y,
                                       rv.z - al[2] * apv.z, rv.w - al[3] * apv.w);
         reinterpret_cast<float4*>(q.R)[e4] = rn;
@@ -900,8 +926,8 @@ __device__ __noinline__ void cgq_rz(const E0Q& q, const float* z, const double* 
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if ((am >> u) & 1u) {
-                    cs.v[u] += (double)r4[u] * z4[u];
-                    c2.v[u] += (double)r4[u] * r4[u];
+                    cs.v[u] = fmaf(r4[u], z4[u], cs.v[u]);
+                    c2.v[u] = fmaf(r4[u], r4[u], c2.v[u]);
                 }
         }
         colsum_finish(cs, rz, sh, q.nc);
@@ -912,6 +938,16 @@ __device__ __noinline__ void cgq_rz(const E0Q& q, const float* z, const double* 
             rr[c] = ldg2(rr_prev + c);
             rz[c] = ldg2(rz_prev + c);
         }
+}
+
+// X (FP64, the caller's layout) = the FP32 iterate, every column
+__device__ __noinline__ void cgq_store_x(const E0Q& q) {
+    CGQ(q)
+        const float4 xv = ldf4q(q.X32, e4);
+        double2* x2 = reinterpret_cast<double2*>(q.X) + 2 * e4;
+        x2[0] = make_double2((double)xv.x, (double)xv.y);
+        x2[1] = make_double2((double)xv.z, (double)xv.w);
+    }
 }
 
 // p = z + beta p for the columns still active
@@ -950,6 +986,7 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
     q.tol2 = a.tol2;
     q.B = a.B;
     q.X = a.X;
+    q.X32 = a.X32;
     q.R = a.R;
     q.P = a.P;
     q.AP = a.AP;
@@ -1001,6 +1038,9 @@ __global__ void __launch_bounds__(256, 2) k_e0_pcg_f(E0Args<float> a) {
             break;
         }
     }
+    q.ql = nullptr;
+    q.na = q.nq;
+    cgq_store_x(q);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.status->iterations = it;
         a.status->converged = s_stop;
@@ -1470,9 +1510,10 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     const int ncols = nrhs * d.nSp;
     char* p = static_cast<char*>(work);
     E0Args<T> a;
-    a.R = reinterpret_cast<T*>(carve<double>(p, n));
-    a.P = reinterpret_cast<T*>(carve<double>(p, n));
-    a.AP = reinterpret_cast<T*>(carve<double>(p, n));
+    a.R = carve<T>(p, n);
+    a.P = carve<T>(p, n);
+    a.AP = carve<T>(p, n);
+    a.X32 = carve<float>(p, n);
     a.acc = carve<double>(p, 9 * (size_t)ncols);
     a.bb = carve<double>(p, ncols);
     a.bar = carve<GridBar>(p, 1);
@@ -1521,8 +1562,8 @@ void set_phase_trace(unsigned long long* buf, int cap) {
 size_t e0_cg_work_bytes(const DevSystem& d, int nrhs) {
     const size_t n = (size_t)nrhs * d.nRp * d.nSp;
     const size_t ncols = (size_t)nrhs * d.nSp;
-    return 3 * (((n * 8) + 255) / 256 * 256) + ((9 * ncols * 8 + 255) / 256 * 256) +
-           ((ncols * 8 + 255) / 256 * 256) + 256;
+    return 3 * (((n * 8) + 255) / 256 * 256) + (((n * 4) + 255) / 256 * 256) +
+           ((9 * ncols * 8 + 255) / 256 * 256) + ((ncols * 8 + 255) / 256 * 256) + 256;
 }
 
 int e0_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nrhs, double tol,
