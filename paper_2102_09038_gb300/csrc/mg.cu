@@ -277,34 +277,62 @@ __device__ __noinline__ void e0_prolong(const MGDeviceLevel Lv, int nq,
     }
 }
 
-// coarsest level: x = (dense inverse of each direction block) B
-__device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* cinv, int nSp, int nc,
-                                      const unsigned short* __restrict__ ql, int na, float* x) {
-    const int km = nSp - 1;
-    ITEMS(Lv.n, 4 * na) {
-        const int col = 4 * quad_at(ql, c >> 2) + (c & 3);
-        // cinv is [i][j][direction], so a warp's lanes (consecutive
-        // columns) read consecutive words
-        const int k = col & km;
-        const float* row = cinv + (size_t)i * Lv.n * nSp + k;
-        const float* bc = Lv.B + col;
-        // 16 independent load pairs in flight per trip
-        constexpr int U = 16;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        int j = 0;
-        for (; j + U <= Lv.n; j += U) {
-            float rv[U], bv[U];
+// coarsest level: x = (dense inverse of each direction block) B, for the
+// active quads.  cinv is [direction][i][j].  Work units are (active quad,
+// chunk of rows), about one per block: the block stages the quad's four B
+// columns in shared memory, and each warp takes two rows at a time with its
+// lanes over j, for the quad's four directions: up to 80 independent
+// 128-byte loads in flight per warp, each inverse row read once.
+__device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* __restrict__ cinv,
+                                      int nSp, int nc, const unsigned short* __restrict__ ql,
+                                      int na, float* __restrict__ x) {
+    constexpr int kTrips = (kDenseCoarseNodes + 31) / 32;
+    __shared__ float sB[4][kDenseCoarseNodes];
+    const int n = Lv.n, kq = (nSp >> 2) - 1;   // n_S^+ = 4^(levels + 1)
+    const int chunks = max(1, min(n, (int)gridDim.x / max(na, 1)));
+    const int rows = (n + chunks - 1) / chunks;
+    const int units = na * chunks;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const int k = u / chunks, h = u - k * chunks;
+        const int p = quad_at(ql, k);
+        const int col0 = 4 * p, d0 = 4 * (p & kq);
+        __syncthreads();   // the previous unit's reads of sB are done
+        for (int t = threadIdx.x; t < 4 * n; t += blockDim.x)
+            sB[t & 3][t >> 2] = ldg2(Lv.B + (size_t)(t >> 2) * nc + col0 + (t & 3));
+        __syncthreads();
+        const int i_end = min(n, (h + 1) * rows);
+        for (int i0 = h * rows + 2 * warp; i0 < i_end; i0 += 2 * nw) {
+            const int i1 = min(i0 + 1, i_end - 1);   // a lone last row is computed twice
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                rv[u] = __ldg(row + (size_t)(j + u) * nSp);
-                bv[u] = ldg2(bc + (size_t)(j + u) * nc);
+            for (int t = 0; t < kTrips; ++t) {
+                const int j = lane + 32 * t;
+                if (j < n) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const float* r0 = cinv + ((size_t)(d0 + c) * n) * n + j;
+                        const float b = sB[c][j];
+                        a0[c] = fmaf(__ldg(r0 + (size_t)i0 * n), b, a0[c]);
+                        a1[c] = fmaf(__ldg(r0 + (size_t)i1 * n), b, a1[c]);
+                    }
+                }
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) acc[u & 3] += rv[u] * bv[u];
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a0[c] += __shfl_xor_sync(0xffffffffu, a0[c], o);
+                    a1[c] += __shfl_xor_sync(0xffffffffu, a1[c], o);
+                }
+            if (lane < 4) {
+                const float v0 = lane == 0 ? a0[0] : lane == 1 ? a0[1] : lane == 2 ? a0[2] : a0[3];
+                const float v1 = lane == 0 ? a1[0] : lane == 1 ? a1[1] : lane == 2 ? a1[2] : a1[3];
+                x[(size_t)i0 * nc + col0 + lane] = v0;
+                x[(size_t)i1 * nc + col0 + lane] = v1;
+            }
         }
-        for (; j < Lv.n; ++j) acc[0] += __ldg(row + (size_t)j * nSp) * ldg2(bc + (size_t)j * nc);
-        x[(size_t)i * nc + col] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-    }}
+    }
 }
 
 // One symmetric V-cycle on B_0 over the quads ql lists (na of them; all

@@ -11,6 +11,8 @@
 namespace rte {
 
 constexpr int kMaxMGLevels = 14;
+// a coarsest level of at most this many nodes is solved by dense inverses
+constexpr int kDenseCoarseNodes = 300;
 
 struct MGDeviceLevel {
     int m = 0, n = 0;

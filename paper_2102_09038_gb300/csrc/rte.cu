@@ -486,7 +486,6 @@ constexpr int kEcMaxTerms = 16;
 
 // Coarsening stops at a level of at most this many nodes, which is then
 // solved with a dense inverse.
-constexpr int kDenseCoarseNodes = 300;
 
 int setup_multigrid(rte_handle* h, const HostSystem& hs) {
     DevSystem& d = h->d;
@@ -533,14 +532,9 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
                 coarse_dense_matrix(mh.levels.back(), w, 6, 1, one);
                 std::copy(one.begin(), one.end(), all.begin() + (size_t)nc * nc * k);
             }
-            std::vector<float> inv;
+            std::vector<float> inv;   // [direction][i][j]
             RTE_TRY(spd_inverse_batch(h, nc, hs.nSp, all, inv));
-            // [k][i][j] -> [i][j][k] (coalesced over directions on the device)
-            std::vector<float> tr(inv.size());
-            const size_t nn = (size_t)nc * nc;
-            for (int k = 0; k < hs.nSp; ++k)
-                for (size_t ij = 0; ij < nn; ++ij) tr[ij * hs.nSp + k] = inv[k * nn + ij];
-            RTE_TRY(upload(h, &d.e0mg.cinv, tr));
+            RTE_TRY(upload(h, &d.e0mg.cinv, inv));
         }
         // level-0 operator of the CG in ELL form, per direction
         std::vector<double> ell6;
