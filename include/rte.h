@@ -88,10 +88,10 @@ typedef struct {
     double mk_tol;          /* relative residual of the (M^- - K^-) PCG      */
     int mk_maxit;
     double e0_tol;          /* relative residual per column of E_0 CG;
-                               0: 1e-12 (FP64) or 1e-1 (mixed modes)         */
+                               0: 1e-12 (FP64) or 0.3 (mixed modes)          */
     int e0_maxit;
     double coarse_tol;      /* relative residual of the E_c CG;
-                               0: 1e-12 (FP64) or 1e-2 (mixed modes)         */
+                               0: 1e-12 (FP64) or 0.1 (mixed modes)          */
     int coarse_maxit;
     int max_iter;           /* outer Richardson iterations                   */
     int max_rhs;            /* workspace is sized for this many RHS          */

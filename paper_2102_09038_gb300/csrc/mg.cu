@@ -278,17 +278,20 @@ __device__ __noinline__ void e0_prolong(const MGDeviceLevel Lv, int nq,
 }
 
 // coarsest level: x = (dense inverse of each direction block) B, for the
-// active quads.  cinv is [direction][i][j].  Work units are (active quad,
-// chunk of rows), about one per block: the block stages the quad's four B
-// columns in shared memory, and each warp takes two rows at a time with its
-// lanes over j, for the quad's four directions: up to 80 independent
-// 128-byte loads in flight per warp, each inverse row read once.
+// active quads.  cinv is [direction][i][j], rows padded with zeros to n4 (a
+// multiple of 4) so that lanes read them as float4.  Work units are (active
+// quad, chunk of rows), about one per block: the block stages the quad's
+// four B columns in shared memory (zero past n), and each warp takes a row
+// at a time with its lanes over j, for the quad's four directions: up to 12
+// independent 512-byte warp loads in flight, each inverse row read once.
 __device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* __restrict__ cinv,
                                       int nSp, int nc, const unsigned short* __restrict__ ql,
                                       int na, float* __restrict__ x) {
-    constexpr int kTrips = (kDenseCoarseNodes + 31) / 32;
-    __shared__ float sB[4][kDenseCoarseNodes];
-    const int n = Lv.n, kq = (nSp >> 2) - 1;   // n_S^+ = 4^(levels + 1)
+    constexpr int kN4 = (kDenseCoarseNodes + 3) & ~3;
+    constexpr int kTrips = (kN4 / 4 + 31) / 32;
+    __shared__ __align__(16) float sB[4][kN4];
+    const int n = Lv.n, n4 = (n + 3) & ~3, q4 = n4 >> 2;
+    const int kq = (nSp >> 2) - 1;   // n_S^+ = 4^(levels + 1)
     const int chunks = max(1, min(n, (int)gridDim.x / max(na, 1)));
     const int rows = (n + chunks - 1) / chunks;
     const int units = na * chunks;
@@ -298,39 +301,35 @@ __device__ __noinline__ void e0_dense(const MGDeviceLevel Lv, const float* __res
         const int p = quad_at(ql, k);
         const int col0 = 4 * p, d0 = 4 * (p & kq);
         __syncthreads();   // the previous unit's reads of sB are done
-        for (int t = threadIdx.x; t < 4 * n; t += blockDim.x)
-            sB[t & 3][t >> 2] = ldg2(Lv.B + (size_t)(t >> 2) * nc + col0 + (t & 3));
+        for (int t = threadIdx.x; t < 4 * n4; t += blockDim.x) {
+            const int j = t >> 2;
+            sB[t & 3][j] = j < n ? ldg2(Lv.B + (size_t)j * nc + col0 + (t & 3)) : 0.f;
+        }
         __syncthreads();
         const int i_end = min(n, (h + 1) * rows);
-        for (int i0 = h * rows + 2 * warp; i0 < i_end; i0 += 2 * nw) {
-            const int i1 = min(i0 + 1, i_end - 1);   // a lone last row is computed twice
-            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int i = h * rows + warp; i < i_end; i += nw) {
+            float a0[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int t = 0; t < kTrips; ++t) {
-                const int j = lane + 32 * t;
-                if (j < n) {
+                const int j4 = lane + 32 * t;
+                if (j4 < q4) {
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        const float* r0 = cinv + ((size_t)(d0 + c) * n) * n + j;
-                        const float b = sB[c][j];
-                        a0[c] = fmaf(__ldg(r0 + (size_t)i0 * n), b, a0[c]);
-                        a1[c] = fmaf(__ldg(r0 + (size_t)i1 * n), b, a1[c]);
+                        const float4* r = reinterpret_cast<const float4*>(
+                                              cinv + (size_t)(d0 + c) * n * n4) + j4;
+                        const float4 b = reinterpret_cast<const float4*>(sB[c])[j4];
+                        const float4 v = __ldg(r + (size_t)i * q4);
+                        a0[c] = fmaf(v.x, b.x, fmaf(v.y, b.y, fmaf(v.z, b.z, fmaf(v.w, b.w, a0[c]))));
                     }
                 }
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    a0[c] += __shfl_xor_sync(0xffffffffu, a0[c], o);
-                    a1[c] += __shfl_xor_sync(0xffffffffu, a1[c], o);
-                }
-            if (lane < 4) {
-                const float v0 = lane == 0 ? a0[0] : lane == 1 ? a0[1] : lane == 2 ? a0[2] : a0[3];
-                const float v1 = lane == 0 ? a1[0] : lane == 1 ? a1[1] : lane == 2 ? a1[2] : a1[3];
-                x[(size_t)i0 * nc + col0 + lane] = v0;
-                x[(size_t)i1 * nc + col0 + lane] = v1;
-            }
+                for (int o = 16; o > 0; o >>= 1) a0[c] += __shfl_xor_sync(0xffffffffu, a0[c], o);
+            if (lane < 4)
+                x[(size_t)i * nc + col0 + lane] =
+                    lane == 0 ? a0[0] : lane == 1 ? a0[1] : lane == 2 ? a0[2] : a0[3];
         }
     }
 }
