@@ -175,8 +175,9 @@ def fp64_peak_tflops(torch):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel group as last captured with ncu on the default workload (the summary
 # and command are in profiles/); a kernel changed since its capture has no
-# entry.  k_e0_pcg_f: mean of two captured launches of 13 PCG iterations.
-PROFILED_DRAM_BYTES = {}
+# entry.  k_e0_pcg_f: mean of two captured launches (the 9th and 10th of the
+# solve).
+PROFILED_DRAM_BYTES = {'e0_cg_lo': 2.81e9}
 
 
 def kernel_work(name, d, nrhs, info):
