@@ -62,6 +62,23 @@ extern "C" {
 #define RTE_MK_EIGEN 0      /* exact, in the full eigenbasis of (S^-, M_S^-) */
 #define RTE_MK_PCG 1        /* PCG with the Lemma apply_high_order_pre prec. */
 
+/* How P_1 is realised (Section 5.3).  RTE_P1_RICHARDSON is P_1^l of eq.
+ * (applyP1): l steps of the preconditioned Richardson iteration for E from
+ * z = 0, a fixed SPD matrix (Lemma preconditioner_pl).  RTE_P1_PCG takes l
+ * steps of conjugate gradients for E z = b preconditioned by E_0^{-1}, from
+ * z = 0: the non-stationary alternative the same section names beside it.
+ * Its result is the E-norm-best point of the same Krylov space (so never
+ * worse than P_1^l b in that norm) but depends nonlinearly on b, so
+ * rte_rates, whose power iterations need a fixed iteration matrix, refuses
+ * it.  Per application: l E_0^{-1} solves (as P_1^l) and l applies of E
+ * (one more than P_1^l).  RTE_P1_AUTO (the default) takes P_1^l in FP64
+ * mode, the paper's method as stated, and the PCG steps in the mixed modes,
+ * where they reach 1e-6 on the 128x128 / 512-triangle workload in 16 outer
+ * iterations instead of 27. */
+#define RTE_P1_AUTO (-1)
+#define RTE_P1_RICHARDSON 0
+#define RTE_P1_PCG 1
+
 typedef struct rte_handle rte_handle;
 
 /* The problem of Section 1, eq. (rte1)-(rte2), with vacuum inflow:
@@ -102,6 +119,8 @@ typedef struct {
     int autotune;           /* 1: time the launch shapes of the SpMM kernels
                                and tensor-core GEMMs at setup (cached per
                                shape for the process); 0: fixed shapes       */
+    int p1_route;           /* RTE_P1_AUTO (default) | RTE_P1_RICHARDSON |
+                               RTE_P1_PCG                                    */
 } rte_options;
 
 typedef struct {

@@ -198,3 +198,29 @@ class Operators:
         for _ in range(1, l):
             z = z - self.solve_E0(self.apply_E(z) - B)
         return z
+
+    def apply_P1_pcg(self, B, l=4):
+        """The non-stationary P_1 named in Section 5.3 beside eq. (applyP1):
+        l steps of the conjugate gradient method for E z = b with
+        preconditioner E_0^{-1}, started from z = 0 (textbook PCG: residual
+        r, preconditioned residual y = E_0^{-1} r, directions p, step length
+        r.y / p.Ep, direction update with the ratio of successive r.y).
+        Inner products are over all of b's coefficients."""
+        z = np.zeros_like(B)
+        r = B.copy()
+        y = self.solve_E0(r)
+        p = y.copy()
+        ry = np.vdot(r, y)
+        for k in range(l):
+            w = self.apply_E(p)
+            pw = np.vdot(p, w)
+            alpha = ry / pw if pw != 0.0 else 0.0
+            z = z + alpha * p
+            if k + 1 == l:
+                break
+            r = r - alpha * w
+            y = self.solve_E0(r)
+            ry_new = np.vdot(r, y)
+            p = y + (ry_new / ry if ry != 0.0 else 0.0) * p
+            ry = ry_new
+        return z

@@ -94,9 +94,11 @@ class Coarse:
         return x.reshape(Qc.shape)
 
 
-def richardson(ops, q, tol=1e-10, maxit=200, l=4, N=4, u0=None, coarse=None):
+def richardson(ops, q, tol=1e-10, maxit=200, l=4, N=4, u0=None, coarse=None, p1='richardson'):
     """Algorithm 3 (eq. Richardson_discrete with the product preconditioner
-    of eq. product_pre) with the readings in the module docstring.
+    of eq. product_pre) with the readings in the module docstring.  p1 picks
+    the realisation of P_1: 'richardson' (P_1^l, eq. applyP1) or 'pcg' (l
+    PCG steps, the non-stationary choice of Section 5.3).
 
     Returns (u, info) where info holds the iteration count, the residual
     history ||r_n||/||q|| and the energy-norm update sizes."""
@@ -116,7 +118,7 @@ def richardson(ops, q, tol=1e-10, maxit=200, l=4, N=4, u0=None, coarse=None):
             upd.append(np.sqrt(max(np.vdot(delta, r - r_prev), 0.0)))
         if rel <= tol or it == maxit:
             break
-        s = ops.apply_P1(r, l)
+        s = ops.apply_P1_pcg(r, l) if p1 == 'pcg' else ops.apply_P1(r, l)
         u_half = u - s
         if coarse is not None:
             t = ops.apply_EK(s) - r

@@ -12,10 +12,12 @@ import ctypes
 import os
 
 __all__ = ['Solver', 'RteError', 'load', 'OPS', 'FP64', 'MIXED_FP32',
-           'MIXED_BF16', 'MK_EIGEN', 'MK_PCG']
+           'MIXED_BF16', 'MK_EIGEN', 'MK_PCG', 'P1_AUTO', 'P1_RICHARDSON',
+           'P1_PCG']
 
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 MK_EIGEN, MK_PCG = 0, 1
+P1_AUTO, P1_RICHARDSON, P1_PCG = -1, 0, 1
 DGEMM_AUTO, DGEMM_SIMT, DGEMM_SPLIT = 0, 1, 2
 OPS = dict(A=1, AT=2, KPLUS=3, MK=4, MK_INV=5, MK_PREC=6, E=7, E0_INV=8,
            P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13, E_LO=14, EK_LO=15)
@@ -50,7 +52,7 @@ class _Options(ctypes.Structure):
                 ('coarse_maxit', ctypes.c_int), ('max_iter', ctypes.c_int),
                 ('max_rhs', ctypes.c_int), ('dgemm', ctypes.c_int),
                 ('split_slices', ctypes.c_int), ('mg_sweeps', ctypes.c_int),
-                ('autotune', ctypes.c_int)]
+                ('autotune', ctypes.c_int), ('p1_route', ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):

@@ -60,6 +60,7 @@ struct rte_handle {
     void* slices = nullptr;                                             // split GEMM operand
     double *e1 = nullptr, *e2 = nullptr, *e3 = nullptr, *e4 = nullptr, *e5 = nullptr,
            *e6 = nullptr, *e7 = nullptr, *e8 = nullptr;                     // even
+    double *e9 = nullptr, *e10 = nullptr;   // even, RTE_P1_PCG only
     double *c1 = nullptr, *c2 = nullptr;                                    // coarse
     // mixed precision: FP32 even vectors, low-precision odd GEMM operands
     bool mixed = false;
@@ -714,6 +715,10 @@ int alloc_workspace(rte_handle* h, int nrhs) {
     }
     double** ev[] = {&h->e1, &h->e2, &h->e3, &h->e4, &h->e5, &h->e6, &h->e7, &h->e8};
     for (auto p : ev) RTE_TRY(dalloc(h, p, ne));
+    if (h->opt.p1_route == RTE_P1_PCG) {
+        RTE_TRY(dalloc(h, &h->e9, ne));
+        RTE_TRY(dalloc(h, &h->e10, ne));
+    }
     RTE_TRY(dalloc(h, &h->c1, nc));
     RTE_TRY(dalloc(h, &h->c2, nc));
     RTE_TRY(dalloc(h, &h->partial, (size_t)nrhs * 1024));
@@ -1007,7 +1012,53 @@ int apply_E_inner(rte_handle* h, const double* x, double* y, int nrhs, bool with
     return RTE_OK;
 }
 
+// z = l steps of CG for E z = b preconditioned by E_0^{-1}, from z = 0
+// (RTE_P1_PCG, Section 5.3).  Uses e5, e6, e9, e10 and sc[8n, 12n) (the
+// (M^- - K^-) PCG inside the inner applies uses sc[0, 6n)); the per-RHS step
+// lengths stay on the device.
+int apply_P1_pcg(rte_handle* h, const double* b, double* z, int nrhs) {
+    const DevSystem& d = h->d;
+    const size_t len = (size_t)d.nRp * d.nSp;
+    const int n = nrhs;
+    cudaStream_t s = h->stream;
+    double *R = h->e9, *P = h->e10, *Y = h->e6, *W = h->e5;
+    double *rho = h->sc + 8 * n, *tmp = h->sc + 9 * n, *alpha = h->sc + 10 * n,
+           *beta = h->sc + 11 * n;
+    const unsigned rb = (unsigned)((n + 63) / 64);
+    RTE_CUDA_TRY(cudaMemcpyAsync(R, b, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
+    RTE_CUDA_TRY(cudaMemsetAsync(z, 0, sizeof(double) * n * len, s));
+    RTE_TRY(e0_inv(h, R, Y, n));                       // y = E_0^{-1} r
+    RTE_CUDA_TRY(cudaMemcpyAsync(P, Y, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
+    dot_per_rhs(s, R, Y, len, n, h->partial, rho);     // rho = r.y
+    for (int k = 0; k < h->opt.l; ++k) {
+        RTE_TRY(apply_E_inner(h, P, W, n, false));     // w = E p
+        {
+            Scope sc(h, "axpy");
+            dot_per_rhs(s, P, W, len, n, h->partial, tmp);
+            k_ratio<<<rb, 64, 0, s>>>(rho, tmp, alpha, n, 1.0);   // alpha = rho / p.w
+            count_launches(1);
+            axpby_per_rhs(s, P, z, len, n, alpha, 0.0, nullptr, 1.0);   // z += alpha p
+        }
+        if (k + 1 == h->opt.l) break;
+        {
+            Scope sc(h, "axpy");
+            k_ratio<<<rb, 64, 0, s>>>(rho, tmp, alpha, n, -1.0);
+            count_launches(1);
+            axpby_per_rhs(s, W, R, len, n, alpha, 0.0, nullptr, 1.0);   // r -= alpha w
+        }
+        RTE_TRY(e0_inv(h, R, Y, n));
+        Scope sc(h, "axpy");
+        dot_per_rhs(s, R, Y, len, n, h->partial, tmp);                  // r.y
+        k_ratio<<<rb, 64, 0, s>>>(tmp, rho, beta, n, 1.0);             // beta = r.y / rho
+        count_launches(1);
+        RTE_CUDA_TRY(cudaMemcpyAsync(rho, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        axpby_per_rhs(s, Y, P, len, n, nullptr, 1.0, beta, 0.0);        // p = y + beta p
+    }
+    return RTE_OK;
+}
+
 int apply_P1(rte_handle* h, const double* b, double* z, int nrhs) {
+    if (h->opt.p1_route == RTE_P1_PCG) return apply_P1_pcg(h, b, z, nrhs);
     const DevSystem& d = h->d;
     const size_t len = (size_t)d.nRp * d.nSp;
     RTE_TRY(e0_inv(h, b, z, nrhs));   // z_1 = E_0^{-1} b
@@ -1091,6 +1142,7 @@ int rte_default_options(rte_options* o) {
     o->split_slices = 7;
     o->mg_sweeps = 2;
     o->autotune = 1;
+    o->p1_route = RTE_P1_AUTO;   // P_1^l in FP64, PCG steps in the mixed modes
     return RTE_OK;
 }
 
@@ -1106,6 +1158,11 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     if (o.precision != RTE_FP64 && o.precision != RTE_MIXED_FP32 &&
         o.precision != RTE_MIXED_BF16)
         return fail(RTE_ERR_ARG, "unknown precision mode");
+    if (o.p1_route != RTE_P1_AUTO && o.p1_route != RTE_P1_RICHARDSON &&
+        o.p1_route != RTE_P1_PCG)
+        return fail(RTE_ERR_ARG, "unknown P_1 route");
+    if (o.p1_route == RTE_P1_AUTO)
+        o.p1_route = o.precision == RTE_FP64 ? RTE_P1_RICHARDSON : RTE_P1_PCG;
     if (o.precision != RTE_FP64 && o.mk_route != RTE_MK_EIGEN)
         return fail(RTE_ERR_ARG, "mixed precision uses the eigenbasis route for (M-K)^-1");
     // inner tolerances left at 0 follow the precision mode: the plain FP64
@@ -1624,6 +1681,8 @@ int power_step(rte_handle* h, double* x, const double* y, double* ratio) {
 int rte_rates(rte_handle* h, int maxit, double tol, unsigned long long seed, double* rho,
               double* eta, int* iters) {
     if (!h || maxit < 1 || !(tol >= 0) || (!rho && !eta)) return fail(RTE_ERR_ARG, "bad argument");
+    if (h->opt.p1_route != RTE_P1_RICHARDSON)
+        return fail(RTE_ERR_ARG, "rates need the stationary P_1^l (RTE_P1_RICHARDSON)");
     const DevSystem& d = h->d;
     cudaStream_t s = h->stream;
     const size_t len = (size_t)d.nRp * d.nSp;

@@ -146,6 +146,10 @@ size_t rte_estimate_bytes(const rte_problem* p, const rte_options* o, int nrhs) 
     size_t b = 0;
     b += r * nRm * nSm * 8 * 5;                // odd work arrays and slices
     b += r * nRp * nSp * 8 * 13;               // even work arrays, E_0 CG vectors
+    b += r * nRp * nSp * 4;                    // E_0 FP32 iterate
+    const bool p1_pcg = o && (o->p1_route == RTE_P1_PCG ||
+                              (o->p1_route == RTE_P1_AUTO && o->precision != RTE_FP64));
+    if (p1_pcg) b += r * nRp * nSp * 8 * 2;    // the P_1 PCG's r and p
     b += nSm * nSm * 8 * 5 + nSp * nSp * 8 * 3;   // dense angular factors, slices
     b += 7 * nRp * nSp * 12;                   // E_0 stencil coefficients
     b += 7 * nRp * nSp * 4 * 4 / 3;            // multigrid coefficients

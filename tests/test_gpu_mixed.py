@@ -145,3 +145,23 @@ def test_autotuned_launch_shapes(prec):
         assert torch.equal(a, b), op
     tuned.close()
     fixed.close()
+
+
+@pytest.mark.parametrize('prec', [0, 2])
+def test_p1_pcg_route_solves(prec):
+    # Algorithm 3 with P_1 as l PCG steps (RTE_P1_PCG) reaches the FP64
+    # residual in FP64 and in the mixed BF16 mode
+    import paper_2102_09038_gb300 as rte
+    p = workloads.checkerboard(m=24, levels=2, g=0.8, ratio=0.97, blocks=4, nrhs=2)
+    disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
+    ops = oracle.Operators(disc, n_plus=2, n_minus=3)
+    s = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, max_rhs=2, p1_route=rte.P1_PCG)
+    q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
+    u, info = s.solve(q, tol=1e-10)
+    s.close()
+    assert info['status'] == 0, info
+    assert info['e0_launches'] == 4 * info['iterations'], info
+    u = u.cpu().numpy()
+    for r in range(p.nrhs):
+        qr = disc.source(p.q_nodal[r])
+        assert np.linalg.norm(ops.apply_EK(u[r]) - qr) / np.linalg.norm(qr) < 2e-10

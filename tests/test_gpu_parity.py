@@ -192,6 +192,38 @@ def test_p1_and_coarse_steps(pair):
         assert np.linalg.norm(res) / np.linalg.norm(qc[r]) < 2e-12
 
 
+@pytest.mark.parametrize('case', ['tiny', 'ragged', 'odd35'])
+def test_p1_pcg_route(case):
+    # P_1 as l = 4 PCG steps for E with E_0^{-1} (RTE_P1_PCG): the operator
+    # against the oracle's PCG, and Algorithm 3 with it against the oracle's
+    # Algorithm 3 with the same P_1
+    import paper_2102_09038_gb300 as rte
+    pr = Pair(case, p1_route=rte.P1_PCG)
+    try:
+        ops, p = pr.ops, pr.p
+        b = pr.even(2)
+        got = pr.run('P1', b, b.shape)
+        ref = np.stack([ops.apply_P1_pcg(v, 4) for v in b])
+        assert relerr(got, ref) < 1e-8
+        qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
+        q = pr.gpu.rhs(qn)
+        qref = np.stack([pr.disc.source(v) for v in p.q_nodal])
+        u, info = pr.gpu.solve(q, tol=1e-11)
+        assert info['status'] == 0, info
+        u = u.cpu().numpy()
+        for r in range(p.nrhs):
+            res = np.linalg.norm(ops.apply_EK(u[r]) - qref[r]) / np.linalg.norm(qref[r])
+            assert res < 1e-10, res
+        uo, io = richardson(ops, qref[0], tol=1e-11, l=4, N=2, p1='pcg')
+        assert abs(info['iterations'] - io['iterations']) <= 1
+        assert relerr(u[0], uo) < 1e-8
+        # the rates need a fixed iteration matrix
+        with pytest.raises(rte.RteError):
+            pr.gpu.rates(maxit=5)
+    finally:
+        pr.gpu.close()
+
+
 def test_precond_product_form(pair):
     # rte_precond = P_1 + W E_c^{-1} W^T (I - (E - K) P_1)  (eq. product_pre)
     ops, nr = pair.ops, 1

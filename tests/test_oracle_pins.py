@@ -381,6 +381,40 @@ def test_fixed_point_and_cluster_rotation(tiny):
     assert np.abs(PG - PG2).max() < 1e-10 * np.abs(PG).max()
 
 
+def test_p1_pcg_krylov_optimality_and_limit(tiny):
+    # The non-stationary P_1 of Section 5.3: l CG steps for E z = b with the
+    # preconditioner E_0^{-1}, from z = 0.  Its iterate is the E-norm-best
+    # point of the Krylov space of E_0^{-1} E and E_0^{-1} b of dimension l,
+    # which also holds P_1^l b of eq. (applyP1): its E-norm error is never
+    # the larger of the two; enough steps reach E^{-1} b; and with g = 0
+    # (E = E_0) one step is exact.
+    p, disc, ops = tiny
+    n = disc.nRp * disc.nSp
+    I = np.eye(n)
+    E = np.stack([ops.apply_E(I[:, i].reshape(disc.nRp, -1)).ravel() for i in range(n)], 1)
+    b = np.random.default_rng(11).standard_normal((disc.nRp, disc.nSp))
+    xs = np.linalg.solve(E, b.ravel())
+
+    def err(z):
+        e = z.ravel() - xs
+        return np.sqrt(e @ E @ e)
+
+    prev = np.inf
+    for l in (1, 2, 3, 4, 6):
+        ec, er = err(ops.apply_P1_pcg(b, l)), err(ops.apply_P1(b, l))
+        assert ec <= er * (1 + 1e-10), (l, ec, er)
+        assert ec < prev
+        prev = ec
+    z = ops.apply_P1_pcg(b, 40)
+    assert np.linalg.norm(z.ravel() - xs) <= 1e-9 * np.linalg.norm(xs)
+    p0 = workloads.constant(3, 1, 0.0, 1.0, 0.9, 1.0)
+    d0 = oracle.Discretisation(p0.m, p0.levels, p0.sigma_t, p0.sigma_s, p0.g)
+    o0 = oracle.Operators(d0, n_plus=2, n_minus=1)
+    b0 = np.random.default_rng(12).standard_normal((d0.nRp, d0.nSp))
+    z1 = o0.apply_P1_pcg(b0, 1)
+    assert np.abs(o0.apply_E(z1) - b0).max() < 1e-11 * np.abs(b0).max()
+
+
 def test_richardson_matches_direct_solve(tiny):
     p, disc, ops = tiny
     q = disc.source(p.q_nodal[0])
