@@ -72,3 +72,44 @@ def test_static_split_gemm_refuses_oversize_operands_on_the_host(lib_path):
     # just above the limit: M = N = 1024, K = 1176 needs 33,718,272 bytes of slices
     assert lib.rte_dgemm_split_static(fake, fake, fake, 1024, 1024, 1176, 7, None) == 1
     assert lib.rte_dgemm_split_static(fake, fake, fake, 1, 1, 1, 0, None) == 1
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program gcc builds."""
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "rte.h"',
+             'int main(void) {', '  printf("%%zu\\n", sizeof(%s));' % struct]
+    lines += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    lines += ['  return 0;', '}']
+    src = tmp_path / ('layout_%s.c' % struct)
+    src.write_text('\n'.join(lines) + '\n')
+    exe = tmp_path / ('layout_%s' % struct)
+    subprocess.run(['gcc', '-I', os.path.join(ROOT, 'include'), str(src), '-o', str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    vals = [int(v) for v in out.split()]
+    return vals[0], vals[1:]
+
+
+@pytest.mark.parametrize('struct, mirror', [('rte_options', '_Options'),
+                                            ('rte_stats', '_Stats'),
+                                            ('rte_problem', '_Problem')])
+def test_binding_structs_match_the_header_layout(struct, mirror, tmp_path):
+    # the ctypes mirrors of the binding have the header's field order,
+    # offsets and size (a field added on one side only would shift the rest)
+    import ctypes
+    import paper_2102_09038_gb300 as rte
+    cls = getattr(rte, mirror)
+    fields = [f[0] for f in cls._fields_]
+    size, offs = _c_layout(struct, fields, tmp_path)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
+
+
+def test_default_options_through_the_library(lib_path):
+    # rte_default_options fills the struct the binding reads back
+    import paper_2102_09038_gb300 as rte
+    o = rte.default_options()
+    assert o.p1_route == rte.P1_AUTO and o.precision == rte.FP64
+    assert o.autotune == 1 and o.max_rhs >= 1
+    o = rte.default_options(p1_route=rte.P1_PCG, precision=rte.MIXED_BF16)
+    assert (o.p1_route, o.precision) == (rte.P1_PCG, rte.MIXED_BF16)
