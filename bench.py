@@ -404,6 +404,10 @@ def run_ours(args):
                    data='synthetic',
                    config=dict(WORKLOAD, nrhs=p.nrhs, dofs=p.dofs,
                                precision=args.precision,
+                               p1=('l PCG steps' if args.precision != 'fp64'
+                                   else 'P_1^l Richardson steps'),
+                               inner_tol=('E_0 0.3, E_c 0.1' if args.precision != 'fp64'
+                                          else 'E_0 and E_c 1e-12'),
                                iterations_per_solve=iters / args.steps,
                                time_to_tol_s=secs / args.steps,
                                l2='inputs larger than L2: odd work arrays %d MB'
