@@ -191,7 +191,9 @@ def kernel_work(name, d, nrhs, info):
         CG vector traffic (P read and AP written by the apply; P, R, AP read,
         R and V-cycle input written by the update; R, z read for r.z and
         r.r; z, P read and P written by the direction update: 12 words of
-        the CG precision, plus 16 B of FP64 X) and the V-cycle's 17 FP32 array
+        the CG precision, plus the iterate read and written: 16 B in FP64,
+        8 B in the FP32 kernel, which writes FP64 X once at the end) and the
+        V-cycle's 17 FP32 array
         passes per level (4^-l of the level-0 size), times the V-cycles of
         the launch (the mean over the solve's launches), each weighted by the
         fraction of direction quads with a column not yet converged: the
@@ -215,7 +217,7 @@ def kernel_work(name, d, nrhs, info):
     if name in ('e0_cg', 'e0_cg_lo'):
         ts = 8 if name == 'e0_cg' else 4
         cols = nrhs * nS
-        cg = nRp * cols * (12 * ts + 16 + (7 * 8 if name == 'e0_cg' else 0))
+        cg = nRp * cols * (12 * ts + 2 * ts + (7 * 8 if name == 'e0_cg' else 0))
         vc = sum(nRp / 4 ** l * cols * 4 * 17 for l in range(d['e0_levels']))
         # the coarsest level's dense per-direction inverses, read once per V-cycle
         mc = d['mesh'] >> (d['e0_levels'] - 1)
@@ -224,7 +226,8 @@ def kernel_work(name, d, nrhs, info):
         # quads still active (converged columns are not visited again)
         n = info.get('e0_launches', 0)
         per = info['e0_active_vcycles'] / n if n else max(info.get('e0_iters', 1), 1)
-        return (cg + vc) * per, 'byte', 'hbm'
+        once = nRp * cols * 16   # B read and X written in FP64, once per launch
+        return (cg + vc) * per + once, 'byte', 'hbm'
     if name == 'coarse_cg':
         dp = d['dP']
         cg = nRp * nrhs * (7 * dp * dp + 12 * dp) * 8
