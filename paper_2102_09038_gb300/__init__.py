@@ -343,7 +343,8 @@ class Solver:
         return self.torch.zeros((nrhs, self.n_nodes, self.n_dirs),
                                 dtype=self.torch.float64, device='cuda')
 
-    def odd(self, nrhs=1):
+    def odd_zeros(self, nrhs=1):
+        # (odd(), below, recovers the odd part of a solution)
         return self.torch.zeros((nrhs, self.n_cells, self.n_odd),
                                 dtype=self.torch.float64, device='cuda')
 
