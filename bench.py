@@ -262,6 +262,7 @@ def run_ours(args):
     p = workloads.checkerboard(m=args.mesh, levels=args.levels, g=0.9, ratio=0.99,
                                seed=rank)
     solver = rte.Solver(p, precision=prec)
+    setup_ms = {k: round(v, 1) for k, v in solver.setup_times().items()}
     qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
     q = solver.rhs(qn)
     u = solver.even(p.nrhs)
@@ -418,7 +419,7 @@ def run_ours(args):
                                parallelism='replicas' if world > 1 else 'single'),
                    e2e=e2e, gpu_launches=launches, roofline=roof,
                    kernel_share=share, clocks=clk.summary(), cpu_baseline=cpu,
-                   fp64_compare=fp64, serving=serving)
+                   fp64_compare=fp64, serving=serving, setup_ms=setup_ms)
         if batch is not None:
             out['batch'] = batch
         print(json.dumps(out))

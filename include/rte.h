@@ -314,6 +314,16 @@ int rte_timing_enable(rte_handle* h, int on);
 int rte_timing_read(rte_handle* h, const char** names, double* ms,
                     long long* launches, int cap, int* count);
 
+/* Wall-clock milliseconds of the stages of the rte_setup that made h (host
+ * assembly, scattering matrices, the two angular eigen-decompositions, the
+ * coarse matrix E_c, the FP64 split operands, the E_0 and E_c multigrid
+ * hierarchies, the workspace, launch tuning); each stage ends with a synchronisation of the
+ * handle's stream, so device work is charged to the stage that issued it.
+ * names[i] and ms[i] for i < min(*count, cap); the names stay valid while
+ * h lives.  Not part of the paper's method: profiling of the setup. */
+int rte_setup_times(const rte_handle* h, const char** names, double* ms, int cap,
+                    int* count);
+
 /* Phase trace of the persistent solver kernels, for profiling: with on != 0
  * the next E_0 / E_c solves record the time after every grid barrier of
  * their launch; rte_trace_read copies the intervals (microseconds) of the

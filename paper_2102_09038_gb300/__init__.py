@@ -122,6 +122,8 @@ def load(path=LIB_PATH):
                                     ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.rte_server_destroy.argtypes = [P]
     lib.rte_server_destroy.restype = V
+    lib.rte_setup_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D), I,
+                                    ctypes.POINTER(I)]
     lib.rte_trace_enable.argtypes = [P, I]
     lib.rte_trace_read.argtypes = [P, ctypes.POINTER(D), I, ctypes.POINTER(I)]
     lib.rte_kernel_launches.argtypes = []
@@ -460,6 +462,16 @@ class Solver:
         _check(_lib.rte_timing_read(self._h, names, ms, cnt, cap,
                                     ctypes.byref(n)))
         return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n.value, cap))}
+
+    def setup_times(self):
+        """{stage: wall-clock ms} of the setup that made this solver
+        (rte_setup_times)."""
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        _check(_lib.rte_setup_times(self._h, names, ms, cap, ctypes.byref(n)))
+        return {names[i].decode(): ms[i] for i in range(min(n.value, cap))}
 
     def trace(self, on=True):
         """Record per-barrier phase times of the next persistent solves."""

@@ -87,6 +87,9 @@ struct rte_handle {
     std::vector<std::string> tnames;
     std::vector<TimerRec> trecs;
     std::vector<double> tms;
+    // wall-clock stages of rte_setup
+    std::vector<std::string> setup_names;
+    std::vector<double> setup_ms;
     std::vector<long long> tcount;
 };
 
@@ -157,6 +160,22 @@ int upload(rte_handle* h, const T** dst, const std::vector<T>& src) {
 }
 
 // ------------------------------------------------------------- timing
+// Wall-clock stages of rte_setup: mark() waits for the stream (so a stage's
+// device work is charged to it) and records the time since the last mark.
+struct SetupClock {
+    rte_handle* h;
+    std::chrono::steady_clock::time_point t = std::chrono::steady_clock::now();
+    void mark(const char* name) {
+        if (h) cudaStreamSynchronize(h->stream);
+        const auto now = std::chrono::steady_clock::now();
+        if (h) {
+            h->setup_names.push_back(name);
+            h->setup_ms.push_back(std::chrono::duration<double, std::milli>(now - t).count());
+        }
+        t = now;
+    }
+};
+
 struct Scope {
     rte_handle* h;
     int idx = -1;
@@ -488,7 +507,7 @@ constexpr int kEcMaxTerms = 16;
 // Coarsening stops at a level of at most this many nodes, which is then
 // solved with a dense inverse.
 
-int setup_multigrid(rte_handle* h, const HostSystem& hs) {
+int setup_multigrid(rte_handle* h, const HostSystem& hs, SetupClock* clk) {
     DevSystem& d = h->d;
     const int cap = h->opt.max_rhs;
     // ------------------------------------------------------------ E_0
@@ -552,6 +571,7 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs) {
         e0_coefficients(h->stream, hs.nRp, hs.nSp, dell, d.e0s, c, nullptr);
         d.e0coef = c;
     }
+    if (clk) clk->mark("E_0 multigrid");
     // ------------------------------------------------------------ E_c
     if (d.dP > 0) {
         MGHost mh;
@@ -1172,12 +1192,15 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     // gave the shortest times to 1e-6 over the workload configurations)
     if (!(o.e0_tol > 0)) o.e0_tol = o.precision == RTE_FP64 ? 1e-12 : 0.3;
     if (!(o.coarse_tol > 0)) o.coarse_tol = o.precision == RTE_FP64 ? 1e-12 : 0.1;
+    SetupClock clk{nullptr};
     HostSystem hs;
     RTE_TRY(build_host_system(*prob, o, hs));
     rte_handle* h = new rte_handle();
     h->opt = o;
     h->stream = (cudaStream_t)stream;
     keep_pool_memory();
+    clk.h = h;
+    clk.mark("host assembly");
     auto bail = [&](int rc) {
         rte_destroy(h);
         return rc;
@@ -1257,6 +1280,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     h->h_m = hs.m_; h->h_MSm = hs.MSm; h->h_A1 = hs.A1; h->h_A2 = hs.A2;
     h->h_omx = hs.omx; h->h_omy = hs.omy;
 
+    clk.mark("uploads and scattering matrices");
     // --------------------------------------- eigenpairs of (S^+, M_S^+)
     std::vector<double> C((size_t)n * n), w;
     for (int i = 0; i < n; ++i)
@@ -1285,6 +1309,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     UP(WpNT, WpNT);
     UP(lamP, h->h_lamP);
 
+    clk.mark("eigenpairs of S+");
     // --------------------------------------- eigenpairs of (S^-, M_S^-)
     // M_S^- = L L^T blockwise; C = L^{-1} S^- L^{-T}; W = L^{-T} Q
     std::vector<double> Linv((size_t)9 * n);
@@ -1346,6 +1371,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     UP(WmN, WmN);
     UP(WmNT, WmNT);
 
+    clk.mark("eigenpairs of S-");
     // ------------------------------- coarse matrix E_c = W^T (E - K^+) W
     if (dP > 0) {
         const int nnz = d.nnz;
@@ -1535,6 +1561,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
             }
         }
     }
+    clk.mark("coarse matrix and low-precision operands");
     // ---------------------------------------- split FP64 GEMM operands
     {
         const bool split = o.dgemm == RTE_DGEMM_SPLIT ||
@@ -1560,15 +1587,31 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         }
     }
 #undef UP
-    rc = setup_multigrid(h, hs);
+    clk.mark("split FP64 operands");
+    rc = setup_multigrid(h, hs, &clk);
     if (rc) return bail(rc);
+    clk.mark("E_c multigrid");
     rc = alloc_workspace(h, o.max_rhs);
     if (rc) return bail(rc);
+    clk.mark("workspace");
     rc = tune_launches(h);
     if (rc) return bail(rc);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess)
         return bail(fail(RTE_ERR_CUDA, "setup synchronisation failed"));
+    clk.mark("launch tuning");
     *out = h;
+    return RTE_OK;
+}
+
+int rte_setup_times(const rte_handle* h, const char** names, double* ms, int cap,
+                    int* count) {
+    if (!h || !count || cap < 0) return fail(RTE_ERR_ARG, "bad argument");
+    const int n = (int)h->setup_ms.size();
+    *count = n;
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (names) names[i] = h->setup_names[i].c_str();
+        if (ms) ms[i] = h->setup_ms[i];
+    }
     return RTE_OK;
 }
 
