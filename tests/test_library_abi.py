@@ -113,3 +113,48 @@ def test_default_options_through_the_library(lib_path):
     assert o.autotune == 1 and o.max_rhs >= 1
     o = rte.default_options(p1_route=rte.P1_PCG, precision=rte.MIXED_BF16)
     assert (o.p1_route, o.precision) == (rte.P1_PCG, rte.MIXED_BF16)
+
+
+def _setup_rc(problem_kw=None, **opts):
+    """rte_setup on arguments it must refuse on the host, before any CUDA
+    call (so this runs without a GPU): (return code, error message)."""
+    import ctypes
+    import numpy as np
+    import paper_2102_09038_gb300 as rte
+    import workloads
+    lib = rte.load()
+    kw = dict(m=2, levels=1, g=0.5, sigma_t=1.0, sigma_s=0.5)
+    kw.update(problem_kw or {})
+    p = workloads.constant(kw['m'], kw['levels'], kw['g'], kw['sigma_t'], kw['sigma_s'])
+    pr, keep = rte._problem_struct(p)
+    if 'mesh_m' in kw:
+        pr.mesh_m = kw['mesh_m']
+    if 'sphere_levels' in kw:
+        pr.sphere_levels = kw['sphere_levels']
+    o = rte.default_options(**opts)
+    h = ctypes.c_void_p()
+    rc = lib.rte_setup(ctypes.byref(pr), ctypes.byref(o), None, ctypes.byref(h))
+    assert not h.value
+    return rc, lib.rte_last_error().decode()
+
+
+@pytest.mark.parametrize('problem_kw, opts, words', [
+    (dict(mesh_m=0), {}, 'mesh_m'),
+    (dict(sphere_levels=6), {}, 'sphere_levels'),
+    (dict(g=1.0), {}, 'g must'),
+    (dict(sigma_s=1.0), {}, 'sigma_s < sigma_t'),
+    (dict(sigma_t=-1.0, sigma_s=0.0), {}, 'sigma_s < sigma_t'),
+    ({}, dict(l=0), 'invalid options'),
+    ({}, dict(n_minus=4), 'invalid options'),
+    ({}, dict(n_plus=3), 'invalid options'),
+    ({}, dict(max_rhs=0), 'invalid options'),
+    ({}, dict(precision=7), 'precision'),
+    ({}, dict(p1_route=5), 'P_1 route'),
+    ({}, dict(precision=2, mk_route=1), 'eigenbasis'),
+    (dict(levels=0), dict(n_plus=4), 'too large'),   # d^+ = 15 > 4 directions
+])
+def test_setup_refuses_bad_arguments_on_the_host(lib_path, problem_kw, opts, words):
+    import paper_2102_09038_gb300 as rte
+    rc, msg = _setup_rc(problem_kw, **opts)
+    assert rte.ERRORS[rc] == 'RTE_ERR_ARG'
+    assert words in msg, msg
