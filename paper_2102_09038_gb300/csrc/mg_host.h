@@ -27,8 +27,9 @@ struct MGHost {
 
 Stencil stencil_of_square(int m);
 
-// Builds levels m, m/2, ... from the fine pattern and values until the mesh
-// no longer halves or has at most 25 nodes.
+// Builds levels m, floor(m/2), ... from the fine pattern and values while
+// the level has m >= 4 and more than max_coarse_nodes nodes; the coarsest is
+// marked for a dense inverse when it has at most max_coarse_nodes nodes.
 int build_hierarchy(int m, const Stencil& fine, const std::vector<double>& vals0, int slots,
                     int bs, int max_coarse_nodes, MGHost& out);
 
