@@ -158,3 +158,23 @@ def test_setup_refuses_bad_arguments_on_the_host(lib_path, problem_kw, opts, wor
     rc, msg = _setup_rc(problem_kw, **opts)
     assert rte.ERRORS[rc] == 'RTE_ERR_ARG'
     assert words in msg, msg
+
+
+def test_memory_estimate_grows_with_the_problem(lib_path):
+    # rte_estimate_bytes (host only) drives the server's HBM admission: it
+    # grows with the right-hand sides and the mesh, and counts the two extra
+    # vectors of the PCG realisation of P_1
+    import paper_2102_09038_gb300 as rte
+    import workloads
+    small = workloads.constant(16, 2, 0.5, 1.0, 0.5)
+    big = workloads.constant(32, 2, 0.5, 1.0, 0.5)
+    e = lambda p, n=1, **o: rte.estimate_bytes(p, nrhs=n, **o)
+    assert 0 < e(small) < e(big)
+    assert e(small, 1) < e(small, 4)
+    ne = (16 + 1) ** 2 * 64 * 8      # one FP64 even vector
+    rich = e(small, precision=rte.MIXED_BF16, p1_route=rte.P1_RICHARDSON)
+    pcg = e(small, precision=rte.MIXED_BF16, p1_route=rte.P1_PCG)
+    assert pcg - rich == 2 * ne
+    assert e(small, precision=rte.MIXED_BF16) == pcg          # the mixed default
+    assert e(small, precision=rte.FP64) == e(small, precision=rte.FP64,
+                                             p1_route=rte.P1_RICHARDSON)
