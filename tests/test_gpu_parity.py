@@ -338,3 +338,17 @@ def test_contraction_rates_match_dense_iteration_matrix():
     assert abs(eta - eta_ref) <= 2e-3 * eta_ref, (eta, eta_ref)
     # the paper's bound eta <= c (Section 5.3) holds for the computed operators
     assert eta <= 0.9 + 1e-9
+
+
+def test_setup_stage_times():
+    # rte_setup_times: every stage of the setup recorded, wall-clock, in order
+    import paper_2102_09038_gb300 as rte
+    s = rte.Solver(CASES['ragged'](), n_plus=2, n_minus=3)
+    try:
+        t = s.setup_times()
+    finally:
+        s.close()
+    assert list(t)[0] == 'host assembly' and list(t)[-1] == 'launch tuning'
+    for name in ('eigenpairs of S+', 'eigenpairs of S-', 'E_0 multigrid', 'E_c multigrid'):
+        assert name in t
+    assert all(v >= 0.0 for v in t.values())
