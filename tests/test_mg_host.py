@@ -80,6 +80,9 @@ int main(int argc, char** argv) {
         }
         std::vector<double> ell;
         std::printf("ell %zu %d\n", l, to_ell(L, slots, bs, ell));
+        std::vector<float> dinv;
+        if (block_diag_inverse(L, bs, dinv) == 0)
+            for (size_t k = 0; k < dinv.size(); ++k) std::printf("I %zu %zu %.9g\n", l, k, (double)dinv[k]);
     }
     std::vector<double> wts(slots);
     for (int s = 0; s < slots; ++s) wts[s] = 1.0 + s;
@@ -108,7 +111,7 @@ def driver(tmp_path_factory):
 def run(exe, m, slots, bs, maxc):
     out = subprocess.run([exe, str(m), str(slots), str(bs), str(maxc)], capture_output=True,
                          text=True, check=True).stdout.splitlines()
-    info = dict(levels=[], A={}, P={}, R={}, ell={}, D=[])
+    info = dict(levels=[], A={}, P={}, R={}, ell={}, D=[], I={})
     for ln in out:
         t = ln.split()
         if t[0] == 'levels':
@@ -124,6 +127,8 @@ def run(exe, m, slots, bs, maxc):
             info['ell'][int(t[1])] = int(t[2])
         elif t[0] == 'D':
             info['D'].append(float(t[2]))
+        elif t[0] == 'I':
+            info['I'].setdefault(int(t[1]), []).append(float(t[3]))
     return info
 
 
@@ -174,6 +179,13 @@ def test_hierarchy_is_galerkin(driver, m, slots, bs, maxc):
             assert np.abs(Ac[s] - G).max() <= 1e-12 * np.abs(G).max()
             assert np.abs(Ac[s] - Ac[s].T).max() <= 1e-12 * np.abs(Ac[s]).max()
     assert all(v == 0 for v in info['ell'].values())     # 7-point pattern on every level
+    # inverses of the diagonal blocks of slot 0 (the block-Jacobi smoother), FP32
+    for l, (ml, nl) in enumerate(levels):
+        A0 = dense(info['A'][l], nl, slots, bs)[0]
+        Dv = np.array(info['I'][l]).reshape(nl, bs, bs)
+        for i in range(nl):
+            blk = A0[i * bs:(i + 1) * bs, i * bs:(i + 1) * bs]
+            assert np.abs(Dv[i] @ blk - np.eye(bs)).max() < 1e-5
     Al = dense(info['A'][len(levels) - 1], nlast, slots, bs)
     D = np.array(info['D']).reshape(nlast * bs, nlast * bs)
     Ws = sum((1.0 + s) * Al[s] for s in range(slots))
