@@ -186,7 +186,13 @@ def angular_matrices(levels, g, r_far=R_FAR, r_near=R_NEAR):
     Sp = 0.5 * (Sp + Sp.T)
     Sm = 0.5 * (Sm + Sm.T)
     return dict(reps=reps, Vinv=Vinv, m=m, MSm=MSm, A1=A1, A2=A2,
-                omx=omx, omy=omy, Splus=Sp, Sminus=Sm)
+                omx=omx, omy=omy, Splus=Sp, Sminus=Sm, qpts=pn, qw=wn)
+
+
+# Faces of the unit square in the order the inflow data uses: (axis of the
+# normal, coordinate of the face, sign of the outward normal along the axis):
+# x = 0, x = 1, y = 0, y = 1.
+FACES = ((0, 0.0, -1.0), (0, 1.0, 1.0), (1, 0.0, -1.0), (1, 1.0, 1.0))
 
 
 def block_diag3(blocks):
@@ -227,6 +233,45 @@ class Discretisation:
         self.MSm = block_diag3(self.an['MSm'])
         # c = ||sigma_s / sigma_t||_inf (Section 2.2)
         self.c = float(np.max(self.sigma_s / self.sigma_t))
+
+    def face_nodes(self, f):
+        """Node indices along boundary face f (order of FACES), in increasing
+        coordinate along the face."""
+        m = self.m
+        idx = np.arange(self.nRp).reshape(m + 1, m + 1)   # [iy, ix]
+        axis, coord, _ = FACES[f]
+        c = 0 if coord == 0.0 else m
+        return idx[:, c] if axis == 0 else idx[c, :]
+
+    def inflow(self, g):
+        """The inflow part of l^+ (Section 2.4, l^+(w^+) = (q, w^+) +
+        2 (|s.n| g, w^+)_{dD_-}) for the test functions w^+ = phi_i mu_k:
+        2 sum_faces int_face phi_i int_{K_k u -K_k, s.n < 0} |s.n| g ds dr,
+        where dD_- = {(s, r): r on the boundary, s.n(r) < 0}.
+
+        g(f, j, s): the inflow on face f at the face's node j (the data is P1
+        along each face, so the space integral is the face's P1 mass) for the
+        directions s (P x 3); returns P values.  The sphere integral runs over
+        the quadrature points of both triangles of every pair (those of -K_k
+        are the mirrored points of K_k) and keeps the points with s.n < 0."""
+        m = self.m
+        h = 1.0 / m
+        pts, w = self.an['qpts'], self.an['qw']
+        B = np.zeros((m + 1, m + 1))
+        for e in range(m):
+            B[e:e + 2, e:e + 2] += h / 6.0 * np.array([[2.0, 1.0], [1.0, 2.0]])
+        out = np.zeros((self.nRp, self.nSp))
+        for f, (axis, _, nsign) in enumerate(FACES):
+            G = np.zeros((m + 1, self.nSp))
+            for sgn in (1.0, -1.0):
+                P = sgn * pts
+                sn = nsign * P[:, :, axis]
+                keep = sn < 0.0
+                for j in range(m + 1):
+                    vals = np.asarray(g(f, j, P.reshape(-1, 3))).reshape(P.shape[:2])
+                    G[j] += np.sum(w * np.abs(sn) * keep * vals, axis=1)
+            out[self.face_nodes(f)] += 2.0 * B @ G
+        return out
 
     def source(self, q_nodal):
         """l^+ for an isotropic source given by nodal values and vacuum
