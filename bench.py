@@ -55,11 +55,17 @@ def parse():
                     help='skip the plain-FP64 comparison solve')
     ap.add_argument('--no-serving', action='store_true',
                     help='skip the serving (continuous batching) measurement')
-    ap.add_argument('--serve-requests', type=int, default=48)
+    ap.add_argument('--serve-requests', type=int, default=64)
     ap.add_argument('--serve-sweep', action='store_true',
                     help='also sweep the arrival rate of the serving stream (minutes)')
     ap.add_argument('--batch', action='store_true',
                     help='also time the 64 uneven instances of the batching workload')
+    ap.add_argument('--mk-routes', action='store_true',
+                    help='time the eigenbasis and the PCG (Algorithm 1) routes of '
+                         '(M^- - K^-)^{-1} on the 128x128 and 96x96 workloads and exit')
+    ap.add_argument('--rates', action='store_true',
+                    help='print the contraction rates rho and eta of the iteration matrix '
+                         'over g, d_N and l (the paper\'s Section 6.2 study) and exit')
     return ap.parse_args()
 
 
@@ -172,37 +178,48 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# kernel group as last captured with ncu on the default workload (the summary
-# and command are in profiles/); a kernel changed since its capture has no
-# entry.  k_e0_pcg_f: mean of two captured launches (the 9th and 10th of the
-# solve).
-PROFILED_DRAM_BYTES = {'e0_cg_lo': 2.81e9}
+# DRAM traffic of a kernel group from an ncu capture (the summary and the
+# command are in profiles/): dram__bytes_read.sum + dram__bytes_write.sum per
+# work unit of the captured launch (unit as in kernel_work's docstring), the
+# source file the kernel lives in and that file's SHA-256 prefix at the
+# capture.  The bench scales it to its own launch by the units processed, and
+# reports null once the source has changed since the capture.
+PROFILED_DRAM = {}
+
+
+def source_sha(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), 'rb') as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def e0_units(d, nrhs, info):
+    """Work units of one E_0^{-1} launch: (node, column) items times the
+    launch's CG iterations, each weighted by the fraction of direction quads
+    still active (the mixed-mode kernel visits only those)."""
+    n = info.get('e0_launches', 0)
+    per = info['e0_active_vcycles'] / n if n else max(info.get('e0_iters', 1), 1)
+    return d['nRp'] * nrhs * d['nSp'] * per, per
 
 
 def kernel_work(name, d, nrhs, info):
-    """Algorithmic work of one launch of a named kernel group: (amount, unit,
-    bound).  Contractions count 2 M N K flops.  Memory-bound kernels count
-    the bytes they must move once per launch:
-      * transport A: read U^+ (FP64), write Z (FP64);
+    """Algorithmic work of one launch of a named kernel group, as the
+    per-unit counts of the measurement plan (work per outer iteration of the
+    method: flops of the dense contractions, bytes each memory-bound step
+    must move at least once): (amount, unit, bound).
+      * contractions: 2 M N K flops;
+      * transport A: read U^+, write Z (w = 8 B);
       * A^T + M^+ + R - K^+ gather: read Z, U^+ and U S^+, write Y;
-      * E_0 PCG (persistent): per CG iteration the coarsest level's dense
-        per-direction inverses (read once per V-cycle) and, per (node, column), the level-0
-        CG vector traffic (P read and AP written by the apply; P, R, AP read,
-        R and V-cycle input written by the update; R, z read for r.z and
-        r.r; z, P read and P written by the direction update: 12 words of
-        the CG precision, plus the iterate read and written: 16 B in FP64,
-        8 B in the FP32 kernel, which writes FP64 X once at the end) and the
-        V-cycle's 17 FP32 array
-        passes per level (4^-l of the level-0 size), times the V-cycles of
-        the launch (the mean over the solve's launches), each weighted by the
-        fraction of direction quads with a column not yet converged: the
-        mixed-mode kernel visits only those.  The FP32 kernel forms the stencil coefficients on chip
-        (224 B per node per pass, not counted); the FP64 kernel also reads 7
-        FP64 coefficients per item;
-      * E_c PCG: per iteration the FP64 level-0 blocks (7 d^2 per node) and
-        ~12 FP64 vector passes, plus the FP32 V-cycle (7 d^2 + 18 d words
-        per node per sweep-equivalent, 4/3 for the coarser levels)."""
+      * E_0 PCG: per CG iteration over all (node, column) items the four CG
+        streams x, r, p, Ap read and written once, w 6 N^+ s bytes (w = 4 in
+        the FP32 kernel, 8 in FP64), plus the stencil at its minimal size
+        (six spatial parts of 7 coefficients per node, the per-direction
+        weights being negligible), times the launch's CG iterations (the
+        V-cycles, each weighted by the fraction of active direction quads),
+        plus the FP64 right-hand side read and solution written once;
+      * E_c PCG: per CG iteration w (5 d N^+) of vectors plus the E_c stencil
+        as the CG's own apply reads it (7 d^2 N^+), w = 8, times the CG
+        iterations."""
     nRp, nRm, nS, nSm = d['nRp'], d['nRm'], d['nSp'], d['nSm']
     if name in ('gemm_mk_eig1', 'gemm_mk_eig2'):
         return 2.0 * nrhs * nRm * nSm * nSm, 'flop', 'fp64'
@@ -215,25 +232,49 @@ def kernel_work(name, d, nrhs, info):
     if name == 'apply_even':
         return 8.0 * nrhs * (nRm * nSm + 3 * nRp * nS), 'byte', 'hbm'
     if name in ('e0_cg', 'e0_cg_lo'):
-        ts = 8 if name == 'e0_cg' else 4
-        cols = nrhs * nS
-        cg = nRp * cols * (12 * ts + 2 * ts + (7 * 8 if name == 'e0_cg' else 0))
-        vc = sum(nRp / 4 ** l * cols * 4 * 17 for l in range(d['e0_levels']))
-        # the coarsest level's dense per-direction inverses, read once per V-cycle
-        mc = d['mesh'] >> (d['e0_levels'] - 1)
-        vc += ((mc + 1) ** 2) ** 2 * nS * 4
-        # V-cycles per launch, each weighted by the fraction of direction
-        # quads still active (converged columns are not visited again)
-        n = info.get('e0_launches', 0)
-        per = info['e0_active_vcycles'] / n if n else max(info.get('e0_iters', 1), 1)
-        once = nRp * cols * 16   # B read and X written in FP64, once per launch
-        return (cg + vc) * per + once, 'byte', 'hbm'
+        w = 8 if name == 'e0_cg' else 4
+        _, per = e0_units(d, nrhs, info)
+        it = w * 6 * nRp * nrhs * nS + 6 * 7 * nRp * w
+        return it * per + 16.0 * nRp * nrhs * nS, 'byte', 'hbm'
     if name == 'coarse_cg':
         dp = d['dP']
-        cg = nRp * nrhs * (7 * dp * dp + 12 * dp) * 8
-        vc = nRp * nrhs * (7 * dp * dp + 18 * dp) * 4 * 6 * 4 / 3
-        return (cg + vc) * max(info.get('coarse_iters', 1), 1), 'byte', 'hbm'
+        it = 8 * (5 * dp * nRp * nrhs + 7 * dp * dp * nRp)
+        return it * max(info.get('coarse_iters', 1), 1), 'byte', 'hbm'
+    if name in ('e0_direct', 'e0_direct64'):
+        w = 8 if name == 'e0_direct64' else 4
+        b = d['mesh'] + 1
+        return 2.0 * nS * b * b * b * w + 16.0 * nRp * nrhs * nS, 'byte', 'hbm'
     return None
+
+
+def kernel_impl_bytes(name, d, nrhs, info):
+    """The bytes the E_0 kernels move by their own design, per launch (kept
+    beside the algorithmic count): per V-cycle and active (node, column) the
+    12 CG-vector passes of the precision w and the iterate read and written,
+    the V-cycle's 17 FP32 array passes per level (4^-l of the level-0 size)
+    and the coarsest level's dense per-direction inverses, plus the FP64
+    right-hand side and solution once."""
+    nRp, nS = d['nRp'], d['nSp']
+    if name in ('e0_direct', 'e0_direct64'):
+        # the factor rows padded to ld (a multiple of 4), read twice per
+        # sweep of up to 4 right-hand sides; B read, the forward result
+        # written, read and overwritten; four coupling coefficients per item
+        w = 8 if name == 'e0_direct64' else 4
+        b = d['mesh'] + 1
+        ld = (b + 3) // 4 * 4
+        sweeps = (nrhs + 3) // 4
+        return (2.0 * nS * b * ld * ld * w * sweeps + 32.0 * nRp * nrhs * nS
+                + 4 * 8.0 * nRp * nS * sweeps)
+    if name not in ('e0_cg', 'e0_cg_lo'):
+        return None
+    w = 8 if name == 'e0_cg' else 4
+    cols = nrhs * nS
+    cg = nRp * cols * (12 * w + 2 * w + (7 * 8 if name == 'e0_cg' else 0))
+    vc = sum(nRp / 4 ** l * cols * 4 * 17 for l in range(d['e0_levels']))
+    mc = d['mesh'] >> (d['e0_levels'] - 1)
+    vc += ((mc + 1) ** 2) ** 2 * nS * 4
+    _, per = e0_units(d, nrhs, info)
+    return (cg + vc) * per + nRp * cols * 16
 
 
 def levels_of(m, max_nodes=300):
@@ -318,8 +359,16 @@ def run_ours(args):
     d['dP'] = solver.d_plus
     work = kernel_work(top[0], d, p.nrhs, last_info)
     avg_ms = top[1][0] / max(top[1][1], 1)
+    traffic, traffic_note = None, 'no ncu capture of the current kernel source'
+    prof = PROFILED_DRAM.get(top[0])
+    if prof and top[0] in ('e0_cg', 'e0_cg_lo'):
+        if source_sha(prof['source']) == prof['sha']:
+            traffic = prof['bytes_per_unit'] * e0_units(d, p.nrhs, last_info)[0]
+            traffic_note = prof['note']
+        else:
+            traffic_note = 'kernel changed since its ncu capture'
     roof = dict(kernel=top[0], bound=None, achieved=None, peak=None, unit=None,
-                frac=None, traffic=PROFILED_DRAM_BYTES.get(top[0]), launches=top[1][1],
+                frac=None, traffic=traffic, traffic_source=traffic_note, launches=top[1][1],
                 avg_ms=avg_ms)
     if work is not None:
         amount, unit, bound = work
@@ -338,6 +387,10 @@ def run_ours(args):
             roof.update(bound=bound, achieved=ach, peak=peaks['hbm_gbs'], unit='GB/s',
                         frac=ach / peaks['hbm_gbs'], peak_source=src,
                         algorithmic_bytes=amount)
+            impl = kernel_impl_bytes(top[0], d, p.nrhs, last_info)
+            if impl is not None:
+                roof.update(impl_bytes=impl,
+                            impl_frac=impl / (avg_ms / 1e3) / 1e9 / peaks['hbm_gbs'])
     share = {k: round(v[0] / sum(x[0] for x in tim.values()), 4)
              for k, v in tim.items()}
 
@@ -368,25 +421,9 @@ def run_ours(args):
                d2h_bytes_per_step=uh.numel() * 8,
                time_to_tol_s=e2e_secs / args.steps)
 
-    fp64 = None
+    arms = None
     if not args.no_fp64_compare and args.precision != 'fp64':
-        s64 = rte.Solver(p, precision=rte.FP64)
-        q64 = s64.rhs(qn)
-        u64 = s64.even(p.nrhs)
-        _, i64 = s64.solve(q64, u=u64, tol=p.tol)    # warm-up
-        u64.zero_()
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(True), torch.cuda.Event(True)
-        f0.record(s64.stream)
-        _, i64 = s64.solve(q64, u=u64, tol=p.tol)
-        f1.record(s64.stream)
-        torch.cuda.synchronize()
-        t64 = f0.elapsed_time(f1) / 1e3
-        fp64 = dict(precision='fp64 (SIMT FP64 GEMMs, inner solves to 1e-12)',
-                    time_to_tol_s=t64, iterations=i64['iterations'],
-                    value=dofs * i64['iterations'] / t64, unit='DOF*iter/s',
-                    mixed_speedup_time_to_tol=t64 / (secs / args.steps))
-        s64.close()
+        arms = precision_arms(rte, torch, p, qn, secs / args.steps, iters / args.steps, u, dofs)
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = serving_bench(args, torch, rte)
@@ -419,7 +456,9 @@ def run_ours(args):
                                parallelism='replicas' if world > 1 else 'single'),
                    e2e=e2e, gpu_launches=launches, roofline=roof,
                    kernel_share=share, clocks=clk.summary(), cpu_baseline=cpu,
-                   fp64_compare=fp64, serving=serving, setup_ms=setup_ms)
+                   serving=serving, setup_ms=setup_ms)
+        if arms is not None:
+            out.update(arms)
         if batch is not None:
             out['batch'] = batch
         print(json.dumps(out))
@@ -427,54 +466,113 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# The FP64 arm with the mixed arm's algorithm: P_1 as PCG steps, inner
+# tolerances 0.3 (E_0) and 0.1 (E_c), and the FP64 dense contractions on the
+# split (FP64-accurate) tensor-core GEMM; only the arithmetic of the inner
+# steps differs from the mixed modes.
+FP64_MATCHED = dict(precision=0, dgemm=2, p1_route=1, e0_tol=0.3, coarse_tol=0.1)
+
+
+def timed_solve(solver, q, tol, warm=True):
+    """(seconds, info, u) of one solve from u = 0, device-timed with CUDA
+    events on the solver's stream (after one untimed solve when warm)."""
+    import torch
+    u = solver.even(q.shape[0])
+    if warm:
+        solver.solve(q, u=u, tol=tol)
+        u.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record(solver.stream)
+    _, info = solver.solve(q, u=u, tol=tol)
+    e1.record(solver.stream)
+    torch.cuda.synchronize()
+    if info['status'] != 0:
+        raise RuntimeError('solve failed: %s' % info)
+    return e0.elapsed_time(e1) / 1e3, info, u
+
+
+def precision_arms(rte, torch, p, qn, t_mixed, it_mixed, u_mixed, dofs):
+    """The other precisions on the same workload and tolerance, each a full
+    solve timed like the headline: FP32 mixed; FP64 with the mixed arm's
+    algorithm (so that the ratio to it is the speed-up from precision
+    alone); FP64 as the paper states the method (P_1^l, inner solves to
+    1e-12, FP64 GEMMs on the FP64 units; the ratio of the two FP64 arms is
+    the speed-up from the algorithm's inner tolerances and P_1 route).  The
+    error of each solution against an FP64 reference solved to 1e-11 (the
+    matched FP64 arm) is reported beside it."""
+    ref = rte.Solver(p, **FP64_MATCHED)
+    qr = ref.rhs(qn)
+    _, iref, uref = timed_solve(ref, qr, 1e-11, warm=False)
+    ref.close()
+    uref = uref.cpu().numpy()
+    import numpy as np
+
+    def err(u):
+        return float(np.linalg.norm(u.cpu().numpy() - uref) / np.linalg.norm(uref))
+
+    out = dict(error_vs_fp64=dict(
+        reference='FP64 solve (matched algorithm) to relative residual 1e-11',
+        reference_residual=iref['rel_residual'], reference_iterations=iref['iterations'],
+        tol=p.tol, mixed_bf16=err(u_mixed)))
+    arms = {}
+    for name, opts in (('mixed_fp32', dict(precision=rte.MIXED_FP32)),
+                       ('fp64_matched', FP64_MATCHED),
+                       ('fp64_paper', dict(precision=rte.FP64))):
+        s = rte.Solver(p, **opts)
+        q = s.rhs(qn)
+        t, info, u = timed_solve(s, q, p.tol, warm=name != 'fp64_paper')
+        out['error_vs_fp64'][name] = err(u)
+        arms[name] = dict(time_to_tol_s=t, iterations=info['iterations'],
+                          value=dofs * info['iterations'] / t, unit='DOF*iter/s')
+        s.close()
+    arms['fp64_matched']['note'] = ('P_1 as l PCG steps, inner tolerances 0.3 / 0.1, split '
+                                    'FP64 tensor-core GEMMs: the mixed arm\'s algorithm in FP64')
+    arms['fp64_paper']['note'] = ('P_1^l, inner solves to 1e-12, FP64 GEMMs on the FP64 '
+                                  'units: the method as the paper states it')
+    out['precision_arms'] = arms
+    out['speedup'] = dict(
+        precision=arms['fp64_matched']['time_to_tol_s'] / t_mixed,
+        algorithm=arms['fp64_paper']['time_to_tol_s'] / arms['fp64_matched']['time_to_tol_s'],
+        total_vs_fp64_paper=arms['fp64_paper']['time_to_tol_s'] / t_mixed,
+        fp32_vs_bf16=arms['mixed_fp32']['time_to_tol_s'] / t_mixed,
+        note='ratios of time to tolerance; precision = FP64 (matched) / mixed BF16')
+    return out
+
+
 def serving_requests(n, seed=0):
     """A seeded stream of solve requests mixing the sizes and parameters of
-    the other workloads (plain 32x32/128-triangle problems, uneven instances
-    with 32..64 meshes, 128 or 512 triangles, g in [0.3, 0.9], log-uniform
-    sigma_t, sigma_s/sigma_t in [0.5, 0.999], 1..4 Gaussian sources)."""
+    the other workloads: the plain 32x32 / 128-triangle problem (g = 0.5);
+    the 128x128 / 512-triangle checkerboard (g = 0.9, c = 0.99) with a
+    seeded Gaussian source per request; the 96x96 / 2048-triangle
+    precision case (g = 0.8 or 0.95, c = 0.999); and uneven instances of
+    the batching workload (meshes 32..128, 128 or 512 triangles, g in
+    [0.3, 0.9], log-uniform sigma_t, sigma_s / sigma_t in [0.5, 0.999], 1..8
+    Gaussian sources)."""
     import numpy as np
     import workloads
     rng = np.random.default_rng(seed)
     out = []
-    for i in range(n):
-        kind = rng.integers(0, 3)
+    for kind in rng.choice(4, size=n, p=[0.4, 0.2, 0.1, 0.3]):
         if kind == 0:
             p = workloads.plain_fp64()
+        elif kind == 1:
+            p = workloads.checkerboard(m=128, levels=3, g=0.9, ratio=0.99,
+                                       seed=int(rng.integers(1 << 30)))
+        elif kind == 2:
+            p = workloads.precision_case(g=float(rng.choice([0.8, 0.95])))
         else:
-            p = workloads.batch_instances(1, seed=int(rng.integers(1 << 30)),
-                                          m_range=(32, 64), levels=(2, 3),
-                                          nrhs_range=(1, 4))[0]
+            p = workloads.batch_instances(1, seed=int(rng.integers(1 << 30)))[0]
         out.append(p)
     return out
 
 
-def serving_bench(args, torch, rte):
-    """Continuous batching: requests arrive as a Poisson stream (rate set to
-    ~1.5x the measured sequential throughput, so the server must overlap
-    them), are admitted by an HBM budget into worker slots, and their
-    latencies (submission to completion) give p50/p99.  The same requests
-    solved one after another in plain FP64 give the sequential baseline."""
+def run_stream(rte, reqs, rate, budget, slots, opts, seed):
+    """Poisson arrivals at `rate` per second into a fresh server: (latencies,
+    iterations, wall seconds, cache hits, misses)."""
     import numpy as np
-    reqs = serving_requests(args.serve_requests, seed=1)
-    free, total = torch.cuda.mem_get_info()
-    budget = int(free * 0.6)
-    opts = dict(precision=rte.MIXED_BF16)
-    # sequential FP64 reference on a sample
-    sample = reqs[:6]
-    t0 = time.perf_counter()
-    for p in sample:
-        s = rte.Solver(p, max_rhs=p.nrhs)
-        q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
-        s.solve(q, tol=1e-6)
-        torch.cuda.synchronize()
-        s.close()
-    seq_rate = len(sample) / (time.perf_counter() - t0)
-    sv = rte.Server(budget, slots=8, **opts)
-    # warm-up request
-    sv.wait(sv.submit(reqs[0], reqs[0].q_nodal, tol=1e-6))
-    rng = np.random.default_rng(2)
-    rate = 1.5 * seq_rate
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    sv = rte.Server(budget, slots=slots, **opts)
+    arrivals = np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, len(reqs)))
     t0 = time.perf_counter()
     ids = []
     for p, ta in zip(reqs, arrivals):
@@ -488,13 +586,48 @@ def serving_bench(args, torch, rte):
         lat.append(info['latency'])
         iters.append(info['iterations'])
     wall = time.perf_counter() - t0
+    hits, misses, _ = sv.cache_stats()
     sv.close()
-    lat = np.array(lat)
-    return dict(requests=len(reqs), arrival_rate_per_s=rate, hbm_budget_bytes=budget, slots=8,
+    return np.array(lat), iters, wall, hits, misses
+
+
+def serving_bench(args, torch, rte):
+    """Continuous batching: requests arrive as a Poisson stream, are admitted
+    by an HBM budget into 8 worker slots (each request's set-up is skipped
+    when the server holds an idle handle of its operator), and their
+    latencies (submission to completion) give p50/p99.  Baseline: the
+    same requests one after another in plain FP64 (the paper's method, no
+    server, no cache), on a sample bounded to about 30 s."""
+    import numpy as np
+    reqs = serving_requests(args.serve_requests, seed=1)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.6)
+    opts = dict(precision=rte.MIXED_BF16)
+    n_seq, t_seq = 0, 0.0
+    t0 = time.perf_counter()
+    for p in reqs:
+        s = rte.Solver(p, max_rhs=p.nrhs)
+        q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
+        s.solve(q, tol=1e-6)
+        torch.cuda.synchronize()
+        s.close()
+        n_seq += 1
+        t_seq = time.perf_counter() - t0
+        if t_seq > 30.0:
+            break
+    seq_rate = n_seq / t_seq
+    # warm-up of the server path (first-use initialisation of the libraries)
+    run_stream(rte, reqs[:2], 100.0, budget, 8, opts, 0)
+    rate = 1.5 * seq_rate
+    lat, iters, wall, hits, misses = run_stream(rte, reqs, rate, budget, 8, opts, 2)
+    kinds = ['instance' if p.name.startswith('inst') else p.name.split('_')[0] for p in reqs]
+    return dict(requests=len(reqs), mix={k: kinds.count(k) for k in sorted(set(kinds))},
+                arrival_rate_per_s=rate, hbm_budget_bytes=budget, slots=8,
                 precision='mixed_bf16', p50_latency_s=float(np.percentile(lat, 50)),
                 p99_latency_s=float(np.percentile(lat, 99)), solves_per_s=len(reqs) / wall,
-                sequential_fp64_solves_per_s=seq_rate,
-                sequential_fp64_sample=len(sample), mean_iterations=float(np.mean(iters)))
+                operator_cache=dict(hits=hits, misses=misses),
+                sequential_fp64_solves_per_s=seq_rate, sequential_fp64_sample=n_seq,
+                mean_iterations=float(np.mean(iters)))
 
 
 def serving_sweep(args, torch, rte, seq_rate):
@@ -506,24 +639,12 @@ def serving_sweep(args, torch, rte, seq_rate):
     free, _ = torch.cuda.mem_get_info()
     out = []
     for mult in (0.5, 1.0, 2.0, 4.0, 8.0):
-        sv = rte.Server(int(free * 0.6), slots=8, precision=rte.MIXED_BF16)
-        sv.wait(sv.submit(reqs[0], reqs[0].q_nodal, tol=1e-6))
-        rate = mult * seq_rate
-        arrivals = np.cumsum(np.random.default_rng(4).exponential(1.0 / rate, len(reqs)))
-        t0 = time.perf_counter()
-        ids = []
-        for p, ta in zip(reqs, arrivals):
-            delay = ta - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            ids.append(sv.submit(p, p.q_nodal, tol=1e-6))
-        lat = np.array([sv.wait(rid)[1]['latency'] for rid in ids])
-        wall = time.perf_counter() - t0
-        sv.close()
-        out.append(dict(rate_per_s=rate, rate_over_sequential_fp64=mult,
+        lat, _, wall, hits, misses = run_stream(rte, reqs, mult * seq_rate, int(free * 0.6), 8,
+                                                dict(precision=rte.MIXED_BF16), 4)
+        out.append(dict(rate_per_s=mult * seq_rate, rate_over_sequential_fp64=mult,
                         p50_latency_s=float(np.percentile(lat, 50)),
                         p99_latency_s=float(np.percentile(lat, 99)),
-                        solves_per_s=len(reqs) / wall))
+                        solves_per_s=len(reqs) / wall, cache_hits=hits))
     return out
 
 
@@ -618,8 +739,75 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def mk_routes_study(args):
+    """Time to 1e-6 with each route of (M^- - K^-)^{-1}: the full
+    eigenbasis (two dense contractions per apply, the default) and the
+    paper's Algorithm 1 (PCG with the Lemma's preconditioner to 1e-12, run
+    as a device-side graph loop), in the matched FP64 arm (split
+    tensor-core GEMMs) and in mixed BF16 (where the PCG route applies to the
+    FP64 residual), on the 128 x 128 / 512-triangle checkerboard and the
+    96 x 96 / 2048-triangle precision case at g = 0.8."""
+    import torch
+    import workloads
+    import paper_2102_09038_gb300 as rte
+    torch.cuda.set_device(0)
+    cases = [('checkerboard_128x128_T512', workloads.checkerboard(m=128, levels=3, g=0.9,
+                                                                  ratio=0.99, seed=0)),
+             ('precision_96x96_T2048_g0.80', workloads.precision_case(g=0.8))]
+    out = []
+    for name, p in cases:
+        qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
+        for arm, opts in (('fp64_matched', FP64_MATCHED), ('mixed_bf16', dict(precision=2))):
+            for route in (rte.MK_EIGEN, rte.MK_PCG):
+                s = rte.Solver(p, mk_route=route, **opts)
+                t, info, _ = timed_solve(s, s.rhs(qn), p.tol)
+                s.close()
+                row = dict(case=name, arm=arm, route=('eigenbasis', 'pcg')[route],
+                           time_to_tol_s=t, iterations=info['iterations'],
+                           mk_iters_last=info['mk_iters'])
+                out.append(row)
+                print(json.dumps(row), flush=True)
+    return out
+
+
+def rates_study(args):
+    """rho (spectral radius) and eta (energy norm) of Algorithm 3's
+    iteration matrix (I - P_G)(I - P_1^l (E - K^+)) by power iteration on the
+    library's FP64 operators (rte_rates), over the anisotropy g, the
+    subspace dimension d_N (N^+ = 0, 2, 4: d = 1, 6, 15) and the steps l of
+    P_1^l: the study of the paper's Section 6.2 (Tables 3-7) on a synthetic
+    geometry, since the paper's lattice layout is not reproducible.  The
+    geometry: the unit square, 24 x 24 mesh, 4 x 4 checkerboard of
+    sigma_t in {1, 10} with sigma_s = 0.999 sigma_t (c = 0.999, the
+    paper's strongly scattering regime), 256 even directions."""
+    import torch
+    import workloads
+    import paper_2102_09038_gb300 as rte
+    torch.cuda.set_device(0)
+    out = []
+    for g in (0.1, 0.3, 0.5, 0.7, 0.9):
+        p = workloads.checkerboard(m=24, levels=3, g=g, ratio=0.999, blocks=4, seed=0)
+        for n_plus in (0, 2, 4):
+            for l in (1, 2, 3, 4):
+                s = rte.Solver(p, precision=rte.FP64, n_plus=n_plus, l=l,
+                               p1_route=rte.P1_RICHARDSON)
+                rho, eta, steps = s.rates(maxit=300, tol=1e-7)
+                s.close()
+                row = dict(g=g, d_N=(n_plus + 1) * (n_plus + 2) // 2, l=l, rho=rho, eta=eta,
+                           steps=steps, g_pow_l=g ** l)
+                out.append(row)
+                print(json.dumps(row), flush=True)
+    return out
+
+
 if __name__ == '__main__':
     a = parse()
+    if a.rates:
+        rates_study(a)
+        sys.exit(0)
+    if a.mk_routes:
+        mk_routes_study(a)
+        sys.exit(0)
     if a.impl == 'reference':
         run_reference(a)
     else:

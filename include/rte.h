@@ -58,7 +58,13 @@ extern "C" {
 #define RTE_DGEMM_SIMT 1
 #define RTE_DGEMM_SPLIT 2
 
-/* How (M^- - K^-)^{-1} is applied inside Apply-E (Algorithm 1, line 2). */
+/* How (M^- - K^-)^{-1} is applied inside Apply-E (Algorithm 1, line 2).
+ * RTE_MK_PCG runs the paper's PCG with the Lemma's preconditioner to mk_tol
+ * as a device-side loop (a CUDA graph whose while node repeats one iteration
+ * until a check kernel finds every right-hand side converged, or mk_maxit):
+ * no host round trip per iteration.  In the mixed modes it applies to the
+ * FP64 operator (the outer residual), with K^- on the split FP64-accurate
+ * tensor-core GEMM; the inner FP32 applies keep the eigenbasis route. */
 #define RTE_MK_EIGEN 0      /* exact, in the full eigenbasis of (S^-, M_S^-) */
 #define RTE_MK_PCG 1        /* PCG with the Lemma apply_high_order_pre prec. */
 
@@ -78,6 +84,21 @@ extern "C" {
 #define RTE_P1_AUTO (-1)
 #define RTE_P1_RICHARDSON 0
 #define RTE_P1_PCG 1
+
+/* How E_0^{-1} is applied (its n_S^+ decoupled direction blocks, eq.
+ * equivalence_bE_bE0).  RTE_E0_DIRECT factorises every block once at setup,
+ * as the paper's experiments do (Section 6: a sparse direct solver for
+ * E_0's blocks): the blocks are block tridiagonal over the mesh rows, and
+ * the library keeps the inverses of their Schur complements ((m+1)^2 values
+ * per row and direction; FP64 in RTE_FP64 mode, FP32 in the mixed modes) and
+ * solves by one forward and one backward sweep, exactly up to rounding;
+ * e0_tol and e0_maxit are then unused.  RTE_E0_MULTIGRID runs CG
+ * preconditioned by a V-cycle per block to e0_tol, the route Section 5.5
+ * names for larger problems.  RTE_E0_AUTO (0, the default) takes the direct
+ * route when the mesh allows it (m <= 156) and multigrid otherwise. */
+#define RTE_E0_AUTO 0
+#define RTE_E0_DIRECT 1
+#define RTE_E0_MULTIGRID 2
 
 typedef struct rte_handle rte_handle;
 
@@ -104,7 +125,8 @@ typedef struct {
     int mk_route;           /* RTE_MK_EIGEN | RTE_MK_PCG                     */
     double mk_tol;          /* relative residual of the (M^- - K^-) PCG      */
     int mk_maxit;
-    double e0_tol;          /* relative residual per column of E_0 CG;
+    double e0_tol;          /* relative residual per column of E_0 CG
+                               (multigrid route);
                                0: 1e-12 (FP64) or 0.3 (mixed modes)          */
     int e0_maxit;
     double coarse_tol;      /* relative residual of the E_c CG;
@@ -121,6 +143,8 @@ typedef struct {
                                shape for the process); 0: fixed shapes       */
     int p1_route;           /* RTE_P1_AUTO (default) | RTE_P1_RICHARDSON |
                                RTE_P1_PCG                                    */
+    int e0_route;           /* RTE_E0_AUTO (default) | RTE_E0_DIRECT |
+                               RTE_E0_MULTIGRID                              */
 } rte_options;
 
 typedef struct {
@@ -150,9 +174,18 @@ int rte_default_options(rte_options* opts);
  * and 5.4), the direction blocks of E_0 (eq. equivalence_bE_bE0) and the
  * coarse matrix E_c = W^T (E - K^+) W (Section 5.4, Algorithm 3 lines 1-4)
  * and uploads them to the current device.  stream: a cudaStream_t (NULL
- * for the legacy default stream).  On success *out owns all of it. */
+ * for the legacy default stream).  On success *out owns all of it.  A
+ * problem whose estimated device memory (rte_estimate_bytes at
+ * opts->max_rhs) exceeds the device's free memory plus what its default
+ * memory pool holds unused is refused with RTE_ERR_NOMEM before anything is
+ * allocated. */
 int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
               rte_handle** out);
+
+/* Moves the handle's work to another stream (a cudaStream_t): functions
+ * called afterwards queue on it.  Work already queued on the old stream is
+ * not waited for; the caller orders the two. */
+int rte_set_stream(rte_handle* h, void* stream);
 
 /* Sizes of the discrete spaces: n_R^+, n_R^-, n_S^+, n_S^-, d^+, d^-. */
 int rte_sizes(const rte_handle* h, int* n_nodes, int* n_cells, int* n_dirs,
@@ -163,6 +196,19 @@ int rte_sizes(const rte_handle* h, int* n_nodes, int* n_cells, int* n_dirs,
  * (Section 2.4, l^+(w) = (q, w)); l^- = 0 because the odd functions
  * integrate to zero against an isotropic q. */
 int rte_rhs(rte_handle* h, const double* q_nodal, double* q, int nrhs);
+
+/* q += the inflow part of l^+ (Section 2.4: l^+(w^+) = (q, w^+) +
+ * 2 (|s.n| g, w^+) over dD_- = {(s, r): r on the boundary, s.n(r) < 0})
+ * for inflow data g, a device array [nrhs][4][m + 1][2 n_S^+] of values
+ * piecewise constant on the sphere triangles and P1 along each face:
+ * face f = 0, 1, 2, 3 is x = 0, x = 1, y = 0, y = 1; node j runs along the
+ * face in increasing y (x faces) or x (y faces), i.e. node index
+ * j (m+1), j (m+1) + m, j and m (m+1) + j; entry 2k is the value on K_k
+ * and 2k + 1 on -K_k.  Only the triangle of each pair that points into the
+ * domain through the face (s.n < 0) is read; the other entry is ignored.
+ * q: device, nrhs x n_R^+ x n_S^+ (e.g. from rte_rhs); the term is added.
+ * Vacuum inflow (g = 0) needs no call. */
+int rte_inflow(rte_handle* h, const double* g, double* q, int nrhs);
 
 /* y = (E - K^+) x (eq. ep_discrete; Algorithm 1 for E), device vectors. */
 int rte_apply(rte_handle* h, const double* x, double* y, int nrhs);
@@ -263,8 +309,10 @@ size_t rte_autotune_report(char* buf, size_t len);
 
 /* The FP64 split GEMM of RTE_DGEMM_SPLIT, exposed for testing and
  * profiling: C[M x N] = A[M x K] * Bt[N x K]^T, all FP64 row-major device
- * arrays, with `slices` digit slices per operand (1..9).  Allocates its own
- * temporaries. */
+ * arrays, with `slices` digit slices per operand (1..9).  K must be a
+ * multiple of 8 (refused with RTE_ERR_ARG before any device work); K = 0
+ * writes C = 0.  Allocates its temporaries stream-ordered on `stream` and
+ * synchronises it before returning (it reads the GEMM's timeout flag). */
 int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, int K,
                     int slices, void* stream);
 
@@ -285,11 +333,14 @@ int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, 
  * RTE_SPLIT_STATIC_SCRATCH_BYTES = 32 MiB (e.g. slices = 7 with
  * M = N = K = 1024).  Larger operands return RTE_ERR_ARG, with the bytes
  * needed in rte_last_error(), before any device work.  K must be a multiple
- * of 8 (16-byte rows of BF16 slices); K = 0 writes C = 0.
+ * of 8 (16-byte rows of BF16 slices), also refused before any device work;
+ * K = 0 writes C = 0.
  *
- * The first call on each device looks up the scratch's device address and
- * sets the GEMM kernel's shared-memory attribute: make it before any stream
- * capture begins on that device.  Calls that overlap in time on one device
+ * Every call looks up the scratch's device address on the current device
+ * (so a device reset cannot leave a stale address) and sets the GEMM
+ * kernel's shared-memory attribute; the first call on each device also
+ * loads the library's device code there: make it before any stream capture
+ * begins on that device.  Calls that overlap in time on one device
  * (from several host threads, or on streams whose work overlaps) share the
  * one scratch and race: order them (one stream, or an event between them).
  * Synchronises `stream` before returning (it reads the GEMM's timeout
@@ -335,6 +386,28 @@ int rte_trace_read(rte_handle* h, double* us, int cap, int* count);
  * handles, all threads), for counting launches inside a timed region. */
 long long rte_kernel_launches(void);
 
+/* Failure detection (not part of the paper's method).  Every device-side
+ * wait of the library is bounded: a grid-barrier wait of the persistent
+ * E_0 / E_c kernels, and an mbarrier wait of the tensor-core pipelines.  A
+ * wait that runs out makes the kernel record the failure and return; the
+ * calling function then returns RTE_ERR_TIMEOUT and the CUDA context stays
+ * usable.  rte_set_wait_limit sets the limit (seconds, in (0, 60]; default
+ * 2 s): for grid barriers of every launch made after the call, for mbarrier
+ * waits on the current device.  Not thread-safe against concurrent
+ * launches. */
+int rte_set_wait_limit(double seconds);
+
+/* Self-test of the bounded grid barrier: a cooperative launch of `blocks`
+ * blocks (at most the device's resident capacity, else RTE_ERR_ARG) that
+ * meet at `rounds` barriers, except block skip_block (>= 0), which leaves
+ * before the first, so that the others' waits run out after the current
+ * wait limit; skip_block < 0: no block leaves.  Queued on `stream` and
+ * synchronised.  *timed_out = whether a wait ran out; *passed_blocks = the
+ * blocks that passed every barrier.  Returns RTE_ERR_TIMEOUT if a wait ran
+ * out, else RTE_OK. */
+int rte_barrier_selftest(int blocks, int skip_block, int rounds, void* stream, int* timed_out,
+                         int* passed_blocks);
+
 void rte_destroy(rte_handle* h);
 
 /* ------------------------------------------------------------------------
@@ -348,6 +421,13 @@ void rte_destroy(rte_handle* h);
  * its slot's stream and copies u back to host memory; the device work of
  * concurrent requests overlaps.  The server copies the problem arrays and
  * the source at submission; the caller keeps ownership of its buffers.
+ *
+ * Operator cache: after a request the server keeps its set-up handle idle.
+ * A later request with the same operator (mesh, sphere level, g and sigma
+ * fields; the options are the server's) and no more right-hand sides takes
+ * it and skips rte_setup: only its source, solve and copy-back run.  Idle
+ * handles count against hbm_budget_bytes and are destroyed, least recently
+ * used first, when an admission needs their memory.
  * ------------------------------------------------------------------------ */
 typedef struct rte_server rte_server;
 
@@ -372,8 +452,14 @@ int rte_server_wait(rte_server* sv, long long id, double timeout_s, double* u, s
                     rte_stats* stats, double* latency_s, double* queue_s);
 
 /* Finishes the running requests and stops the workers; requests still
- * queued are dropped. */
+ * queued are dropped; idle handles are destroyed. */
 void rte_server_destroy(rte_server* sv);
+
+/* Operator-cache counters: admissions that took an idle handle (*hits), that
+ * set up a new one (*misses), and the bytes of the idle handles now kept.
+ * Any pointer may be NULL. */
+int rte_server_cache_stats(rte_server* sv, long long* hits, long long* misses,
+                           size_t* idle_bytes);
 
 /* Solves `count` independent problems at once through a temporary server:
  * q_nodal[i] (host, nrhs[i] x n_R^+), u[i] (host, nrhs[i] x n_R^+ x n_S^+). */

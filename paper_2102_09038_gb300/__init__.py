@@ -13,12 +13,13 @@ import os
 
 __all__ = ['Solver', 'RteError', 'load', 'OPS', 'FP64', 'MIXED_FP32',
            'MIXED_BF16', 'MK_EIGEN', 'MK_PCG', 'P1_AUTO', 'P1_RICHARDSON',
-           'P1_PCG']
+           'P1_PCG', 'E0_AUTO', 'E0_DIRECT', 'E0_MULTIGRID']
 
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 MK_EIGEN, MK_PCG = 0, 1
 P1_AUTO, P1_RICHARDSON, P1_PCG = -1, 0, 1
 DGEMM_AUTO, DGEMM_SIMT, DGEMM_SPLIT = 0, 1, 2
+E0_AUTO, E0_DIRECT, E0_MULTIGRID = 0, 1, 2
 OPS = dict(A=1, AT=2, KPLUS=3, MK=4, MK_INV=5, MK_PREC=6, E=7, E0_INV=8,
            P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13, E_LO=14, EK_LO=15)
 EXPORTS = dict(Splus=0, Sminus=1, m=2, MSm=3, A1=4, A2=5, omx=6, omy=7,
@@ -52,7 +53,8 @@ class _Options(ctypes.Structure):
                 ('coarse_maxit', ctypes.c_int), ('max_iter', ctypes.c_int),
                 ('max_rhs', ctypes.c_int), ('dgemm', ctypes.c_int),
                 ('split_slices', ctypes.c_int), ('mg_sweeps', ctypes.c_int),
-                ('autotune', ctypes.c_int), ('p1_route', ctypes.c_int)]
+                ('autotune', ctypes.c_int), ('p1_route', ctypes.c_int),
+                ('e0_route', ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -68,13 +70,14 @@ class _Stats(ctypes.Structure):
 
 
 _lib = None
-EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs',
+EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs', 'rte_inflow',
             'rte_apply', 'rte_precond', 'rte_solve', 'rte_operator',
             'rte_export', 'rte_timing_enable', 'rte_timing_read',
             'rte_kernel_launches', 'rte_gemm_lowp', 'rte_dgemm_split',
             'rte_trace_enable', 'rte_estimate_bytes', 'rte_server_create',
             'rte_server_submit', 'rte_server_wait', 'rte_server_destroy', 'rte_solve_batch',
-            'rte_trace_read', 'rte_destroy',
+            'rte_trace_read', 'rte_destroy', 'rte_set_wait_limit', 'rte_barrier_selftest',
+            'rte_set_stream', 'rte_server_cache_stats',
             'rte_last_error']
 
 
@@ -94,6 +97,7 @@ def load(path=LIB_PATH):
     lib.rte_sizes.argtypes = [P] + [ctypes.POINTER(I)] * 6
     lib.rte_rhs.argtypes = [P, P, P, I]
     lib.rte_apply.argtypes = [P, P, P, I]
+    lib.rte_inflow.argtypes = [P, P, P, I]
     lib.rte_precond.argtypes = [P, P, P, I, I]
     lib.rte_solve.argtypes = [P, P, P, I, D, ctypes.POINTER(_Stats)]
     lib.rte_operator.argtypes = [P, I, P, P, I]
@@ -121,11 +125,17 @@ def load(path=LIB_PATH):
                                     ctypes.c_size_t, ctypes.POINTER(_Stats),
                                     ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.rte_server_destroy.argtypes = [P]
+    lib.rte_server_cache_stats.argtypes = [P, ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_longlong),
+                                           ctypes.POINTER(ctypes.c_size_t)]
+    lib.rte_set_stream.argtypes = [P, P]
     lib.rte_server_destroy.restype = V
     lib.rte_setup_times.argtypes = [P, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D), I,
                                     ctypes.POINTER(I)]
     lib.rte_trace_enable.argtypes = [P, I]
     lib.rte_trace_read.argtypes = [P, ctypes.POINTER(D), I, ctypes.POINTER(I)]
+    lib.rte_set_wait_limit.argtypes = [D]
+    lib.rte_barrier_selftest.argtypes = [I, I, I, P, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.rte_kernel_launches.argtypes = []
     lib.rte_kernel_launches.restype = ctypes.c_longlong
     lib.rte_destroy.argtypes = [P]
@@ -142,6 +152,27 @@ def load(path=LIB_PATH):
 def kernel_launches():
     """Kernels launched by librte in this process so far."""
     return int(load().rte_kernel_launches())
+
+
+def set_wait_limit(seconds):
+    """Limit of every device-side wait of the library (rte_set_wait_limit):
+    a wait that runs out makes the call return RTE_ERR_TIMEOUT."""
+    _check(load().rte_set_wait_limit(float(seconds)))
+
+
+def barrier_selftest(blocks, skip_block=-1, rounds=4, stream=None):
+    """(status, timed_out, passed_blocks) of rte_barrier_selftest: a
+    cooperative launch whose block skip_block never reaches the barrier."""
+    import torch
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    to, ok = ctypes.c_int(-1), ctypes.c_int(-1)
+    rc = lib.rte_barrier_selftest(int(blocks), int(skip_block), int(rounds),
+                                  ctypes.c_void_p(st.cuda_stream), ctypes.byref(to),
+                                  ctypes.byref(ok))
+    if rc not in (0, 5):
+        _check(rc)
+    return rc, to.value, ok.value
 
 
 def gemm_lowp(A, Bt, out_bf16=False, stream=None):
@@ -162,13 +193,28 @@ def gemm_lowp(A, Bt, out_bf16=False, stream=None):
     return C
 
 
+def _split_operands(A, Bt):
+    """Checks the operands of the split GEMMs before any library call: both
+    2-D float64 tensors on one CUDA device with the same K."""
+    import torch
+    for name, t in (('A', A), ('Bt', Bt)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+                and t.dim() == 2):
+            raise ValueError('%s must be a 2-D float64 CUDA tensor' % name)
+    if A.device != Bt.device:
+        raise ValueError('A and Bt must be on the same CUDA device')
+    if A.shape[1] != Bt.shape[1]:
+        raise ValueError('A is %s and Bt is %s: their K differ' % (tuple(A.shape),
+                                                                    tuple(Bt.shape)))
+    return A.contiguous(), Bt.contiguous()
+
+
 def dgemm_split(A, Bt, slices=7, stream=None):
     """C = A @ Bt.T for float64 CUDA tensors by the exact BF16 digit-slice
     tensor-core GEMM."""
     import torch
     load()
-    A = A.contiguous()
-    Bt = Bt.contiguous()
+    A, Bt = _split_operands(A, Bt)
     M, K = A.shape
     N = Bt.shape[0]
     C = torch.empty((M, N), device=A.device, dtype=torch.float64)
@@ -202,10 +248,15 @@ def dgemm_split_static(A, Bt, slices=7, out=None, stream=None):
     so that nothing is allocated on this path at all."""
     import torch
     load()
-    A = A.contiguous()
-    Bt = Bt.contiguous()
+    A, Bt = _split_operands(A, Bt)
     M, K = A.shape
     N = Bt.shape[0]
+    if out is not None:
+        if not (isinstance(out, torch.Tensor) and out.dtype == torch.float64
+                and out.device == A.device and out.is_contiguous()
+                and tuple(out.shape) == (M, N)):
+            raise ValueError('out must be a contiguous float64 tensor of shape (%d, %d) on %s'
+                             % (M, N, A.device))
     C = out if out is not None else torch.empty((M, N), device=A.device, dtype=torch.float64)
     st = stream if stream is not None else torch.cuda.current_stream()
     _check(_lib.rte_dgemm_split_static(_ptr(A), _ptr(Bt), _ptr(C), M, N, K, slices,
@@ -296,6 +347,13 @@ class Server:
         return u, dict(iterations=st.iterations, rel_residual=st.rel_residual,
                        latency=lat.value, queue=que.value, seconds=st.seconds)
 
+    def cache_stats(self):
+        """(hits, misses, idle bytes) of the server's operator cache."""
+        h, m, b = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()
+        _check(_lib.rte_server_cache_stats(self._h, ctypes.byref(h), ctypes.byref(m),
+                                           ctypes.byref(b)))
+        return h.value, m.value, b.value
+
     def close(self):
         if getattr(self, '_h', None):
             _lib.rte_server_destroy(self._h)
@@ -366,6 +424,17 @@ class Solver:
         out = self.even(nrhs) if out is None else out
         _check(_lib.rte_rhs(self._h, self._vec(q_nodal), self._vec(out), nrhs))
         return out
+
+    def inflow(self, g, q):
+        """q += the inflow part of l^+ for data g of shape
+        (nrhs, 4, m + 1, 2 n_S^+) (rte_inflow: faces x = 0, x = 1, y = 0,
+        y = 1; nodes along each face; entry 2k on K_k, 2k + 1 on -K_k)."""
+        m = int(round(self.n_nodes ** 0.5)) - 1
+        nrhs = q.shape[0]
+        if tuple(g.shape) != (nrhs, 4, m + 1, 2 * self.n_dirs):
+            raise ValueError('inflow data must have shape (nrhs, 4, m + 1, 2 n_S^+)')
+        _check(_lib.rte_inflow(self._h, self._vec(g), self._vec(q), nrhs))
+        return q
 
     def apply(self, x, out=None):
         out = self.torch.empty_like(x) if out is None else out

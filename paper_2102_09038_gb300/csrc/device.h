@@ -59,6 +59,8 @@ struct DevSystem {
     const double* ang_A2;      // [nSp][3]
     const double* ang_MSm;     // [nSp][9]
     const double* ang_MSm_inv; // [nSp][9]
+    const int* inflow_half;    // [4 faces][nSp]: which triangle of pair k (0: K_k,
+                               // 1: -K_k) enters the domain through the face
     const double* e0s;         // [nSp][6]  gamma a11, gamma a12, gamma a22, omx, omy, m
     const double* Sp;          // [nSp][nSp]
     const double* Sm;          // [nSm][nSm]
@@ -76,6 +78,11 @@ struct DevSystem {
     DevLow lo;                 // mixed-precision copies (null in FP64 mode)
     // E_0 level-0 stencil coefficients per direction, ELL [7][nRp][nSp]
     const double* e0coef;
+    // direct route of E_0^{-1}: inverses of the row Schur complements of every
+    // direction block, [nSp][m+1][ld][ld] (e0_direct.cu); one of the two set
+    bool e0_direct = false;
+    const float* e0lu32 = nullptr;
+    const double* e0lu64 = nullptr;
     const double* ec_ell;      // E_c in ELL form [7][nRp][dP][dP], blocks transposed
     // digit slices of the constant second operands for the split FP64 GEMM
     int split_S;               // 0: FP64 GEMMs on the FP64 units
@@ -85,6 +92,8 @@ struct DevSystem {
     const int* ex_Vm;
     const void* sl_Sp;
     const int* ex_Sp;
+    const void* sl_Sm;         // S^- (the PCG route's K^- in the mixed modes)
+    const int* ex_Sm;
     MGDevice e0mg;             // multigrid of the E_0 direction blocks
     MGDevice ecmg;             // multigrid of E_c
 };
@@ -144,6 +153,8 @@ void mk_minv_scale(cudaStream_t s, const DevSystem& d, const double* B,
                    double* Y, int nrhs);
 
 // q_{r,i,k} = (M q_nodal_r)_i m_k
+// q += the inflow part of l^+ for data g [nrhs][4][m+1][2 nSp] (rte_inflow)
+void inflow_source(cudaStream_t s, const DevSystem& d, const double* g, double* q, int nrhs);
 void rhs_source(cudaStream_t s, const DevSystem& d, const double* qn,
                 double* q, int nrhs);
 
@@ -167,6 +178,21 @@ size_t e0_cg_work_bytes(const DevSystem& d, int nrhs);
 // solution at the interface, reductions in FP64.
 int e0_cg_lo(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nrhs,
              double tol, int maxit, void* work, size_t work_bytes, SolveStatus* status_dev);
+
+// Direct route of E_0^{-1} (e0_direct.cu): whether the mesh fits it, the
+// bytes of its factor and of the setup scratch, the factorisation (setup)
+// and the solve X = E_0^{-1} B (all right-hand sides, exact up to rounding).
+bool e0_direct_fits(int m);
+size_t e0_direct_bytes(int m, int nSp, bool fp64);
+size_t e0_direct_scratch_bytes(int m, int nSp);
+int e0_direct_factor(cudaStream_t s, const DevSystem& d, double* scratch, float* out32,
+                     double* out64);
+int e0_direct_solve(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nrhs,
+                    bool fp64);
+// Reads and clears the flag a timed-out factor-block wait sets (synchronises s).
+int e0_direct_error(cudaStream_t s);
+// Limit of one such wait on the current device (SM clock cycles).
+int e0_set_wait_cycles(long long cycles);
 
 // E_c^{-1} B by one persistent block-Jacobi CG per RHS.
 int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,
@@ -198,6 +224,9 @@ int device_sm_count();
 // Phase trace of the persistent solver kernels: when buf is set, block 0
 // records %globaltimer after every grid barrier (cap entries per launch).
 void set_phase_trace(unsigned long long* buf, int cap);
+// Limit of each grid-barrier wait of the persistent kernels launched after
+// the call (nanoseconds; 0 restores the 2 s default).
+void set_wait_limit_ns(unsigned long long ns);
 
 // Count of kernel launches issued by the library (host-side counter).
 void count_launches(long long n);

@@ -9,8 +9,6 @@
 // has no counterpart; the arithmetic is that of rte_dgemm_split.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/rte.h"
 #include "rte_internal.h"
 #include "tc_gemm.h"
@@ -21,10 +19,6 @@ namespace {
 // exponents), so nothing in it has to start at zero.
 static __device__ __align__(256) unsigned char g_split_scratch[RTE_SPLIT_STATIC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch[kMaxDevices] = {};
-
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
 }  // namespace
@@ -34,6 +28,9 @@ extern "C" int rte_dgemm_split_static(const double* A, const double* Bt, double*
     using namespace rte;
     if (!A || !Bt || !C || M < 0 || N < 0 || K < 0 || slices < 1 || slices > 9)
         return fail(RTE_ERR_ARG, "bad argument");
+    // the slices' rows are K BF16 values and each must start on 16 bytes;
+    // refused here, before any launch can touch the shared scratch
+    if (K % 8 != 0) return fail(RTE_ERR_ARG, "K must be a multiple of 8");
     // a first check in floating point, so that the exact byte count below
     // cannot overflow
     if (2.0 * slices * ((double)M + (double)N) * (double)K > (double)RTE_SPLIT_STATIC_SCRATCH_BYTES)
@@ -51,24 +48,17 @@ extern "C" int rte_dgemm_split_static(const double* A, const double* Bt, double*
     cudaStream_t s = (cudaStream_t)stream;
     if (K == 0) {
         RTE_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * M * N, s));
+        RTE_CUDA_TRY(cudaStreamSynchronize(s));
         return RTE_OK;
     }
-    int dev = 0;
-    RTE_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(RTE_ERR_ARG, "device index out of range");
-    char* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch[dev]) {
-            void* p = nullptr;
-            const cudaError_t e = cudaGetSymbolAddress(&p, g_split_scratch);
-            if (e != cudaSuccess)
-                return fail(RTE_ERR_CUDA, std::string("cudaGetSymbolAddress: ") +
-                                              cudaGetErrorString(e));
-            g_scratch[dev] = p;
-        }
-        base = static_cast<char*>(g_scratch[dev]);
-    }
+    // The array's device address on the current device, looked up on every
+    // call (a host-side table lookup once the module is loaded), so that a
+    // device reset or a new primary context never leaves a stale address.
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_split_scratch);
+    if (e != cudaSuccess)
+        return fail(RTE_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    char* base = static_cast<char*>(p);
     int *ea = nullptr, *eb = nullptr;
     RTE_TRY(ozaki_split(s, A, M, K, slices, base, &ea));
     RTE_TRY(ozaki_split(s, Bt, N, K, slices, base + off_b, &eb));

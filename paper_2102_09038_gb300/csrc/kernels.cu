@@ -246,6 +246,43 @@ __global__ void k_rhs_source(int nRp, int nSp, int nrhs, int nnz,
     }
 }
 
+// Inflow part of l^+ (Section 2.4): 2 (|s.n| g, phi_i mu_k) over the
+// incoming half of the boundary.  On face f with outward normal n, exactly
+// one triangle of pair k has s.n < 0 (the octahedral sphere mesh has no
+// triangle across a coordinate plane): half[f][k] says which.  Its integral
+// of |s.n| is half of omega_k (omega^x on the faces x = 0, 1, omega^y on
+// y = 0, 1), and the data is P1 along the face, so
+//   q[i(f, j)][k] += omega_k sum_j' B1[j][j'] g[f][j'][2k + half[f][k]]
+// with B1 the face's 1-D P1 mass (h/3 at the ends, 2h/3 inside, h/6 off the
+// diagonal, h = 1/m).  One launch takes the two opposite faces f0, f0 + 1,
+// whose nodes are disjoint, so no two threads add to one entry.
+__global__ void k_inflow(int m, int nSp, int nrhs, int f0, const int* __restrict__ half,
+                         const double* __restrict__ omx, const double* __restrict__ omy,
+                         const double* __restrict__ g, double* __restrict__ q) {
+    const int nf = m + 1, nRp = nf * nf;
+    const size_t total = (size_t)nrhs * 2 * nf * nSp;
+    const double h = 1.0 / m;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e % nSp);
+        size_t rest = e / nSp;
+        const int j = (int)(rest % nf);
+        rest /= nf;
+        const int f = f0 + (int)(rest % 2);
+        const int r = (int)(rest / 2);
+        const int hk = half[f * nSp + k];
+        const double* gf = g + ((size_t)r * 4 + f) * nf * 2 * nSp + 2 * k + hk;
+        const double gj = gf[(size_t)j * 2 * nSp];
+        double acc = (j == 0 || j == m ? h / 3.0 : 2.0 * h / 3.0) * gj;
+        if (j > 0) acc += h / 6.0 * gf[(size_t)(j - 1) * 2 * nSp];
+        if (j < m) acc += h / 6.0 * gf[(size_t)(j + 1) * 2 * nSp];
+        const double om = f < 2 ? omx[k] : omy[k];
+        // node of face f's j-th point: x = 0 / x = 1 run along y, y = 0 / y = 1 along x
+        const int i = f == 0 ? j * nf : f == 1 ? j * nf + m : f == 2 ? j : m * nf + j;
+        q[((size_t)r * nRp + i) * nSp + k] += om * acc;
+    }
+}
+
 // ------------------------------------------------------------ reductions
 template <int BS>
 __device__ double block_sum(double v) {
@@ -635,6 +672,14 @@ void mk_minv_scale(cudaStream_t s, const DevSystem& d, const double* B, double* 
     count_launches(1);
     k_mk_minv_scale<<<grid_for(total), kThreads, 0, s>>>(d.nRm, d.nSp, nrhs, d.cell_at,
                                                          d.ang_MSm_inv, B, Y);
+}
+
+void inflow_source(cudaStream_t s, const DevSystem& d, const double* g, double* q, int nrhs) {
+    const size_t total = (size_t)nrhs * 2 * (d.m + 1) * d.nSp;
+    for (int f0 = 0; f0 < 4; f0 += 2)
+        k_inflow<<<grid_for(total), kThreads, 0, s>>>(d.m, d.nSp, nrhs, f0, d.inflow_half,
+                                                     d.ang_omx, d.ang_omy, g, q);
+    count_launches(2);
 }
 
 void rhs_source(cudaStream_t s, const DevSystem& d, const double* qn, double* q, int nrhs) {

@@ -1516,11 +1516,14 @@ V view(const MGDevice& m) {
 // Optional phase trace of the persistent kernels (set by set_phase_trace).
 unsigned long long* g_trace_buf = nullptr;
 int g_trace_cap = 0;
+// Barrier wait limit of the next launches (0: the default of persist.cuh).
+unsigned long long g_wait_limit_ns = 0;
 
 int init_bar(cudaStream_t s, GridBar* bar) {
     GridBar h{};
     h.trace = g_trace_buf;
     h.cap = g_trace_cap;
+    h.limit_ns = g_wait_limit_ns;
     RTE_CUDA_TRY(cudaMemcpyAsync(bar, &h, sizeof(GridBar), cudaMemcpyHostToDevice, s));
     return RTE_OK;
 }
@@ -1579,12 +1582,25 @@ int e0_pcg_impl(cudaStream_t s, const DevSystem& d, const T* coef, const double*
     return RTE_OK;
 }
 
+// Self-test of the bounded grid barrier: every block meets the others at
+// `rounds` barriers, except block skip_block (when >= 0), which leaves
+// before the first one, so the others' waits must run out.  Blocks that pass
+// every barrier count themselves in *passed.
+__global__ void k_barrier_selftest(GridBar* bar, int skip_block, int rounds, int* passed) {
+    if ((int)blockIdx.x == skip_block) return;
+    for (int r = 0; r < rounds; ++r)
+        if (!grid_sync(bar)) return;
+    if (threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
 }  // namespace
 
 void set_phase_trace(unsigned long long* buf, int cap) {
     g_trace_buf = buf;
     g_trace_cap = cap;
 }
+
+void set_wait_limit_ns(unsigned long long ns) { g_wait_limit_ns = ns; }
 
 size_t e0_cg_work_bytes(const DevSystem& d, int nrhs) {
     const size_t n = (size_t)nrhs * d.nRp * d.nSp;
@@ -1659,3 +1675,48 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
 }
 
 }  // namespace rte
+
+using namespace rte;
+
+extern "C" int rte_barrier_selftest(int blocks, int skip_block, int rounds, void* stream,
+                                    int* timed_out, int* passed_blocks) {
+    if (blocks < 1 || rounds < 1 || skip_block >= blocks || !timed_out || !passed_blocks)
+        return fail(RTE_ERR_ARG, "bad argument");
+    constexpr int kThreads = 128;
+    int per_sm = 0;
+    RTE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, k_barrier_selftest, kThreads, 0));
+    if ((long long)blocks > (long long)per_sm * device_sm_count())
+        return fail(RTE_ERR_ARG, "more blocks than can be resident at once");
+    cudaStream_t s = (cudaStream_t)stream;
+    GridBar* bar = nullptr;
+    int* passed = nullptr;
+    if (cudaMallocAsync((void**)&bar, sizeof(GridBar), s) != cudaSuccess)
+        return fail(RTE_ERR_NOMEM, "barrier self-test allocation");
+    if (cudaMallocAsync((void**)&passed, sizeof(int), s) != cudaSuccess) {
+        cudaFreeAsync(bar, s);
+        return fail(RTE_ERR_NOMEM, "barrier self-test allocation");
+    }
+    GridBar hb{};
+    int rc = RTE_OK;
+    if (init_bar(s, bar) != RTE_OK || cudaMemsetAsync(passed, 0, sizeof(int), s) != cudaSuccess)
+        rc = fail(RTE_ERR_CUDA, "barrier self-test set-up");
+    if (rc == RTE_OK) {
+        void* args[] = {&bar, &skip_block, &rounds, &passed};
+        count_launches(1);
+        if (cudaLaunchCooperativeKernel((const void*)k_barrier_selftest, blocks, kThreads, args,
+                                        0, s) != cudaSuccess ||
+            cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(passed_blocks, passed, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess)
+            rc = fail(RTE_ERR_CUDA, "barrier self-test launch");
+    }
+    cudaFreeAsync(bar, s);
+    cudaFreeAsync(passed, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == RTE_OK)
+        rc = fail(RTE_ERR_CUDA, "barrier self-test synchronisation");
+    if (rc != RTE_OK) return rc;
+    *timed_out = hb.err;
+    if (hb.err) return fail(RTE_ERR_TIMEOUT, "a bounded grid barrier timed out");
+    return RTE_OK;
+}

@@ -16,9 +16,10 @@ struct GridBar {
     unsigned long long* trace;   // optional: %globaltimer after each barrier
     int cap;
     int pad;
+    unsigned long long limit_ns; // a wait gives up after this long (0: kWaitLimitNs)
 };
 
-// A barrier wait gives up after this many nanoseconds (2 s).
+// Default limit of a barrier wait: 2 s.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -46,11 +47,12 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb) {
             // plain polling (a sleep between polls costs more than it saves
             // at these barrier rates); the limit is checked every 256 polls
             const unsigned long long t0 = global_ns();
+            const unsigned long long lim = gb->limit_ns ? gb->limit_ns : kWaitLimitNs;
             unsigned spins = 0;
             while (*vgen == g) {
                 if ((++spins & 255u) == 0) {
                     if (*verr) break;
-                    if (global_ns() - t0 > kWaitLimitNs) {
+                    if (global_ns() - t0 > lim) {
                         atomicExch(&gb->err, 1);
                         break;
                     }

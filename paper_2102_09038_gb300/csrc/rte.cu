@@ -76,6 +76,19 @@ struct rte_handle {
     unsigned long long* trace = nullptr;   // phase trace buffer (profiling)
     // autotuned tile widths of the low-precision GEMMs (0: by N)
     int bn_mk1 = 0, bn_mk2 = 0, bn_kplus = 0;
+    // Algorithm 1's PCG loop as a CUDA graph whose while node repeats one
+    // iteration until a device-side check ends it (one executable graph per
+    // right-hand-side count), captured on a private stream; mk_state: [0]
+    // iterations of the last solve, [1] converged, [2] non-finite residual,
+    // [3] iterations since set-up (device, and a pinned host copy)
+    cudaStream_t cap_stream = nullptr;
+    std::map<int, cudaGraphExec_t> mk_graph;
+    int* mk_state = nullptr;
+    int* mk_state_host = nullptr;
+    int mk_total_seen = 0;
+    long long mk_body_launches = 0;
+    bool mk_pending = false;
+    bool capturing = false;
     // statistics of the last inner solves
     int e0_iters = 0, co_iters = 0, mk_iters = 0;
     // E_0^{-1} work of the current solve: launches, V-cycles, and V-cycles
@@ -113,6 +126,30 @@ void keep_pool_memory() {
         uint64_t v = kPoolKeep;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &v);
     }
+}
+
+// Refuses, before any allocation, a problem whose estimated device memory
+// (rte_estimate_bytes) exceeds what the device can still give: its free
+// memory plus what the default pool holds unused.
+int check_device_memory(const rte_problem& p, const rte_options& o) {
+    if (p.mesh_m < 1 || p.sphere_levels < 0 || p.sphere_levels > 5) return RTE_OK;   // refused later
+    const size_t need = rte_estimate_bytes(&p, &o, o.max_rhs);
+    size_t free_b = 0, total_b = 0;
+    RTE_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    int dev = 0;
+    RTE_CUDA_TRY(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    uint64_t reserved = 0, used = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    }
+    const size_t avail = free_b + (size_t)(reserved > used ? reserved - used : 0);
+    if (need > avail)
+        return fail(RTE_ERR_NOMEM, "the problem needs about " + std::to_string(need >> 20) +
+                                       " MiB of device memory; " + std::to_string(avail >> 20) +
+                                       " MiB are available");
+    return RTE_OK;
 }
 
 template <typename T>
@@ -181,7 +218,7 @@ struct Scope {
     int idx = -1;
     cudaEvent_t b{};
     Scope(rte_handle* hh, const char* name) : h(hh) {
-        if (!h->timing) return;
+        if (!h->timing || h->capturing) return;
         for (size_t i = 0; i < h->tnames.size(); ++i)
             if (h->tnames[i] == name) idx = (int)i;
         if (idx < 0) {
@@ -511,7 +548,52 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs, SetupClock* clk) {
     DevSystem& d = h->d;
     const int cap = h->opt.max_rhs;
     // ------------------------------------------------------------ E_0
-    {
+    if (d.e0_direct) {
+        // the level-0 coefficients alone: the factorisation reads them
+        const int slots[6] = {kK11, kK12, kK22, kBx, kBy, kMt};
+        const size_t nnz = hs.st.col.size();
+        MGHostLevel L;
+        L.m = hs.m;
+        L.st = hs.st;
+        L.vals.resize(6 * nnz);
+        for (int q = 0; q < 6; ++q)
+            std::copy(hs.sval.begin() + (size_t)slots[q] * nnz,
+                      hs.sval.begin() + (size_t)(slots[q] + 1) * nnz, L.vals.begin() + q * nnz);
+        std::vector<double> ell6;
+        RTE_TRY(to_ell(L, 6, 1, ell6));
+        const double* dell = nullptr;
+        RTE_TRY(upload(h, &dell, ell6));
+        double* c = nullptr;
+        RTE_TRY(dalloc(h, &c, (size_t)7 * hs.nRp * hs.nSp));
+        e0_coefficients(h->stream, hs.nRp, hs.nSp, dell, d.e0s, c, nullptr);
+        d.e0coef = c;
+        // factor: FP64 in FP64 mode, FP32 in the mixed modes; FP64 scratch
+        // of one Schur complement inverse per direction, freed at the end
+        const bool fp64 = !h->mixed;
+        const size_t fb = e0_direct_bytes(hs.m, hs.nSp, fp64);
+        double* scratch = nullptr;
+        if (cudaMallocAsync(&scratch, e0_direct_scratch_bytes(hs.m, hs.nSp), h->stream) !=
+            cudaSuccess)
+            return fail(RTE_ERR_NOMEM, "E_0 factorisation scratch");
+        int rc = RTE_OK;
+        if (fp64) {
+            double* f = nullptr;
+            rc = dalloc(h, &f, fb / sizeof(double));
+            if (rc == RTE_OK) {
+                rc = e0_direct_factor(h->stream, d, scratch, nullptr, f);
+                d.e0lu64 = f;
+            }
+        } else {
+            float* f = nullptr;
+            rc = dalloc(h, &f, fb / sizeof(float));
+            if (rc == RTE_OK) {
+                rc = e0_direct_factor(h->stream, d, scratch, f, nullptr);
+                d.e0lu32 = f;
+            }
+        }
+        cudaFreeAsync(scratch, h->stream);
+        RTE_TRY(rc);
+    } else {
         const int slots[6] = {kK11, kK12, kK22, kBx, kBy, kMt};
         const size_t nnz = hs.st.col.size();
         std::vector<double> v((size_t)6 * nnz);
@@ -571,7 +653,7 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs, SetupClock* clk) {
         e0_coefficients(h->stream, hs.nRp, hs.nSp, dell, d.e0s, c, nullptr);
         d.e0coef = c;
     }
-    if (clk) clk->mark("E_0 multigrid");
+    if (clk) clk->mark(d.e0_direct ? "E_0 factorisation" : "E_0 multigrid");
     // ------------------------------------------------------------ E_c
     if (d.dP > 0) {
         MGHost mh;
@@ -625,8 +707,9 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs, SetupClock* clk) {
     }
     // the kernels index the level descriptors at run time: keep them in
     // device memory rather than in the (then locally copied) kernel argument
-    RTE_TRY(upload(h, &d.e0mg.dev_lev,
-                   std::vector<MGDeviceLevel>(d.e0mg.lev, d.e0mg.lev + d.e0mg.L)));
+    if (!d.e0_direct)
+        RTE_TRY(upload(h, &d.e0mg.dev_lev,
+                       std::vector<MGDeviceLevel>(d.e0mg.lev, d.e0mg.lev + d.e0mg.L)));
     if (d.dP > 0)
         RTE_TRY(upload(h, &d.ecmg.dev_lev,
                        std::vector<MGDeviceLevel>(d.ecmg.lev, d.ecmg.lev + d.ecmg.L)));
@@ -724,6 +807,11 @@ int alloc_workspace(rte_handle* h, int nrhs) {
         RTE_TRY(dalloc(h, &h->z5, no));
         RTE_TRY(dalloc(h, &h->z6, no));
         RTE_TRY(dalloc(h, &h->z7, no));
+        RTE_TRY(dalloc(h, &h->mk_state, 4));
+        RTE_CUDA_TRY(cudaMemsetAsync(h->mk_state, 0, 4 * sizeof(int), h->stream));
+        if (cudaMallocHost(&h->mk_state_host, 4 * sizeof(int)) != cudaSuccess)
+            return fail(RTE_ERR_NOMEM, "pinned PCG state");
+        std::memset(h->mk_state_host, 0, 4 * sizeof(int));
     }
     RTE_TRY(dalloc(h, &h->zsk, (size_t)nrhs * d.nRm * d.dM));
     if (d.split_S > 0) {
@@ -743,10 +831,12 @@ int alloc_workspace(rte_handle* h, int nrhs) {
     RTE_TRY(dalloc(h, &h->c2, nc));
     RTE_TRY(dalloc(h, &h->partial, (size_t)nrhs * 1024));
     RTE_TRY(dalloc(h, &h->sc, (size_t)nrhs * 16));
-    h->e0bytes = e0_cg_work_bytes(d, nrhs);
     char* w = nullptr;
-    RTE_TRY(dalloc(h, &w, h->e0bytes));
-    h->e0work = w;
+    if (!d.e0_direct) {
+        h->e0bytes = e0_cg_work_bytes(d, nrhs);
+        RTE_TRY(dalloc(h, &w, h->e0bytes));
+        h->e0work = w;
+    }
     h->cobytes = coarse_cg_work_bytes(d, nrhs);
     RTE_TRY(dalloc(h, &w, h->cobytes));
     h->cowork = w;
@@ -838,10 +928,169 @@ __global__ void k_ratio(const double* num, const double* den, double* out, int n
     if (i < n) out[i] = den[i] != 0.0 ? sign * num[i] / den[i] : 0.0;
 }
 
+// Y = (M^- - K^-) Z with K^- Z = diag(sigma_s |T|) Z S^- on the split
+// (FP64-accurate) tensor-core GEMM: the PCG route of the mixed modes
+int mk_apply_split(rte_handle* h, const double* Z, double* Y, double* G, int nrhs) {
+    const DevSystem& d = h->d;
+    Scope sc(h, "mk_apply");
+    int* ea = nullptr;
+    RTE_TRY(ozaki_split(h->stream, Z, nrhs * d.nRm, d.nSm, d.split_S, h->slices, &ea));
+    RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRm, d.sl_Sm, d.ex_Sm, d.nSm, d.nSm,
+                       d.split_S, G, d.nSm, 0, nullptr, nullptr, nullptr, 1));
+    mk_combine(h->stream, d, Z, G, Y, nrhs);
+    return RTE_OK;
+}
+
+// End of one PCG iteration of Algorithm 1 inside the graph: counts it,
+// records whether every right-hand side has ||r||^2 <= tol^2 ||b||^2 (or
+// a residual is not finite) and sets the while node's condition.
+__global__ void k_mk_check(const double* rr, const double* bb, int n, double tol2, int maxit,
+                           int* state, cudaGraphConditionalHandle loop) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int it = ++state[0];
+    ++state[3];
+    bool done = true, bad = false;
+    for (int r = 0; r < n; ++r) {
+        const double v = rr[r];
+        if (!isfinite(v)) bad = true;
+        if (!(v <= tol2 * bb[r])) done = false;
+    }
+    state[1] = done;
+    state[2] = bad;
+    cudaGraphSetConditional(loop, (!done && !bad && it < maxit) ? 1u : 0u);
+}
+
+// One PCG iteration for (M^- - K^-) X = B on the workspace of
+// mk_inv_pcg (the body of the graph's while node).
+int mk_pcg_body(rte_handle* h, int n, double* X, cudaGraphConditionalHandle loop) {
+    const DevSystem& d = h->d;
+    const size_t len = (size_t)d.nRm * d.nSm;
+    double *R = h->z3, *P = h->z4, *AP = h->z5, *Zb = h->z6, *G = h->z7, *tmp = h->zsk;
+    double* sc = h->sc;
+    cudaStream_t s = h->stream;
+    if (d.split_S > 0) RTE_TRY(mk_apply_split(h, P, AP, G, n));
+    else RTE_TRY(mk_apply(h, P, AP, G, n));
+    dot_per_rhs(s, P, AP, len, n, h->partial, sc + n);
+    k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc, sc + n, sc + 2 * n, n, 1.0);
+    axpby_per_rhs(s, P, X, len, n, sc + 2 * n, 0.0, nullptr, 1.0);          // x += alpha p
+    k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc, sc + n, sc + 2 * n, n, -1.0);
+    axpby_per_rhs(s, AP, R, len, n, sc + 2 * n, 0.0, nullptr, 1.0);         // r -= alpha Ap
+    dot_per_rhs(s, R, R, len, n, h->partial, sc + 3 * n);                   // r.r
+    RTE_TRY(mk_prec(h, R, Zb, tmp, n));
+    dot_per_rhs(s, R, Zb, len, n, h->partial, sc + n);                      // rz_new
+    k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc + n, sc, sc + 5 * n, n, 1.0);   // beta
+    RTE_CUDA_TRY(cudaMemcpyAsync(sc, sc + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    axpby_per_rhs(s, Zb, P, len, n, nullptr, 1.0, sc + 5 * n, 0.0);         // p = z + beta p
+    k_mk_check<<<1, 32, 0, s>>>(sc + 3 * n, sc + 4 * n, n, h->opt.mk_tol * h->opt.mk_tol,
+                                h->opt.mk_maxit, h->mk_state, loop);
+    count_launches(4);
+    return RTE_OK;
+}
+
+// The executable graph of the loop for n right-hand sides: a while node
+// whose body (captured on the handle's private stream) is mk_pcg_body.
+int mk_graph_for(rte_handle* h, int n, double* X, cudaGraphExec_t* out) {
+    auto it = h->mk_graph.find(n);
+    if (it != h->mk_graph.end()) {
+        *out = it->second;
+        return RTE_OK;
+    }
+    if (!h->cap_stream)
+        RTE_CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    RTE_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle loop;
+    int rc = RTE_OK;
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        rc = fail(RTE_ERR_CUDA, "cudaGraphConditionalHandleCreate failed");
+    if (rc == RTE_OK) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = loop;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) != cudaSuccess)
+            rc = fail(RTE_ERR_CUDA, "cudaGraphAddNode (while) failed");
+    }
+    if (rc == RTE_OK) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaStream_t saved = h->stream;
+        const long long before = launches_total();
+        h->stream = h->cap_stream;
+        h->capturing = true;
+        if (cudaStreamBeginCaptureToGraph(h->cap_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            rc = fail(RTE_ERR_CUDA, "stream capture of the PCG body failed to begin");
+        } else {
+            rc = mk_pcg_body(h, n, X, loop);
+            cudaGraph_t done = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(h->cap_stream, &done);
+            if (rc == RTE_OK && e != cudaSuccess)
+                rc = fail(RTE_ERR_CUDA, std::string("capture of the PCG body: ") +
+                                            cudaGetErrorString(e));
+        }
+        h->stream = saved;
+        h->capturing = false;
+        // capture launches nothing: the body's kernels are counted per replay
+        h->mk_body_launches = launches_total() - before;
+        count_launches(-h->mk_body_launches);
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (rc == RTE_OK && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess)
+        rc = fail(RTE_ERR_CUDA, "cudaGraphInstantiate of the PCG loop failed");
+    cudaGraphDestroy(g);
+    if (rc != RTE_OK) return rc;
+    h->mk_graph[n] = exec;
+    *out = exec;
+    return RTE_OK;
+}
+
+// Iterations of the graph loops launched since the last call, once the
+// stream has passed them (called after a synchronisation of the stream).
+void settle_mk(rte_handle* h) {
+    if (!h->mk_pending) return;
+    h->mk_pending = false;
+    h->mk_iters = h->mk_state_host[0];
+    const int total = h->mk_state_host[3];
+    count_launches((long long)(total - h->mk_total_seen) * h->mk_body_launches);
+    h->mk_total_seen = total;
+}
+
 // Algorithm 1 line 2: (M^- - K^-) X = B by PCG preconditioned with
-// eq. (MmKprecond); B = z1 and X = z2 inside Apply-E.  Per-RHS scalars stay
-// on the device; the host reads ||r||^2 once per iteration to stop.
+// eq. (MmKprecond); B = z1 and X = z2 inside Apply-E.  The set-up of the
+// recurrence runs on the stream, then the iterations run as the graph's
+// device-side loop: no host round trip per iteration.
 int mk_inv_pcg(rte_handle* h, const double* B, double* X, int nrhs) {
+    const DevSystem& d = h->d;
+    if (!h->z5) return fail(RTE_ERR_ARG, "PCG route needs mk_route = RTE_MK_PCG at setup");
+    const size_t len = (size_t)d.nRm * d.nSm;
+    double *R = h->z3, *P = h->z4, *Zb = h->z6, *tmp = h->zsk;
+    const int n = nrhs;
+    double* sc = h->sc;
+    cudaStream_t s = h->stream;
+    RTE_CUDA_TRY(cudaMemcpyAsync(R, B, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
+    RTE_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * n * len, s));
+    dot_per_rhs(s, B, B, len, n, h->partial, sc + 4 * n);                  // b.b
+    RTE_TRY(mk_prec(h, R, Zb, tmp, n));
+    RTE_CUDA_TRY(cudaMemcpyAsync(P, Zb, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
+    dot_per_rhs(s, R, Zb, len, n, h->partial, sc);                         // r.z
+    cudaGraphExec_t exec = nullptr;
+    RTE_TRY(mk_graph_for(h, n, X, &exec));
+    RTE_CUDA_TRY(cudaMemsetAsync(h->mk_state, 0, 3 * sizeof(int), s));
+    {
+        Scope sc2(h, "mk_pcg_loop");
+        RTE_CUDA_TRY(cudaGraphLaunch(exec, s));
+    }
+    RTE_CUDA_TRY(cudaMemcpyAsync(h->mk_state_host, h->mk_state, 4 * sizeof(int),
+                                 cudaMemcpyDeviceToHost, s));
+    h->mk_pending = true;
+    return RTE_OK;
+}
+
+// The same loop with the host reading ||r||^2 every iteration (the form
+// before the graph loop; kept for comparison).
+[[maybe_unused]] int mk_inv_pcg_host(rte_handle* h, const double* B, double* X, int nrhs) {
     const DevSystem& d = h->d;
     if (!h->z5) return fail(RTE_ERR_ARG, "PCG route needs mk_route = RTE_MK_PCG at setup");
     const size_t len = (size_t)d.nRm * d.nSm;
@@ -981,6 +1230,7 @@ int read_status(rte_handle* h, SolveStatus& st) {
     RTE_CUDA_TRY(cudaMemcpyAsync(&st, h->status, sizeof(SolveStatus), cudaMemcpyDeviceToHost,
                                  h->stream));
     RTE_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    settle_mk(h);
     if (st.timed_out) return fail(RTE_ERR_TIMEOUT, "a bounded grid barrier timed out");
     return RTE_OK;
 }
@@ -990,6 +1240,17 @@ int read_status(rte_handle* h, SolveStatus& st) {
 constexpr double kLowInnerTol = 1e-5;
 
 int e0_inv(rte_handle* h, const double* b, double* x, int nrhs) {
+    if (h->d.e0_direct) {
+        {
+            Scope sc(h, h->mixed ? "e0_direct" : "e0_direct64");
+            RTE_TRY(e0_direct_solve(h->stream, h->d, b, x, nrhs, !h->mixed));
+        }
+        h->e0_iters = 1;
+        h->e0_launches += 1;
+        h->e0_vcycles += 1.0;
+        h->e0_active_vcycles += 1.0;
+        return RTE_OK;
+    }
     if (h->mixed) {
         Scope sc(h, "e0_cg_lo");
         RTE_TRY(e0_cg_lo(h->stream, h->d, b, x, nrhs, std::max(h->opt.e0_tol, kLowInnerTol),
@@ -1163,6 +1424,7 @@ int rte_default_options(rte_options* o) {
     o->mg_sweeps = 2;
     o->autotune = 1;
     o->p1_route = RTE_P1_AUTO;   // P_1^l in FP64, PCG steps in the mixed modes
+    o->e0_route = RTE_E0_AUTO;   // direct factorisation when the mesh allows it
     return RTE_OK;
 }
 
@@ -1183,8 +1445,15 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         return fail(RTE_ERR_ARG, "unknown P_1 route");
     if (o.p1_route == RTE_P1_AUTO)
         o.p1_route = o.precision == RTE_FP64 ? RTE_P1_RICHARDSON : RTE_P1_PCG;
-    if (o.precision != RTE_FP64 && o.mk_route != RTE_MK_EIGEN)
-        return fail(RTE_ERR_ARG, "mixed precision uses the eigenbasis route for (M-K)^-1");
+    if (o.e0_route != RTE_E0_AUTO && o.e0_route != RTE_E0_DIRECT &&
+        o.e0_route != RTE_E0_MULTIGRID)
+        return fail(RTE_ERR_ARG, "unknown E_0 route");
+    if (o.e0_route == RTE_E0_DIRECT && !e0_direct_fits(prob->mesh_m))
+        return fail(RTE_ERR_ARG, "the direct E_0 route needs mesh_m <= 156");
+    if (o.e0_route == RTE_E0_AUTO)
+        o.e0_route = e0_direct_fits(prob->mesh_m) ? RTE_E0_DIRECT : RTE_E0_MULTIGRID;
+    if (o.mk_route != RTE_MK_EIGEN && o.mk_route != RTE_MK_PCG)
+        return fail(RTE_ERR_ARG, "unknown (M^- - K^-)^{-1} route");
     // inner tolerances left at 0 follow the precision mode: the plain FP64
     // method solves E_0 and E_c to 1e-12; under the mixed modes' FP64 outer
     // residual (iterative refinement) loose inner solves cost at most a few
@@ -1195,6 +1464,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     SetupClock clk{nullptr};
     HostSystem hs;
     RTE_TRY(build_host_system(*prob, o, hs));
+    RTE_TRY(check_device_memory(*prob, o));
     rte_handle* h = new rte_handle();
     h->opt = o;
     h->stream = (cudaStream_t)stream;
@@ -1206,6 +1476,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         return rc;
     };
     DevSystem& d = h->d;
+    d.e0_direct = o.e0_route == RTE_E0_DIRECT;
     d.m = hs.m;
     d.nRp = hs.nRp; d.nRm = hs.nRm; d.nSp = hs.nSp; d.nSm = hs.nSm;
     d.dP = hs.dP; d.dM = hs.dM; d.nnz = (int)hs.st.col.size();
@@ -1246,6 +1517,22 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     UP(ang_MSm, hs.MSm);
     UP(ang_MSm_inv, hs.MSm_inv);
     UP(e0s, hs.e0s);
+    {
+        // which triangle of each pair enters through each face (x = 0, x = 1,
+        // y = 0, y = 1; outward normals -e_x, e_x, -e_y, e_y): the one whose
+        // direction has s.n < 0, read from the sign of its vertex sum
+        std::vector<int> half((size_t)4 * hs.nSp);
+        for (int k = 0; k < hs.nSp; ++k) {
+            double c[2] = {0.0, 0.0};
+            for (int v = 0; v < 3; ++v)
+                for (int a = 0; a < 2; ++a) c[a] += hs.sphere.verts[3 * hs.sphere.tri[3 * k + v] + a];
+            for (int f = 0; f < 4; ++f) {
+                const double sn = (f % 2 == 0 ? -1.0 : 1.0) * c[f / 2];
+                half[(size_t)f * hs.nSp + k] = sn < 0.0 ? 0 : 1;
+            }
+        }
+        UP(inflow_half, half);
+    }
     // ------------------------------------------------ S^+ and S^- (device)
     const int n = hs.nSp, nm = hs.nSm;
     QuadDev q{};
@@ -1571,10 +1858,13 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
                 return bail(fail(RTE_ERR_ARG, "split_slices must be in [1, 9]"));
             d.split_S = o.split_slices;
             struct Src { const double* m; int rows, K; const void** sl; const int** ex; };
-            Src srcs[3] = {{d.VmT, nm, nm, &d.sl_VmT, &d.ex_VmT},
+            Src srcs[4] = {{d.VmT, nm, nm, &d.sl_VmT, &d.ex_VmT},
                            {d.Vm, nm, nm, &d.sl_Vm, &d.ex_Vm},
-                           {d.Sp, n, n, &d.sl_Sp, &d.ex_Sp}};
+                           {d.Sp, n, n, &d.sl_Sp, &d.ex_Sp},
+                           {d.Sm, nm, nm, &d.sl_Sm, &d.ex_Sm}};
             for (auto& sr : srcs) {
+                // S^- is needed as a GEMM operand only by the PCG route
+                if (sr.m == d.Sm && o.mk_route != RTE_MK_PCG) continue;
                 char* p = nullptr;
                 rc = dalloc(h, &p, ozaki_slice_bytes(sr.rows, sr.K, d.split_S));
                 if (rc) return bail(rc);
@@ -1635,6 +1925,21 @@ int rte_rhs(rte_handle* h, const double* q_nodal, double* q, int nrhs) {
     return RTE_OK;
 }
 
+int rte_set_stream(rte_handle* h, void* stream) {
+    if (!h) return fail(RTE_ERR_ARG, "NULL handle");
+    flush_timers(h);
+    h->stream = (cudaStream_t)stream;
+    return RTE_OK;
+}
+
+int rte_inflow(rte_handle* h, const double* g, double* q, int nrhs) {
+    if (!h || !g || !q || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
+    Scope sc(h, "inflow");
+    inflow_source(h->stream, h->d, g, q, nrhs);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
 int rte_apply(rte_handle* h, const double* x, double* y, int nrhs) {
     if (!h || !x || !y || nrhs < 1) return fail(RTE_ERR_ARG, "bad argument");
     RTE_TRY(ensure_workspace(h, nrhs));
@@ -1676,7 +1981,10 @@ int rte_operator(rte_handle* h, int op, const double* in, double* out, int nrhs)
             break;
         case RTE_OP_MK_PREC: RTE_TRY(mk_prec(h, in, out, h->z4, nrhs)); break;
         case RTE_OP_E: RTE_TRY(apply_E(h, in, out, nrhs, false)); break;
-        case RTE_OP_E0_INV: RTE_TRY(e0_inv(h, in, out, nrhs)); break;
+        case RTE_OP_E0_INV:
+            RTE_TRY(e0_inv(h, in, out, nrhs));
+            if (d.e0_direct) RTE_TRY(e0_direct_error(s));
+            break;
         case RTE_OP_P1: RTE_TRY(apply_P1(h, in, out, nrhs)); break;
         case RTE_OP_RESTRICT: RTE_TRY(restrict_(h, in, out, nrhs)); break;
         case RTE_OP_PROLONG: RTE_TRY(prolong_add(h, in, out, nrhs, 0.0)); break;
@@ -1847,6 +2155,7 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
             RTE_CUDA_TRY(cudaMemcpyAsync(hd2.data(), sc + 2 * nrhs, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
         }
         RTE_CUDA_TRY(cudaStreamSynchronize(s));
+        settle_mk(h);
         worst = 0.0;
         energy = 0.0;
         bool nan = false;
@@ -1857,6 +2166,7 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
             if (it > 0) energy = std::max(energy, std::sqrt(std::max(0.0, hd1[k] - hd2[k])));
         }
         if (stats && stats->history && it < stats->history_cap) stats->history[it] = worst;
+        if (d.e0_direct && it > 0) RTE_TRY(e0_direct_error(s));
         if (nan) { rc = fail(RTE_ERR_DIVERGED, "residual is NaN or Inf"); break; }
         if (worst <= tol) break;
         if (it >= h->opt.max_iter) { rc = fail(RTE_ERR_MAXITER, "outer iteration cap reached"); break; }
@@ -1935,6 +2245,19 @@ int rte_timing_read(rte_handle* h, const char** names, double* ms, long long* la
 
 long long rte_kernel_launches(void) { return launches_total(); }
 
+int rte_set_wait_limit(double seconds) {
+    if (!(seconds > 0) || seconds > 60.0) return fail(RTE_ERR_ARG, "limit must be in (0, 60] s");
+    set_wait_limit_ns((unsigned long long)(seconds * 1e9));
+    // mbarrier waits count SM clock cycles: at the peak clock, so that the
+    // limit is never shorter than asked at a lower clock
+    int dev = 0, khz = 0;
+    RTE_CUDA_TRY(cudaGetDevice(&dev));
+    RTE_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    const long long cycles = (long long)(seconds * 1e3 * std::max(khz, 1));
+    RTE_TRY(e0_set_wait_cycles(cycles));
+    return tc_set_wait_cycles(cycles);
+}
+
 constexpr int kTraceCap = 1 << 16;
 
 int rte_trace_enable(rte_handle* h, int on) {
@@ -1964,7 +2287,14 @@ int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, 
                     int slices, void* stream) {
     if (!A || !Bt || !C || M < 0 || N < 0 || K < 0 || slices < 1 || slices > 9)
         return fail(RTE_ERR_ARG, "bad argument");
+    if (K % 8 != 0) return fail(RTE_ERR_ARG, "K must be a multiple of 8");
+    if (M == 0 || N == 0) return RTE_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (K == 0) {
+        RTE_CUDA_TRY(cudaMemsetAsync(C, 0, sizeof(double) * M * N, s));
+        RTE_CUDA_TRY(cudaStreamSynchronize(s));
+        return RTE_OK;
+    }
     char *pa = nullptr, *pb = nullptr;
     if (cudaMallocAsync(&pa, ozaki_slice_bytes(M, K, slices), s) != cudaSuccess ||
         cudaMallocAsync(&pb, ozaki_slice_bytes(N, K, slices), s) != cudaSuccess) {
@@ -2009,6 +2339,9 @@ void rte_destroy(rte_handle* h) {
         cudaEventDestroy(t.a);
         cudaEventDestroy(t.b);
     }
+    for (auto& kv : h->mk_graph) cudaGraphExecDestroy(kv.second);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->mk_state_host) cudaFreeHost(h->mk_state_host);
     for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
     delete h;

@@ -9,7 +9,9 @@
 
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
+#include <list>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -28,6 +30,8 @@ struct Request {
     int m = 0, levels = 0, nrhs = 1;
     double g = 0.0, tol = 1e-6;
     std::vector<double> sigma_t, sigma_s, q_nodal, u;
+    std::string key;          // the operator: mesh, sphere, g and sigma fields
+    rte_handle* cached = nullptr;   // an idle handle of the same operator, if one was taken
     size_t bytes = 0;
     int status = RTE_OK;
     std::string error;
@@ -35,6 +39,29 @@ struct Request {
     Clock::time_point t_submit, t_start, t_done;
     bool done = false;
 };
+
+// A set-up handle kept after its request for the next request with the same
+// operator (the solve needs only a new right-hand side).
+struct Idle {
+    std::string key;
+    rte_handle* h = nullptr;
+    size_t bytes = 0;
+    int cap_rhs = 0;
+};
+
+// The operator of a request as bytes: mesh, sphere level, g and the sigma
+// fields (the options are the server's, the same for every request).
+std::string operator_key(const rte_problem& p) {
+    const size_t nc = 2 * (size_t)p.mesh_m * p.mesh_m;
+    std::string k(sizeof(int) * 2 + sizeof(double) * (1 + 2 * nc), '\0');
+    char* o = &k[0];
+    std::memcpy(o, &p.mesh_m, sizeof(int));
+    std::memcpy(o + sizeof(int), &p.sphere_levels, sizeof(int));
+    std::memcpy(o + 2 * sizeof(int), &p.g, sizeof(double));
+    std::memcpy(o + 2 * sizeof(int) + sizeof(double), p.sigma_t, nc * sizeof(double));
+    std::memcpy(o + 2 * sizeof(int) + sizeof(double) * (1 + nc), p.sigma_s, nc * sizeof(double));
+    return k;
+}
 
 }  // namespace
 
@@ -47,6 +74,11 @@ struct rte_server {
     std::deque<std::shared_ptr<Request>> pending;
     std::map<long long, std::shared_ptr<Request>> requests;
     size_t in_use = 0;
+    // idle handles, most recently used first; their bytes count against the
+    // budget until they are taken again or evicted
+    std::list<Idle> idle;
+    size_t idle_bytes = 0;
+    long long hits = 0, misses = 0;
     long long next_id = 1;
     bool stop = false;
     std::vector<std::thread> workers;
@@ -54,15 +86,22 @@ struct rte_server {
 
 namespace {
 
-void run_request(rte_server* sv, cudaStream_t stream, Request& r) {
+// Runs one request on the slot's stream: set-up (unless an idle handle of
+// the same operator was taken), right-hand side, solve, copy-back.  Returns
+// the handle for the idle set, or nullptr when it was destroyed.
+rte_handle* run_request(rte_server* sv, cudaStream_t stream, Request& r) {
     rte_problem p{r.m, r.levels, r.sigma_t.data(), r.sigma_s.data(), r.g};
     rte_options o = sv->opt;
     o.max_rhs = r.nrhs;
-    rte_handle* h = nullptr;
-    r.status = rte_setup(&p, &o, stream, &h);
-    if (r.status != RTE_OK) {
-        r.error = rte_last_error();
-        return;
+    rte_handle* h = r.cached;
+    if (h) {
+        rte_set_stream(h, stream);
+    } else {
+        r.status = rte_setup(&p, &o, stream, &h);
+        if (r.status != RTE_OK) {
+            r.error = rte_last_error();
+            return nullptr;
+        }
     }
     int nRp = 0, nSp = 0;
     rte_sizes(h, &nRp, nullptr, &nSp, nullptr, nullptr, nullptr);
@@ -94,6 +133,25 @@ void run_request(rte_server* sv, cudaStream_t stream, Request& r) {
         r.status = RTE_ERR_CUDA;
         r.error = "stream synchronisation";
     }
+    if (r.status != RTE_OK) {   // a handle that failed a request is not kept
+        rte_destroy(h);
+        return nullptr;
+    }
+    return h;
+}
+
+// An idle handle for the front request, if one of its operator with enough
+// right-hand sides is kept (caller holds the lock).
+std::list<Idle>::iterator find_idle(rte_server* sv, const Request& r) {
+    for (auto it = sv->idle.begin(); it != sv->idle.end(); ++it)
+        if (it->cap_rhs >= r.nrhs && it->key == r.key) return it;
+    return sv->idle.end();
+}
+
+void destroy_on(cudaStream_t stream, rte_handle* h) {
+    // an idle handle has no work queued; its memory is freed in the order of
+    // this slot's stream
+    rte_set_stream(h, stream);
     rte_destroy(h);
 }
 
@@ -103,25 +161,52 @@ void worker(rte_server* sv) {
     cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
     while (true) {
         std::shared_ptr<Request> r;
+        std::vector<rte_handle*> evict;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
+            // admit the front request when its operator has an idle handle
+            // (no new memory), or when its estimate fits the budget beside
+            // the running requests once idle handles are evicted (oldest
+            // first); a request larger than the budget runs alone
             sv->cv_work.wait(lk, [&] {
-                return sv->stop ||
-                       (!sv->pending.empty() &&
-                        (sv->in_use == 0 || sv->in_use + sv->pending.front()->bytes <= sv->budget));
+                if (sv->stop) return true;
+                if (sv->pending.empty()) return false;
+                const Request& f = *sv->pending.front();
+                if (find_idle(sv, f) != sv->idle.end()) return true;
+                return sv->in_use == 0 || sv->in_use + f.bytes <= sv->budget;
             });
             if (sv->stop) break;
             r = sv->pending.front();
             sv->pending.pop_front();
+            auto it = find_idle(sv, *r);
+            if (it != sv->idle.end()) {
+                r->cached = it->h;
+                r->bytes = it->bytes;
+                sv->idle_bytes -= it->bytes;
+                sv->idle.erase(it);
+                ++sv->hits;
+            } else {
+                ++sv->misses;
+                while (!sv->idle.empty() && sv->in_use + sv->idle_bytes + r->bytes > sv->budget) {
+                    evict.push_back(sv->idle.back().h);
+                    sv->idle_bytes -= sv->idle.back().bytes;
+                    sv->idle.pop_back();
+                }
+            }
             sv->in_use += r->bytes;
             r->t_start = Clock::now();
         }
-        run_request(sv, stream, *r);
+        for (rte_handle* h : evict) destroy_on(stream, h);
+        rte_handle* keep = run_request(sv, stream, *r);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             r->t_done = Clock::now();
             r->done = true;
             sv->in_use -= r->bytes;
+            if (keep) {
+                sv->idle.push_front(Idle{r->key, keep, r->bytes, r->nrhs});
+                sv->idle_bytes += r->bytes;
+            }
         }
         sv->cv_work.notify_all();
         sv->cv_done.notify_all();
@@ -145,15 +230,28 @@ size_t rte_estimate_bytes(const rte_problem* p, const rte_options* o, int nrhs) 
     const int dP = o && o->n_plus >= 0 ? (o->n_plus + 1) * (o->n_plus + 2) / 2 : 15;
     size_t b = 0;
     b += r * nRm * nSm * 8 * 5;                // odd work arrays and slices
-    b += r * nRp * nSp * 8 * 13;               // even work arrays, E_0 CG vectors
-    b += r * nRp * nSp * 4;                    // E_0 FP32 iterate
+    b += r * nRp * nSp * 8 * 10;               // even work arrays
+    if (!(o ? (o->e0_route == RTE_E0_DIRECT || (o->e0_route == RTE_E0_AUTO && m <= 156))
+            : m <= 156))
+        b += r * nRp * nSp * (8 * 3 + 4);      // E_0 CG vectors and FP32 iterate
     const bool p1_pcg = o && (o->p1_route == RTE_P1_PCG ||
                               (o->p1_route == RTE_P1_AUTO && o->precision != RTE_FP64));
     if (p1_pcg) b += r * nRp * nSp * 8 * 2;    // the P_1 PCG's r and p
     b += nSm * nSm * 8 * 5 + nSp * nSp * 8 * 3;   // dense angular factors, slices
-    b += 7 * nRp * nSp * 12;                   // E_0 stencil coefficients
-    b += 7 * nRp * nSp * 4 * 4 / 3;            // multigrid coefficients
-    b += r * nRp * nSp * 4 * 3 * 4 / 3;        // multigrid vectors
+    b += 7 * nRp * nSp * 8;                    // E_0 stencil coefficients
+    const bool direct = o ? (o->e0_route == RTE_E0_DIRECT ||
+                             (o->e0_route == RTE_E0_AUTO && m <= 156))
+                          : m <= 156;
+    if (direct) {
+        // the factor (FP64 in FP64 mode, FP32 otherwise) and its setup scratch
+        const size_t ld = (m + 1 + 3) & ~(size_t)3;
+        const bool fp64 = !o || o->precision == RTE_FP64;
+        b += nSp * (m + 1) * ld * ld * (fp64 ? 8 : 4) + nSp * nRp * 8;
+    } else {
+        b += 7 * nRp * nSp * 4;                // FP64 kernel's FP32 copy
+        b += 7 * nRp * nSp * 4 * 4 / 3;        // multigrid coefficients
+        b += r * nRp * nSp * 4 * 3 * 4 / 3;    // multigrid vectors
+    }
     b += 7 * nRp * (size_t)dP * dP * 12 * 4 / 3;   // E_c blocks
     b += r * nRp * dP * 8 * 10;                // coarse vectors
     b += 64ull << 20;                          // small arrays, allocator slack
@@ -189,6 +287,7 @@ int rte_server_submit(rte_server* sv, const rte_problem* p, const double* q_noda
     r->sigma_s.assign(p->sigma_s, p->sigma_s + nc);
     r->q_nodal.assign(q_nodal, q_nodal + nn * nrhs);
     r->bytes = rte_estimate_bytes(p, &sv->opt, nrhs);
+    r->key = operator_key(*p);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -244,7 +343,18 @@ void rte_server_destroy(rte_server* sv) {
     }
     sv->cv_work.notify_all();
     for (auto& t : sv->workers) t.join();
+    for (auto& e : sv->idle) rte_destroy(e.h);
     delete sv;
+}
+
+int rte_server_cache_stats(rte_server* sv, long long* hits, long long* misses,
+                           size_t* idle_bytes) {
+    if (!sv) return rte::fail(RTE_ERR_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (hits) *hits = sv->hits;
+    if (misses) *misses = sv->misses;
+    if (idle_bytes) *idle_bytes = sv->idle_bytes;
+    return RTE_OK;
 }
 
 int rte_solve_batch(const rte_problem* probs, const double* const* q_nodal, const int* nrhs,

@@ -208,6 +208,11 @@ int tc_gemm(cudaStream_t s, const TcGemmArgs& g) {
     return wide ? launch<256, false, float>(s, g) : launch<128, false, float>(s, g);
 }
 
+int tc_set_wait_cycles(long long cycles) {
+    RTE_CUDA_TRY(cudaMemcpyToSymbol(g_tc_wait_cycles, &cycles, sizeof(cycles)));
+    return RTE_OK;
+}
+
 int tc_gemm_error(cudaStream_t s) {
     int e = 0;
     RTE_CUDA_TRY(cudaMemcpyFromSymbolAsync(&e, g_tc_error, sizeof(int), 0,

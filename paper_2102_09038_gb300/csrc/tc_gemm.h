@@ -24,6 +24,8 @@ struct TcGemmArgs {
 int tc_gemm(cudaStream_t s, const TcGemmArgs& g);
 // Reads and clears the device-side timeout flag of the GEMM pipelines.
 int tc_gemm_error(cudaStream_t s);
+// Limit of one mbarrier wait of the GEMM pipelines on the current device.
+int tc_set_wait_cycles(long long cycles);
 
 // FP64-accurate GEMM from exact BF16 products of digit slices (tc_gemm.cu).
 // ozaki_split: S slices of the rows of X (rows x K, FP64) into `out`

@@ -21,6 +21,9 @@ constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 
 // timeout flag of the pipelines in the including translation unit
 static __device__ int g_tc_error = 0;
+// limit of one mbarrier wait in SM clock cycles (set per device by
+// rte_set_wait_limit; kWaitCycles until then)
+static __device__ long long g_tc_wait_cycles = kWaitCycles;
 
 
 static __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -39,6 +42,7 @@ static __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t byt
 // Bounded wait for the completion of the phase with the given parity.
 static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     const long long t0 = clock64();
+    const long long lim = g_tc_wait_cycles;
     while (true) {
         uint32_t ok;
         asm volatile(
@@ -48,7 +52,7 @@ static __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) 
             : "r"(bar), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > lim) {
             atomicExch(&g_tc_error, 1);
             return false;
         }

@@ -80,6 +80,48 @@ def test_config3_precision_2048_triangles():
     assert oracle_residual(p, u16) <= 1.05e-8
 
 
+# The FP64 arm with the mixed modes' algorithm (P_1 as PCG steps, inner
+# tolerances 0.3 / 0.1, FP64-accurate split GEMMs): the reference solutions
+# below, and the FP64 solution at the same tolerance as the mixed ones.
+FP64_MATCHED = dict(precision=0, dgemm=2, p1_route=1, e0_tol=0.3, coarse_tol=0.1)
+
+ERROR_CASES = {
+    'config2': lambda: workloads.checkerboard(m=128, levels=3, g=0.9, ratio=0.99, seed=0),
+    'config3_g0.80': lambda: workloads.precision_case(g=0.8),
+    'config3_g0.95': lambda: workloads.precision_case(g=0.95),
+    'config4_inst0': lambda: workloads.batch_instances(64, seed=0)[0],
+    'config4_inst3': lambda: workloads.batch_instances(64, seed=0)[3],
+}
+
+
+@pytest.mark.parametrize('case', sorted(ERROR_CASES))
+def test_error_vs_fp64_at_the_benchmark_tolerance(case):
+    """The mixed solutions at the benchmark's tolerance 1e-6 against an FP64
+    reference solved to 1e-11 (certified by its residual in the oracle's
+    operator): the relative L2 error is at most 1e-6 (FP32) and 1e-4 (BF16
+    scattering).  Where FP32 misses 1e-6, the FP64 solution at the same
+    tolerance misses it as well (the tolerance, not the precision, sets the
+    error) and tolerance 1e-7 meets it.  Measured (multigrid E_0 route):
+    errors at 1e-6 of 1.6e-7 (128 x 128), 1.9e-7 (2048 triangles, g = 0.8),
+    1.19e-6 in every precision at g = 0.95, c = 0.999 (1.05e-7 at 1e-7), and
+    2e-9 to 8e-7 for the batching instances; the mixed and FP64 errors agree
+    to two or three digits."""
+    p = ERROR_CASES[case]()
+    uref, iref = gpu_solve(p, 1e-11, **FP64_MATCHED)
+    assert oracle_residual(p, uref) <= 1e-10
+    u64, _ = gpu_solve(p, 1e-6, **FP64_MATCHED)
+    u32, _ = gpu_solve(p, 1e-6, precision=1)
+    u16, _ = gpu_solve(p, 1e-6, precision=2)
+    e64, e32, e16 = relerr(u64, uref), relerr(u32, uref), relerr(u16, uref)
+    assert e16 <= 1e-4, (e64, e32, e16)
+    if e32 > 1e-6:
+        # the tolerance, not the precision, sets the error: FP64 at the same
+        # tolerance is as far off, and a tenfold tighter one meets the bound
+        assert e64 >= 0.9 * e32, (e64, e32)
+        u32, _ = gpu_solve(p, 1e-7, precision=1)
+        assert relerr(u32, uref) <= 1e-6
+
+
 def test_config4_uneven_batch_with_odd_meshes():
     # instances of the batching configuration (meshes 32..128, odd ones
     # included, 128/512 triangles, 1-8 right-hand sides), solved together by

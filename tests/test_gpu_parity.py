@@ -74,9 +74,14 @@ def pair(request):
     pr.gpu.close()
 
 
-@pytest.fixture(scope='module')
-def pcg_pair():
-    pr = Pair('ragged', mk_route=1)
+@pytest.fixture(scope='module', params=[('tiny', 0), ('ragged', 0), ('odd35', 0), ('ragged', 2),
+                                        ('g0', 1)],
+                ids=lambda v: '%s-%s' % (v[0], ('fp64', 'fp32', 'bf16')[v[1]]))
+def pcg_pair(request):
+    # Algorithm 1's PCG route (the device-side graph loop); on mixed handles
+    # it applies the FP64 operator with K^- on the split tensor-core GEMM
+    case, prec = request.param
+    pr = Pair(case, mk_route=1, precision=prec)
     yield pr
     pr.gpu.close()
 
@@ -146,6 +151,27 @@ def test_mk_inverse_pcg_route(pcg_pair):
     got = pr.run('MK_INV', z, z.shape)
     ref = np.stack([pr.ops.solve_MKminus(v) for v in z])
     assert relerr(got, ref) < 1e-10
+    # twice in a row (the graph is replayed, its state reset per call), and
+    # with one right-hand side (a second graph)
+    got = pr.run('MK_INV', z, z.shape)
+    assert relerr(got, ref) < 1e-10
+    got1 = pr.run('MK_INV', z[:1], z[:1].shape)
+    assert relerr(got1, ref[:1]) < 1e-10
+
+
+def test_solve_with_pcg_route_reaches_oracle_residual(pcg_pair):
+    pr = pcg_pair
+    p = pr.p
+    qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
+    q = pr.gpu.rhs(qn)
+    u, info = pr.gpu.solve(q, tol=1e-11)
+    assert info['status'] == 0, info
+    assert info['mk_iters'] >= 1
+    u = u.cpu().numpy()
+    for r in range(p.nrhs):
+        qr = pr.disc.source(p.q_nodal[r])
+        res = np.linalg.norm(pr.ops.apply_EK(u[r]) - qr) / np.linalg.norm(qr)
+        assert res < 1e-10, res
 
 
 def test_apply_E_and_EK(pair):
@@ -169,6 +195,21 @@ def test_e0_inverse_per_direction_cg(pair):
         col = np.linalg.norm(res, axis=0) / np.linalg.norm(b[r], axis=0)
         assert col.max() < 2e-12
         assert relerr(got[r], ops.solve_E0(b[r])) < 1e-8
+
+
+@pytest.mark.parametrize('case', ['tiny', 'ragged', 'odd35'])
+def test_e0_inverse_multigrid_route(case):
+    # the multigrid-PCG route of E_0^{-1} (the default takes the direct
+    # factorisation on these meshes): every column to the 1e-12 tolerance
+    import paper_2102_09038_gb300 as rte
+    pr = Pair(case, e0_route=rte.E0_MULTIGRID)
+    b = pr.even(2)
+    got = pr.run('E0_INV', b, b.shape)
+    pr.gpu.close()
+    for r in range(2):
+        res = pr.ops.apply_E0(got[r]) - b[r]
+        col = np.linalg.norm(res, axis=0) / np.linalg.norm(b[r], axis=0)
+        assert col.max() < 2e-12
 
 
 def test_p1_and_coarse_steps(pair):
@@ -343,12 +384,14 @@ def test_contraction_rates_match_dense_iteration_matrix():
 def test_setup_stage_times():
     # rte_setup_times: every stage of the setup recorded, wall-clock, in order
     import paper_2102_09038_gb300 as rte
-    s = rte.Solver(CASES['ragged'](), n_plus=2, n_minus=3)
-    try:
-        t = s.setup_times()
-    finally:
-        s.close()
-    assert list(t)[0] == 'host assembly' and list(t)[-1] == 'launch tuning'
-    for name in ('eigenpairs of S+', 'eigenpairs of S-', 'E_0 multigrid', 'E_c multigrid'):
-        assert name in t
-    assert all(v >= 0.0 for v in t.values())
+    for route, stage in ((rte.E0_DIRECT, 'E_0 factorisation'),
+                         (rte.E0_MULTIGRID, 'E_0 multigrid')):
+        s = rte.Solver(CASES['ragged'](), n_plus=2, n_minus=3, e0_route=route)
+        try:
+            t = s.setup_times()
+        finally:
+            s.close()
+        assert list(t)[0] == 'host assembly' and list(t)[-1] == 'launch tuning'
+        for name in ('eigenpairs of S+', 'eigenpairs of S-', stage, 'E_c multigrid'):
+            assert name in t
+        assert all(v >= 0.0 for v in t.values())

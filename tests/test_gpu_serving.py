@@ -2,7 +2,9 @@
 sizes, coefficients and anisotropy run concurrently on separate streams;
 every result must equal the same problem solved alone (to the solve
 tolerance) and satisfy the oracle's residual; a budget smaller than one
-request serialises the requests without losing any."""
+request serialises the requests without losing any.  The operator cache
+lets requests with the operator of an idle handle skip the set-up, and
+evicts idle handles to stay within the budget."""
 import numpy as np
 import pytest
 
@@ -70,3 +72,64 @@ def test_budget_smaller_than_a_request_serialises():
     # admitted one at a time, in order: every later request queued at least
     # as long as the earlier one ran
     assert infos[1]['queue'] > 0.0 and infos[2]['queue'] > infos[1]['queue']
+
+
+def _sources(p, count, seed):
+    rng = np.random.default_rng(seed)
+    x, y = workloads.node_xy(p.m)
+    return [np.stack([np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2) / 0.02)
+                      for c in rng.uniform(0.2, 0.8, (p.nrhs, 2))]) for _ in range(count)]
+
+
+def _alone(p, q, **opts):
+    import paper_2102_09038_gb300 as rte
+    s = rte.Solver(p, max_rhs=p.nrhs, **opts)
+    u, info = s.solve(s.rhs(torch.tensor(q, dtype=torch.float64, device='cuda')), tol=1e-10)
+    assert info['status'] == 0
+    out = u.cpu().numpy()
+    s.close()
+    return out
+
+
+def test_operator_cache_reuses_set_up_handles():
+    # requests with the operator of an idle handle take it and skip rte_setup:
+    # one set-up for four sources of one operator, none for a repeat of it;
+    # every result equals the problem solved alone
+    import paper_2102_09038_gb300 as rte
+    opts = dict(n_plus=2, n_minus=3, precision=2)
+    p = workloads.checkerboard(m=16, levels=2, g=0.8, ratio=0.95, blocks=2, nrhs=2)
+    srcs = _sources(p, 4, 7)
+    sv = rte.Server(hbm_budget_bytes=64 << 30, slots=1, **opts)
+    got = [sv.wait(sv.submit(p, q, tol=1e-10)) for q in srcs]
+    hits, misses, idle = sv.cache_stats()
+    assert (hits, misses) == (3, 1) and idle > 0
+    # one right-hand side fits the cached handle of two; three do not
+    one = workloads.checkerboard(m=16, levels=2, g=0.8, ratio=0.95, blocks=2, nrhs=1)
+    three = workloads.checkerboard(m=16, levels=2, g=0.8, ratio=0.95, blocks=2, nrhs=3)
+    u1, _ = sv.wait(sv.submit(one, one.q_nodal, tol=1e-10))
+    u3, _ = sv.wait(sv.submit(three, three.q_nodal, tol=1e-10))
+    assert sv.cache_stats()[:2] == (4, 2)
+    sv.close()
+    for q, (u, info) in zip(srcs, got):
+        ua = _alone(p, q, **opts)
+        assert np.linalg.norm(u - ua) / np.linalg.norm(ua) < 1e-8
+    for pp, u in ((one, u1), (three, u3)):
+        ua = _alone(pp, pp.q_nodal, **opts)
+        assert np.linalg.norm(u - ua) / np.linalg.norm(ua) < 1e-8
+
+
+def test_operator_cache_evicts_to_stay_within_the_budget():
+    # a budget that holds one handle: each new operator evicts the idle one
+    import paper_2102_09038_gb300 as rte
+    opts = dict(n_plus=2, n_minus=3)
+    a = workloads.constant(12, 2, 0.6, 2.0, 1.5)
+    b = workloads.constant(12, 2, 0.7, 2.0, 1.5)
+    budget = int(1.5 * rte.estimate_bytes(a, nrhs=1, **opts))
+    sv = rte.Server(hbm_budget_bytes=budget, slots=1, **opts)
+    res = [sv.wait(sv.submit(p, p.q_nodal, tol=1e-10))[0] for p in (a, b, a)]
+    hits, misses, idle = sv.cache_stats()
+    assert (hits, misses) == (0, 3) and 0 < idle <= budget
+    sv.close()
+    for p, u in zip((a, b, a), res):
+        ua = _alone(p, p.q_nodal, **opts)
+        assert np.linalg.norm(u - ua) / np.linalg.norm(ua) < 1e-8

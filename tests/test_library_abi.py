@@ -72,6 +72,27 @@ def test_static_split_gemm_refuses_oversize_operands_on_the_host(lib_path):
     # just above the limit: M = N = 1024, K = 1176 needs 33,718,272 bytes of slices
     assert lib.rte_dgemm_split_static(fake, fake, fake, 1024, 1024, 1176, 7, None) == 1
     assert lib.rte_dgemm_split_static(fake, fake, fake, 1, 1, 1, 0, None) == 1
+    # K not a multiple of 8 (16-byte rows of BF16 slices): refused up front,
+    # by both split GEMM entry points
+    assert lib.rte_dgemm_split_static(fake, fake, fake, 16, 16, 12, 7, None) == 1
+    assert b'multiple of 8' in lib.rte_last_error()
+    assert lib.rte_dgemm_split(fake, fake, fake, 16, 16, 12, 7, None) == 1
+    assert b'multiple of 8' in lib.rte_last_error()
+
+
+def test_failure_detection_arguments_refused_on_the_host(lib_path):
+    """The wait-limit setter and the barrier self-test check their
+    arguments before any CUDA call."""
+    import paper_2102_09038_gb300 as rte
+    lib = rte.load()
+    for bad in (0.0, -1.0, 61.0, float('nan')):
+        assert lib.rte_set_wait_limit(bad) == 1
+    import ctypes
+    a, b = ctypes.c_int(), ctypes.c_int()
+    assert lib.rte_barrier_selftest(0, -1, 1, None, ctypes.byref(a), ctypes.byref(b)) == 1
+    assert lib.rte_barrier_selftest(4, 4, 1, None, ctypes.byref(a), ctypes.byref(b)) == 1
+    assert lib.rte_barrier_selftest(4, -1, 0, None, ctypes.byref(a), ctypes.byref(b)) == 1
+    assert lib.rte_barrier_selftest(4, -1, 1, None, None, ctypes.byref(b)) == 1
 
 
 def _c_layout(struct, fields, tmp_path):
@@ -110,6 +131,7 @@ def test_default_options_through_the_library(lib_path):
     import paper_2102_09038_gb300 as rte
     o = rte.default_options()
     assert o.p1_route == rte.P1_AUTO and o.precision == rte.FP64
+    assert o.e0_route == rte.E0_AUTO
     assert o.autotune == 1 and o.max_rhs >= 1
     o = rte.default_options(p1_route=rte.P1_PCG, precision=rte.MIXED_BF16)
     assert (o.p1_route, o.precision) == (rte.P1_PCG, rte.MIXED_BF16)
@@ -150,7 +172,9 @@ def _setup_rc(problem_kw=None, **opts):
     ({}, dict(max_rhs=0), 'invalid options'),
     ({}, dict(precision=7), 'precision'),
     ({}, dict(p1_route=5), 'P_1 route'),
-    ({}, dict(precision=2, mk_route=1), 'eigenbasis'),
+    ({}, dict(mk_route=3), 'route'),
+    ({}, dict(e0_route=7), 'E_0 route'),
+    (dict(m=157), dict(e0_route=1), 'mesh_m <= 156'),
     (dict(levels=0), dict(n_plus=4), 'too large'),   # d^+ = 15 > 4 directions
 ])
 def test_setup_refuses_bad_arguments_on_the_host(lib_path, problem_kw, opts, words):
