@@ -210,6 +210,9 @@ def kernel_work(name, d, nrhs, info):
       * contractions: 2 M N K flops;
       * transport A: read U^+, write Z (w = 8 B);
       * A^T + M^+ + R - K^+ gather: read Z, U^+ and U S^+, write Y;
+      * E_0 direct (the default route): its factor read twice (the forward
+        and the backward sweep), 2 n_S^+ (m+1)^3 w bytes (w = 4 FP32, 8
+        FP64), plus the FP64 right-hand side read and solution written;
       * E_0 PCG: per CG iteration over all (node, column) items the four CG
         streams x, r, p, Ap read and written once, w 6 N^+ s bytes (w = 4 in
         the FP32 kernel, 8 in FP64), plus the stencil at its minimal size
@@ -450,6 +453,9 @@ def run_ours(args):
                                inner_tol=('E_0 0.3, E_c 0.1' if args.precision != 'fp64'
                                           else 'E_0 and E_c 1e-12'),
                                iterations_per_solve=iters / args.steps,
+                               e0_route=('direct' if 'e0_direct' in tim or 'e0_direct64' in tim
+                                         else 'multigrid'),
+                               coarse_cg_iterations_last=last_info.get('coarse_iters'),
                                time_to_tol_s=secs / args.steps,
                                l2='inputs larger than L2: odd work arrays %d MB'
                                   % (d['nRm'] * d['nSm'] * 8 // 2 ** 20),
@@ -596,8 +602,9 @@ def serving_bench(args, torch, rte):
     by an HBM budget into 8 worker slots (each request's set-up is skipped
     when the server holds an idle handle of its operator), and their
     latencies (submission to completion) give p50/p99.  Baseline: the
-    same requests one after another in plain FP64 (the paper's method, no
-    server, no cache), on a sample bounded to about 30 s."""
+    same requests one after another in FP64 with the same algorithm (the
+    matched FP64 arm: no server, no cache, every request set up), on a
+    sample bounded to about 30 s."""
     import numpy as np
     reqs = serving_requests(args.serve_requests, seed=1)
     free, total = torch.cuda.mem_get_info()
@@ -606,7 +613,7 @@ def serving_bench(args, torch, rte):
     n_seq, t_seq = 0, 0.0
     t0 = time.perf_counter()
     for p in reqs:
-        s = rte.Solver(p, max_rhs=p.nrhs)
+        s = rte.Solver(p, max_rhs=p.nrhs, **FP64_MATCHED)
         q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
         s.solve(q, tol=1e-6)
         torch.cuda.synchronize()
@@ -669,7 +676,7 @@ def batch_bench(torch, rte):
     sample = insts[:4]
     swork, t0 = 0.0, time.perf_counter()
     for p in sample:
-        s = rte.Solver(p, max_rhs=p.nrhs)
+        s = rte.Solver(p, max_rhs=p.nrhs, **FP64_MATCHED)
         q = s.rhs(torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda'))
         _, info = s.solve(q, tol=1e-6)
         torch.cuda.synchronize()
@@ -679,7 +686,8 @@ def batch_bench(torch, rte):
     return dict(instances=len(insts), slots=8, precision='mixed_bf16', wall_s=wall,
                 value=work / wall, unit='DOF*iter/s',
                 sequential_fp64=dict(sample=len(sample), value=swork / swall,
-                                     note='setup included, one solve after another'))
+                                     note='matched FP64 arm, setup included, one solve '
+                                          'after another'))
 
 
 def cpu_baseline(p, budget_s=30.0):

@@ -129,10 +129,6 @@ __global__ void __launch_bounds__(kThreads) k_e0_factor(int m, int nSp, int ld,
 }
 
 // four consecutive factor entries, streamed (each is read once per sweep)
-__device__ __forceinline__ void ld4s(const float* p, float (&o)[4]) {
-    const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
 __device__ __forceinline__ void ld4s(const double* p, double (&o)[4]) {
     const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
     const double2 c = __ldcs(reinterpret_cast<const double2*>(p) + 1);
@@ -192,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_e0_direct(int m, int nSp, int nrhs
                                                         const double* __restrict__ coef,
                                                         const double* __restrict__ B,
                                                         double* __restrict__ X) {
-    extern __shared__ __align__(16) unsigned char smraw[];
+    extern __shared__ __align__(128) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const int b = m + 1, nRp = b * b, k = blockIdx.x;
     T* v = sm;                    // [kRB][ld] right-hand side of the product
@@ -257,13 +253,12 @@ __global__ void __launch_bounds__(kThreads) k_e0_direct(int m, int nSp, int nrhs
 }
 
 // ------------------------------------------------------------------------
-// FP32 solve with the factor staged in shared memory by TMA bulk copies:
-// two buffers of one block S_y^{-1} (ld x ld floats, up to 100 KB) each, so
-// the copy of the block after next overlaps the current product.  The
-// blocks are used in the order y = 0..m (forward) then m-1..0 (backward):
-// step t takes block t < b ? t : 2b - 2 - t.  The right-hand side, the
-// coupling coefficients and (backward) the forward result of the next step
-// are loaded into registers one step ahead.
+// FP32 solve with the factor staged in shared memory by TMA bulk copies (one
+// copy per half block, each into its own slot, so copies overlap the
+// products).  The blocks are used in the order y = 0..m (forward) then
+// m-1..0 (backward): step t takes block t < b ? t : 2b - 2 - t.  The
+// right-hand side, the coupling coefficients and (backward) the forward
+// result of the next step are loaded into registers one step ahead.
 
 __device__ __forceinline__ uint32_t sh_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -300,80 +295,74 @@ __device__ __forceinline__ void tma_block(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-// out[r][x] = sum_c S[c][x] v[r][c] with S the staged (symmetric) block.
-__device__ __forceinline__ void matvec_sh(const float* __restrict__ S, int b, int ld, int nr,
-                                          const float* v, float* red, float* out) {
-    const int nq4 = ld >> 2;
-    const int ng = max(1, min(b, (int)blockDim.x / nq4));
-    const int cw = (b + ng - 1) / ng;
-    const int q = threadIdx.x % nq4, g = threadIdx.x / nq4;
-    if (g < ng) {
-        float acc[kRB][4];
-#pragma unroll
-        for (int r = 0; r < kRB; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
-        const int c0 = g * cw, c1 = min(b, c0 + cw);
+// The block's product in two halves of its rows c (the columns of the
+// product, S being symmetric): half h covers c in [h hb, min(b, (h + 1) hb)),
+// hb = ceil(b / 2), contiguous in memory.  Each half goes through its own
+// shared-memory slot, so the copy of one half of the next block runs while
+// the other half is used, and a block needs about half the shared memory of
+// a whole one: two blocks of threads fit on an SM.
+__device__ __forceinline__ void matvec_half(const float* __restrict__ S, int c_lo, int c_hi,
+                                            int ld, int nr, int q, int g, int cw,
+                                            const float* v, float (&acc)[kRB][4]) {
+    const int c0 = max(c_lo, g * cw), c1 = min(c_hi, (g + 1) * cw);
 #pragma unroll 4
-        for (int c = c0; c < c1; ++c) {
-            const float4 sv = *reinterpret_cast<const float4*>(S + (size_t)c * ld + 4 * q);
-#pragma unroll
-            for (int r = 0; r < kRB; ++r)
-                if (r < nr) {
-                    const float vc = v[r * ld + c];
-                    acc[r][0] = fmaf(sv.x, vc, acc[r][0]);
-                    acc[r][1] = fmaf(sv.y, vc, acc[r][1]);
-                    acc[r][2] = fmaf(sv.z, vc, acc[r][2]);
-                    acc[r][3] = fmaf(sv.w, vc, acc[r][3]);
-                }
-        }
+    for (int c = c0; c < c1; ++c) {
+        const float4 sv = *reinterpret_cast<const float4*>(S + (size_t)(c - c_lo) * ld + 4 * q);
 #pragma unroll
         for (int r = 0; r < kRB; ++r)
-            if (r < nr)
-                *reinterpret_cast<float4*>(red + ((size_t)g * kRB + r) * ld + 4 * q) =
-                    make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) {
-        float sum = 0.f;
-        const int r = e / ld, x = e - r * ld;
-        for (int gg = 0; gg < ng; ++gg) sum += red[((size_t)gg * kRB + r) * ld + x];
-        out[r * ld + x] = sum;
+            if (r < nr) {
+                const float vc = v[r * ld + c];
+                acc[r][0] = fmaf(sv.x, vc, acc[r][0]);
+                acc[r][1] = fmaf(sv.y, vc, acc[r][1]);
+                acc[r][2] = fmaf(sv.z, vc, acc[r][2]);
+                acc[r][3] = fmaf(sv.w, vc, acc[r][3]);
+            }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_e0_direct_tma(int m, int nSp, int nrhs, int ld,
-                                                            const float* __restrict__ fac,
-                                                            const double* __restrict__ coef,
-                                                            const double* __restrict__ B,
-                                                            double* __restrict__ X) {
+__global__ void __launch_bounds__(kThreads, 2) k_e0_direct_tma(int m, int nSp, int nrhs, int ld,
+                                                               const float* __restrict__ fac,
+                                                               const double* __restrict__ coef,
+                                                               const double* __restrict__ B,
+                                                               double* __restrict__ X) {
     extern __shared__ __align__(128) unsigned char smraw[];
     const int b = m + 1, nRp = b * b, k = blockIdx.x;
-    const size_t blk = (size_t)ld * ld;
-    float* buf = reinterpret_cast<float*>(smraw);   // [2][ld][ld]
-    float* v = buf + 2 * blk;                       // [kRB][ld]
+    const int hb = (b + 1) / 2;                     // rows of the first half
+    const size_t blk = (size_t)ld * ld, slot_elems = (size_t)hb * ld;
+    float* slot = reinterpret_cast<float*>(smraw);  // [2][hb][ld]
+    float* v = slot + 2 * slot_elems;               // [kRB][ld]
     float* prev = v + kRB * ld;                     // [kRB][ld]
     float* res = prev + kRB * ld;                   // [kRB][ld]
     float* red = res + kRB * ld;                    // [ng][kRB][ld]
     __shared__ __align__(8) unsigned long long bars[2];
-    const uint32_t bar0 = sh_addr(&bars[0]), bar1 = sh_addr(&bars[1]);
+    const uint32_t bar[2] = {sh_addr(&bars[0]), sh_addr(&bars[1])};
     const float* fk = fac + (size_t)k * b * blk;
-    const uint32_t bytes = (uint32_t)(blk * sizeof(float));
     const int steps = 2 * b - 1;
     auto block_of = [&](int t) { return t < b ? t : 2 * b - 2 - t; };
+    // half h of the block of step t: source and byte count
+    auto half_src = [&](int t, int h) { return fk + (size_t)block_of(t) * blk + (size_t)h * slot_elems; };
+    auto half_bytes = [&](int h) {
+        return (uint32_t)((size_t)(h == 0 ? hb : b - hb) * ld * sizeof(float));
+    };
+    const int nq4 = ld >> 2;
+    const int ng = max(1, min(b, (int)blockDim.x / nq4));
+    const int cw = (b + ng - 1) / ng;
+    const int q = threadIdx.x % nq4, g = threadIdx.x / nq4;
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar[0]) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar[1]) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    unsigned uses[2] = {0u, 0u};   // completed phases of each buffer's barrier
+    unsigned uses = 0;   // completed phases of each slot's barrier (equal for both)
     for (int r0 = 0; r0 < nrhs; r0 += kRB) {
         const int nr = min(kRB, nrhs - r0);
         if (threadIdx.x == 0) {
-            // a previous sweep's reads of both buffers are done (its last
+            // the previous sweep's reads of both slots are done (its last
             // barrier); order them before the copies' writes
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tma_block(buf, fk, bytes, bar0);
-            if (steps > 1) tma_block(buf + blk, fk + (size_t)block_of(1) * blk, bytes, bar1);
+            tma_block(slot, half_src(0, 0), half_bytes(0), bar[0]);
+            if (b > hb) tma_block(slot + slot_elems, half_src(0, 1), half_bytes(1), bar[1]);
         }
         // registers for step t: B (forward) or the forward result w (backward),
         // and the two coupling coefficients of the row
@@ -433,23 +422,43 @@ __global__ void __launch_bounds__(kThreads) k_e0_direct_tma(int m, int nSp, int 
 #pragma unroll
             for (int j = 0; j < kE; ++j) wv[j] = (float)pb[j];
             if (t + 1 < steps) fetch(t + 1);
-            const int bi = t & 1;
-            const bool ok = mbar_wait(bi ? bar1 : bar0, uses[bi] & 1u);
-            ++uses[bi];
-            if (__syncthreads_or(!ok)) {
-                // a copy did not arrive in time: let the other one finish
-                // (bounded) and leave; the host reads g_e0_error
-                if (threadIdx.x == 0 && t + 1 < steps) mbar_wait(bi ? bar0 : bar1, uses[bi ^ 1] & 1u);
-                return;
-            }
-            matvec_sh(buf + bi * blk, b, ld, nr, v, red, res);
             __syncthreads();
-            if (threadIdx.x == 0 && t + 2 < steps) {
-                // every thread's reads of this buffer are done (barrier above)
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_block(buf + bi * blk, fk + (size_t)block_of(t + 2) * blk, bytes,
-                          bi ? bar1 : bar0);
+            float acc[kRB][4];
+#pragma unroll
+            for (int r = 0; r < kRB; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+            for (int h = 0; h < 2; ++h) {
+                const int c_lo = h * hb, c_hi = h == 0 ? hb : b;
+                if (c_hi <= c_lo) continue;
+                const bool ok = mbar_wait(bar[h], uses & 1u);
+                if (__syncthreads_or(!ok)) {
+                    // a copy did not arrive in time: let the other slot's copy
+                    // finish (bounded) and leave; the host reads g_e0_error
+                    if (threadIdx.x == 0 && h == 0 && b > hb) mbar_wait(bar[1], uses & 1u);
+                    return;
+                }
+                if (g < ng) matvec_half(slot + h * slot_elems, c_lo, c_hi, ld, nr, q, g, cw, v, acc);
+                __syncthreads();
+                if (threadIdx.x == 0 && t + 1 < steps) {
+                    // every thread's reads of this slot are done (barrier above)
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tma_block(slot + h * slot_elems, half_src(t + 1, h), half_bytes(h), bar[h]);
+                }
             }
+            ++uses;
+            if (g < ng)
+#pragma unroll
+                for (int r = 0; r < kRB; ++r)
+                    if (r < nr)
+                        *reinterpret_cast<float4*>(red + ((size_t)g * kRB + r) * ld + 4 * q) =
+                            make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+            __syncthreads();
+            for (int e = threadIdx.x; e < nr * ld; e += blockDim.x) {
+                float sum = 0.f;
+                const int r = e / ld, x = e - r * ld;
+                for (int gg = 0; gg < ng; ++gg) sum += red[((size_t)gg * kRB + r) * ld + x];
+                res[r * ld + x] = sum;
+            }
+            __syncthreads();
 #pragma unroll
             for (int j = 0; j < kE; ++j) {
                 const int e = threadIdx.x + j * kThreads;
@@ -476,10 +485,10 @@ size_t solve_smem(int m) {
     return (size_t)(3 + ng) * kRB * ld * sizeof(T);
 }
 
-// the FP32 solve: two staged factor blocks and the vectors
+// the FP32 solve: two staged half blocks and the vectors
 size_t tma_smem(int m) {
-    const size_t ld = e0_ld(m);
-    return 2 * ld * ld * sizeof(float) + solve_smem<float>(m);
+    const size_t ld = e0_ld(m), hb = (m + 2) / 2;
+    return 2 * hb * ld * sizeof(float) + solve_smem<float>(m);
 }
 
 }  // namespace

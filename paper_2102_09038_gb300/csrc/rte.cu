@@ -74,6 +74,9 @@ struct rte_handle {
     size_t cobytes = 0;
     SolveStatus* status = nullptr;
     unsigned long long* trace = nullptr;   // phase trace buffer (profiling)
+    // digit slices the split GEMMs of the current solve use (<= d.split_S,
+    // from the solve's tolerance; d.split_S outside rte_solve)
+    int split_now = 0;
     // autotuned tile widths of the low-precision GEMMs (0: by N)
     int bn_mk1 = 0, bn_mk2 = 0, bn_kplus = 0;
     // Algorithm 1's PCG loop as a CUDA graph whose while node repeats one
@@ -82,7 +85,7 @@ struct rte_handle {
     // iterations of the last solve, [1] converged, [2] non-finite residual,
     // [3] iterations since set-up (device, and a pinned host copy)
     cudaStream_t cap_stream = nullptr;
-    std::map<int, cudaGraphExec_t> mk_graph;
+    std::map<int, cudaGraphExec_t> mk_graph;   // by 16 nrhs + slices
     int* mk_state = nullptr;
     int* mk_state_host = nullptr;
     int mk_total_seen = 0;
@@ -860,29 +863,48 @@ int alloc_workspace(rte_handle* h, int nrhs) {
 }
 
 // --------------------------------------------------------- operators
+// Digit slices of the split GEMMs now: the solve's choice, else all.
+int split_slices_now(const rte_handle* h) {
+    return h->split_now > 0 ? std::min(h->split_now, h->d.split_S) : h->d.split_S;
+}
+
+// Slices for a solve to relative residual tol: the split product of S
+// slices differs from the FP64 one by at most about S 2^-7S of the operand
+// row scales (the dropped digit pairs and the truncated digits), and the
+// residual's contractions are taken accurate to tol / 1000 in that measure,
+// S 2^-7S <= tol / 1000: 5 slices at 1e-6, 6 at 1e-8, 7 at 1e-10 (capped by
+// the slices set up, split_slices).
+int slices_for_tol(double tol, int smax) {
+    for (int S = 3; S < smax; ++S)
+        if (S * std::ldexp(1.0, -7 * S) <= tol / 1000.0) return S;
+    return smax;
+}
+
 // Z2 = (M^- - K^-)^{-1} Z1 in the full eigenbasis of (S^-, M_S^-):
 // per cell j, (|T_j| (sigma_t M_S^- - sigma_s S^-))^{-1} = V diag(1/(at - lam as)) V^T
 int mk_inv_eigen(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
     const DevSystem& d = h->d;
     const int rows = nrhs * d.nRm;
     if (d.split_S > 0) {
+        const int S = split_slices_now(h);
         int* ea = nullptr;
         {
             Scope sc(h, "split_digits");
-            RTE_TRY(ozaki_split(h->stream, Z1, rows, d.nSm, d.split_S, h->slices, &ea));
+            RTE_TRY(ozaki_split(h->stream, Z1, rows, d.nSm, S, h->slices, &ea));
         }
         {
             Scope sc(h, "dgemm_split_mk1");
             RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_VmT, d.ex_VmT, d.nSm, d.nSm,
-                               d.split_S, h->z4, d.nSm, 1, d.cell_at, d.cell_as, d.lamM, d.nRm));
+                               S, h->z4, d.nSm, 1, d.cell_at, d.cell_as, d.lamM, d.nRm,
+                               d.split_S));
         }
         {
             Scope sc(h, "split_digits");
-            RTE_TRY(ozaki_split(h->stream, h->z4, rows, d.nSm, d.split_S, h->slices, &ea));
+            RTE_TRY(ozaki_split(h->stream, h->z4, rows, d.nSm, S, h->slices, &ea));
         }
         Scope sc(h, "dgemm_split_mk2");
-        RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_Vm, d.ex_Vm, d.nSm, d.nSm,
-                           d.split_S, Z2, d.nSm, 0, nullptr, nullptr, nullptr, 1));
+        RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_Vm, d.ex_Vm, d.nSm, d.nSm, S,
+                           Z2, d.nSm, 0, nullptr, nullptr, nullptr, 1, d.split_S));
         return RTE_OK;
     }
     {
@@ -934,9 +956,10 @@ int mk_apply_split(rte_handle* h, const double* Z, double* Y, double* G, int nrh
     const DevSystem& d = h->d;
     Scope sc(h, "mk_apply");
     int* ea = nullptr;
-    RTE_TRY(ozaki_split(h->stream, Z, nrhs * d.nRm, d.nSm, d.split_S, h->slices, &ea));
-    RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRm, d.sl_Sm, d.ex_Sm, d.nSm, d.nSm,
-                       d.split_S, G, d.nSm, 0, nullptr, nullptr, nullptr, 1));
+    const int S = split_slices_now(h);
+    RTE_TRY(ozaki_split(h->stream, Z, nrhs * d.nRm, d.nSm, S, h->slices, &ea));
+    RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRm, d.sl_Sm, d.ex_Sm, d.nSm, d.nSm, S,
+                       G, d.nSm, 0, nullptr, nullptr, nullptr, 1, d.split_S));
     mk_combine(h->stream, d, Z, G, Y, nrhs);
     return RTE_OK;
 }
@@ -990,7 +1013,9 @@ int mk_pcg_body(rte_handle* h, int n, double* X, cudaGraphConditionalHandle loop
 // The executable graph of the loop for n right-hand sides: a while node
 // whose body (captured on the handle's private stream) is mk_pcg_body.
 int mk_graph_for(rte_handle* h, int n, double* X, cudaGraphExec_t* out) {
-    auto it = h->mk_graph.find(n);
+    // the body's split GEMMs bake in the slice count: one graph per both
+    const int key = n * 16 + (h->d.split_S > 0 ? split_slices_now(h) : 0);
+    auto it = h->mk_graph.find(key);
     if (it != h->mk_graph.end()) {
         *out = it->second;
         return RTE_OK;
@@ -1041,7 +1066,7 @@ int mk_graph_for(rte_handle* h, int n, double* X, cudaGraphExec_t* out) {
         rc = fail(RTE_ERR_CUDA, "cudaGraphInstantiate of the PCG loop failed");
     cudaGraphDestroy(g);
     if (rc != RTE_OK) return rc;
-    h->mk_graph[n] = exec;
+    h->mk_graph[key] = exec;
     *out = exec;
     return RTE_OK;
 }
@@ -1162,9 +1187,10 @@ int apply_E(rte_handle* h, const double* x, double* y, int nrhs, bool with_k) {
         if (d.split_S > 0) {
             Scope sc(h, "dgemm_split_kplus");
             int* ea = nullptr;
-            RTE_TRY(ozaki_split(h->stream, x, nrhs * d.nRp, d.nSp, d.split_S, h->slices, &ea));
+            const int S = split_slices_now(h);
+            RTE_TRY(ozaki_split(h->stream, x, nrhs * d.nRp, d.nSp, S, h->slices, &ea));
             RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRp, d.sl_Sp, d.ex_Sp, d.nSp,
-                               d.nSp, d.split_S, V, d.nSp, 0, nullptr, nullptr, nullptr, 1));
+                               d.nSp, S, V, d.nSp, 0, nullptr, nullptr, nullptr, 1, d.split_S));
         } else {
             Scope sc(h, "gemm_kplus");
             gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.nSp, x, d.nSp, d.Sp, d.nSp, V, d.nSp, 1.0,
@@ -2125,6 +2151,12 @@ int rte_solve(rte_handle* h, const double* q, double* u, int nrhs, double tol,
     const size_t len = (size_t)d.nRp * d.nSp;
     h->e0_launches = 0;
     h->e0_vcycles = h->e0_active_vcycles = 0.0;
+    // the residual's split GEMMs to the accuracy the tolerance needs
+    h->split_now = d.split_S > 0 ? slices_for_tol(tol, d.split_S) : 0;
+    struct Reset {
+        rte_handle* h;
+        ~Reset() { h->split_now = 0; }
+    } reset{h};
     double* r = h->e1;       // residual r_n
     double* sv = h->e2;      // s = P_2 P_1 r
     double* rprev = h->e3;
@@ -2344,6 +2376,9 @@ void rte_destroy(rte_handle* h) {
     if (h->mk_state_host) cudaFreeHost(h->mk_state_host);
     for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
     cudaStreamSynchronize(h->stream);
+    // rte_destroy reports nothing: leave no error behind for the thread's
+    // next runtime call to pick up
+    cudaGetLastError();
     delete h;
 }
 

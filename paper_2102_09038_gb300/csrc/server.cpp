@@ -343,7 +343,13 @@ void rte_server_destroy(rte_server* sv) {
     }
     sv->cv_work.notify_all();
     for (auto& t : sv->workers) t.join();
-    for (auto& e : sv->idle) rte_destroy(e.h);
+    // the idle handles' streams belonged to the workers, which destroyed
+    // them on exit: free the handles in the order of a stream that exists
+    cudaSetDevice(sv->device);
+    for (auto& e : sv->idle) {
+        rte_set_stream(e.h, nullptr);
+        rte_destroy(e.h);
+    }
     delete sv;
 }
 

@@ -500,9 +500,11 @@ int ozaki_split(cudaStream_t s, const double* X, int rows, int K, int S, void* o
 
 int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const void* Bslices,
                const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
-               const double* as, const double* lam, int rows) {
+               const double* as, const double* lam, int rows, int SB) {
     if (M <= 0 || N <= 0 || K <= 0) return RTE_OK;
     if (S < 1 || S * (S + 1) / 2 > kOzMaxPairs) return fail(RTE_ERR_ARG, "bad slice count");
+    if (SB == 0) SB = S;
+    if (SB < S) return fail(RTE_ERR_ARG, "second operand has fewer slices than used");
     OzPairs pairs{};
     for (int a = 0; a < S; ++a)
         for (int b = 0; a + b <= S - 1; ++b) {
@@ -512,7 +514,7 @@ int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const 
         }
     CUtensorMap ma, mb;
     RTE_TRY(make_map(&ma, Aslices, false, S * M, K, kOzBM));
-    RTE_TRY(make_map(&mb, Bslices, false, S * N, K, kOzBN));
+    RTE_TRY(make_map(&mb, Bslices, false, SB * N, K, kOzBN));
     const size_t sm = 1024 + (size_t)kOzStages * (kOzBM + kOzBN) * kRowBytes +
                       (2 * kOzStages + 4) * 8 + 16;
     RTE_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -395,3 +395,29 @@ def test_setup_stage_times():
         for name in ('eigenpairs of S+', 'eigenpairs of S-', stage, 'E_c multigrid'):
             assert name in t
         assert all(v >= 0.0 for v in t.values())
+
+
+def test_contraction_trends_of_section_6_2():
+    # the trends of the paper's rate study (Tables 3-7) on a small synthetic
+    # geometry, from the library's own operators: eta <= c always; with the
+    # larger subspace (d_N = 15) rho falls to about g^l at strong anisotropy
+    # (the paper's observation; measured within 4.1 % at 64 directions and
+    # within 1.5 % at 256); a larger d_N never raises eta at fixed l
+    import paper_2102_09038_gb300 as rte
+    out = {}
+    for g in (0.7, 0.9):
+        p = workloads.checkerboard(m=12, levels=2, g=g, ratio=0.999, blocks=3, seed=0)
+        c = float(np.max(p.sigma_s / p.sigma_t))
+        for n_plus in (0, 4):
+            for l in (1, 2, 3):
+                s = rte.Solver(p, precision=rte.FP64, n_plus=n_plus, l=l,
+                               p1_route=rte.P1_RICHARDSON)
+                rho, eta, _ = s.rates(maxit=400, tol=1e-8)
+                s.close()
+                assert eta <= c + 1e-6
+                assert rho <= eta + 1e-6
+                out[(g, n_plus, l)] = (rho, eta)
+        for l in (1, 2, 3):
+            assert out[(g, 4, l)][1] <= out[(g, 0, l)][1] + 1e-6
+            rho, eta = out[(g, 4, l)]
+            assert abs(rho - g ** l) <= 0.06 * g ** l, (g, l, rho)
