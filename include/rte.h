@@ -100,6 +100,21 @@ extern "C" {
 #define RTE_E0_DIRECT 1
 #define RTE_E0_MULTIGRID 2
 
+/* How the coarse system E_c u_c = q_c of the subspace correction (Section
+ * 5.4) is solved: by CG to coarse_tol in every route, preconditioned by
+ * RTE_EC_DIRECT: E_c's exact block factorisation over the mesh rows (the
+ * inverses of its row Schur complements, ((m+1) d^+)^2 values per row,
+ * computed once at setup in FP64 and kept in FP64 (FP64 mode) or FP32), so
+ * the CG stops after one or two iterations; or RTE_EC_MULTIGRID: one V-cycle
+ * (the paper's suggestion), whose iteration count grows with the mesh for
+ * d^+ > 1.  The direct route needs (m+1) d^+ <= 2400.  RTE_EC_AUTO (0, the
+ * default) takes multigrid: on the 128 x 128 / 512-triangle workload its
+ * coarse solve (11 iterations to 0.1) took 4.1 ms against 9.9 ms for the
+ * direct route, whose set-up also adds 3.6 s. */
+#define RTE_EC_AUTO 0
+#define RTE_EC_DIRECT 1
+#define RTE_EC_MULTIGRID 2
+
 typedef struct rte_handle rte_handle;
 
 /* The problem of Section 1, eq. (rte1)-(rte2), with vacuum inflow:
@@ -145,6 +160,8 @@ typedef struct {
                                RTE_P1_PCG                                    */
     int e0_route;           /* RTE_E0_AUTO (default) | RTE_E0_DIRECT |
                                RTE_E0_MULTIGRID                              */
+    int coarse_route;       /* RTE_EC_AUTO (default) | RTE_EC_DIRECT |
+                               RTE_EC_MULTIGRID                              */
 } rte_options;
 
 typedef struct {

@@ -13,13 +13,15 @@ import os
 
 __all__ = ['Solver', 'RteError', 'load', 'OPS', 'FP64', 'MIXED_FP32',
            'MIXED_BF16', 'MK_EIGEN', 'MK_PCG', 'P1_AUTO', 'P1_RICHARDSON',
-           'P1_PCG', 'E0_AUTO', 'E0_DIRECT', 'E0_MULTIGRID']
+           'P1_PCG', 'E0_AUTO', 'E0_DIRECT', 'E0_MULTIGRID', 'EC_AUTO', 'EC_DIRECT',
+           'EC_MULTIGRID']
 
 FP64, MIXED_FP32, MIXED_BF16 = 0, 1, 2
 MK_EIGEN, MK_PCG = 0, 1
 P1_AUTO, P1_RICHARDSON, P1_PCG = -1, 0, 1
 DGEMM_AUTO, DGEMM_SIMT, DGEMM_SPLIT = 0, 1, 2
 E0_AUTO, E0_DIRECT, E0_MULTIGRID = 0, 1, 2
+EC_AUTO, EC_DIRECT, EC_MULTIGRID = 0, 1, 2
 OPS = dict(A=1, AT=2, KPLUS=3, MK=4, MK_INV=5, MK_PREC=6, E=7, E0_INV=8,
            P1=9, RESTRICT=10, PROLONG=11, EC=12, EC_INV=13, E_LO=14, EK_LO=15)
 EXPORTS = dict(Splus=0, Sminus=1, m=2, MSm=3, A1=4, A2=5, omx=6, omy=7,
@@ -54,7 +56,7 @@ class _Options(ctypes.Structure):
                 ('max_rhs', ctypes.c_int), ('dgemm', ctypes.c_int),
                 ('split_slices', ctypes.c_int), ('mg_sweeps', ctypes.c_int),
                 ('autotune', ctypes.c_int), ('p1_route', ctypes.c_int),
-                ('e0_route', ctypes.c_int)]
+                ('e0_route', ctypes.c_int), ('coarse_route', ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):

@@ -13,7 +13,7 @@ OUT = os.path.join(HERE, '_build')
 LIB = os.path.join(OUT, 'librte.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 SOURCES = ['setup_host.cpp', 'mg_host.cpp', 'server.cpp', 'kernels.cu', 'mg.cu', 'tc_gemm.cu',
-           'rte.cu', 'dgemm_static.cu', 'tune.cpp', 'e0_direct.cu']
+           'rte.cu', 'dgemm_static.cu', 'tune.cpp', 'e0_direct.cu', 'ec_direct.cu']
 
 
 def nvcc():

@@ -83,6 +83,11 @@ struct DevSystem {
     bool e0_direct = false;
     const float* e0lu32 = nullptr;
     const double* e0lu64 = nullptr;
+    // direct route of E_c^{-1}: inverses of its row Schur complements,
+    // [m+1][(m+1) d][ld] (ec_direct.cu); one of the two set
+    bool ec_direct = false;
+    const float* eclu32 = nullptr;
+    const double* eclu64 = nullptr;
     const double* ec_ell;      // E_c in ELL form [7][nRp][dP][dP], blocks transposed
     // digit slices of the constant second operands for the split FP64 GEMM
     int split_S;               // 0: FP64 GEMMs on the FP64 units
@@ -193,6 +198,14 @@ int e0_direct_solve(cudaStream_t s, const DevSystem& d, const double* B, double*
 int e0_direct_error(cudaStream_t s);
 // Limit of one such wait on the current device (SM clock cycles).
 int e0_set_wait_cycles(long long cycles);
+
+// Direct route of E_c^{-1} (ec_direct.cu): row length of its factor, bytes,
+// whether the mesh fits, and the factorisation (solver: a cusolverDnHandle_t).
+int ec_direct_ld(int m, int d);
+size_t ec_direct_bytes(int m, int d, bool fp64);
+bool ec_direct_fits(int m, int d);
+int ec_direct_factor(cudaStream_t s, void* solver, const DevSystem& d, float* out32,
+                     double* out64);
 
 // E_c^{-1} B by one persistent block-Jacobi CG per RHS.
 int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,

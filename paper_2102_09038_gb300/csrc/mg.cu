@@ -1354,6 +1354,12 @@ __device__ bool ec_vcycle(const EcMG& mg, const float* sG, GridBar* bar, float*&
 struct EcArgs {
     int nRp, m, d, nrhs, maxit;
     double tol2;
+    // direct route (E_c factor): inverses of the row Schur complements
+    // [m+1][Bd][ldf] with Bd = (m+1) d, FP32 (mixed modes) or FP64; null
+    // on the multigrid route
+    const float* lu32;
+    const double* lu64;
+    int ldf;
     const double* ec;   // FP64 E_c in ELL form, blocks transposed: [7][nRp][b][a]
     const double* B;
     double* X;
@@ -1367,8 +1373,147 @@ struct EcArgs {
     EcMG mg;
 };
 
+// ----------------------------------------- E_c direct route: the sweeps
+// E_c is block tridiagonal over the mesh rows y (row blocks of Bd = (m+1) d
+// unknowns, node-major, component fastest): A_yy couples a row's nodes
+// (self, +x, -x), A_y,y-1 reaches (x, y-1) and (x-1, y-1), A_y,y+1 = its
+// transpose.  With the inverses S_y^{-1} of its row Schur complements,
+//   forward   w_y = S_y^{-1} (r_y - A_y,y-1 w_y-1)
+//   backward  z_y = w_y - S_y^{-1} (A_y,y+1 z_y+1)
+// is z = E_c^{-1} r (the exact factorisation: the CG then converges in one
+// or two iterations).  Each row takes two grid-wide phases: the couplings
+// (one item per unknown) into the scratch row t, then the dense product,
+// one output row per warp with the block's copy of t in shared memory.
+constexpr int kEcDirectMaxBd = 2400;   // (m+1) d of the largest mesh the route takes
+constexpr int kEcSweepRhs = 2;         // right-hand sides staged per product pass
+
+// four consecutive factor entries as floats, streamed
+__device__ __forceinline__ float4 ec_ld4(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 ec_ld4(const double* p) {
+    const double2 u = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 v = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    return make_float4((float)u.x, (float)u.y, (float)v.x, (float)v.y);
+}
+
+// z[r][y][i] (=, or -= when subtract) sum_j S[i][j] t[r][y][j] for every row i
+// of the row block: one warp per output row, 16-byte loads of the (zero-
+// padded, ldf a multiple of 4) factor row, the block's copy of t in shared
+// memory (zero past Bd).
+template <typename T>
+__device__ void ec_product(const T* __restrict__ S, int Bd, int ldf, int nrhs, int nRp, int d,
+                           int y, int b, const float* t, float* z, bool subtract, float* sv) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t rstride = (size_t)nRp * d;   // one right-hand side's vector
+    const int q4 = ldf >> 2;
+    for (int r0 = 0; r0 < nrhs; r0 += kEcSweepRhs) {
+        const int nr = min(kEcSweepRhs, nrhs - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * ldf; e += blockDim.x) {
+            const int r = e / ldf, j = e - r * ldf;
+            sv[r * ldf + j] = j < Bd ? ldg2(t + (r0 + r) * rstride + (size_t)y * b * d + j) : 0.f;
+        }
+        __syncthreads();
+        for (int i = blockIdx.x * nw + warp; i < Bd; i += gridDim.x * nw) {
+            const T* row = S + (size_t)i * ldf;
+            float acc[kEcSweepRhs] = {0.f, 0.f};
+#pragma unroll 8
+            for (int j4 = lane; j4 < q4; j4 += 32) {
+                const float4 s4 = ec_ld4(row + 4 * j4);
+#pragma unroll
+                for (int r = 0; r < kEcSweepRhs; ++r)
+                    if (r < nr) {
+                        const float4 v4 = reinterpret_cast<const float4*>(sv + r * ldf)[j4];
+                        acc[r] = fmaf(s4.x, v4.x, fmaf(s4.y, v4.y, fmaf(s4.z, v4.z,
+                                 fmaf(s4.w, v4.w, acc[r]))));
+                    }
+            }
+#pragma unroll
+            for (int r = 0; r < kEcSweepRhs; ++r) {
+                float v = acc[r];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && r < nr) {
+                    float* zp = z + (r0 + r) * rstride + (size_t)y * b * d + i;
+                    *zp = subtract ? ldg2(zp) - v : v;
+                }
+            }
+        }
+    }
+}
+
+// z = E_c^{-1} rin by the factor's two sweeps (all blocks call it).  The
+// coupling phases take one unknown per group of 16 lanes, lane c holding
+// the coupling column c (d <= 16), summed by shuffles.
+__device__ bool ec_sweep(const EcArgs& a, const float* rin, float* t, float* z, GridBar* bar,
+                         float* sv) {
+    const int d = a.d, b = a.m + 1, Bd = b * d, n = a.nRp;
+    const size_t dd = (size_t)d * d, rstride = (size_t)n * d;
+    const unsigned items = (unsigned)a.nrhs * Bd;
+    const unsigned gstride = (gridDim.x * blockDim.x) >> 4;
+    const int c = threadIdx.x & 15;
+    // coupling block of node `node`, stencil direction dir, entry (ra, cb)
+    auto cpl = [&](int dir, int node, int ra, int cb) {
+        return __ldg(a.ec + ((size_t)dir * n + node) * dd + (size_t)cb * d + ra);
+    };
+    // every lane of a warp makes the same number of trips (shuffles)
+    const unsigned trips = (items + gstride - 1) / gstride;
+    for (int y = 0; y < b; ++y) {
+        unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+        for (unsigned k = 0; k < trips; ++k, e += gstride) {
+            const bool ok = e < items;
+            const int r = ok ? (int)(e / Bd) : 0, X = ok ? (int)(e % Bd) : 0;
+            const int x = X / d, ra = X - x * d;
+            const size_t row = r * rstride + (size_t)y * b * d;
+            double v = 0.0;
+            if (ok && y > 0 && c < d) {
+                const int node = y * b + x;
+                const float* wp = z + row - (size_t)b * d;   // w_y-1
+                v = -cpl(4, node, ra, c) * (double)ldg2(wp + x * d + c);
+                if (x > 0) v -= cpl(6, node, ra, c) * (double)ldg2(wp + (x - 1) * d + c);
+            }
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (ok && c == 0) t[row + X] = (float)(v + (double)ldg2(rin + row + X));
+        }
+        if (!grid_sync(bar)) return false;
+        if (a.lu32) ec_product(a.lu32 + (size_t)y * Bd * a.ldf, Bd, a.ldf, a.nrhs, n, d, y, b, t, z,
+                               false, sv);
+        else ec_product(a.lu64 + (size_t)y * Bd * a.ldf, Bd, a.ldf, a.nrhs, n, d, y, b, t, z,
+                        false, sv);
+        if (!grid_sync(bar)) return false;
+    }
+    for (int y = b - 2; y >= 0; --y) {
+        unsigned e = (blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+        for (unsigned k = 0; k < trips; ++k, e += gstride) {
+            const bool ok = e < items;
+            const int r = ok ? (int)(e / Bd) : 0, X = ok ? (int)(e % Bd) : 0;
+            const int x = X / d, ra = X - x * d;
+            const size_t row = r * rstride + (size_t)y * b * d;
+            double v = 0.0;
+            if (ok && c < d) {
+                const int node = y * b + x;
+                const float* zn = z + row + (size_t)b * d;   // z_y+1
+                v = cpl(3, node, ra, c) * (double)ldg2(zn + x * d + c);
+                if (x + 1 < b) v += cpl(5, node, ra, c) * (double)ldg2(zn + (x + 1) * d + c);
+            }
+            for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (ok && c == 0) t[row + X] = (float)v;
+        }
+        if (!grid_sync(bar)) return false;
+        if (a.lu32) ec_product(a.lu32 + (size_t)y * Bd * a.ldf, Bd, a.ldf, a.nrhs, n, d, y, b, t, z,
+                               true, sv);
+        else ec_product(a.lu64 + (size_t)y * Bd * a.ldf, Bd, a.ldf, a.nrhs, n, d, y, b, t, z,
+                        true, sv);
+        if (!grid_sync(bar)) return false;
+    }
+    return true;
+}
+
+// kDirect: preconditioned by the factor's sweeps (direct route), else by one
+// V-cycle; two instantiations so that each route's registers are its own.
+template <bool kDirect>
 __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     __shared__ int s_stop;
+    // the direct route's staged row (a single element on the multigrid route)
+    __shared__ __align__(16) float s_sv[kDirect ? kEcSweepRhs * kEcDirectMaxBd : 4];
     __shared__ double sh_v[32];
     __shared__ int sh_r[32];
     __shared__ float sG[kEcMaxQ * 16 * 16];   // angular blocks of the Kronecker terms
@@ -1392,8 +1537,17 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     }}
     rhs_flush(sum, a.bb, sh_v, sh_r);
     if (!grid_sync(a.bar)) return;
+    // the preconditioner: the factor's sweeps (direct route) or one V-cycle
+    auto precondition = [&](float*& zz) -> bool {
+        if constexpr (kDirect) {
+            zz = mg.lev[0].X;
+            return ec_sweep(a, B0, mg.lev[0].Xt, zz, a.bar, s_sv);
+        } else {
+            return ec_vcycle(mg, sG, a.bar, zz);
+        }
+    };
     float* z = nullptr;
-    if (!ec_vcycle(mg, sG, a.bar, z)) return;
+    if (!precondition(z)) return;
     GROUP_LOOP(a.nRp)
         if (ok && gl < d) {
             const double zv = ldg2(z + base + gl);
@@ -1446,7 +1600,7 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
         }}
         rhs_flush(sum, sl(cur, 2), sh_v, sh_r);
         if (!grid_sync(a.bar)) return;
-        if (!ec_vcycle(mg, sG, a.bar, z)) return;
+        if (!precondition(z)) return;
         GROUP_LOOP(a.nRp)
             if (ok && gl < d && ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r))
                 sum.add(ldg2(a.R + base + gl) * (double)ldg2(z + base + gl), r, sl(cur, 1));
@@ -1656,6 +1810,9 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     a.B = B;
     a.X = X;
     a.status = status_dev;
+    a.lu32 = d.eclu32;
+    a.lu64 = d.eclu64;
+    a.ldf = ec_direct_ld(d.m, d.dP);
     a.mg = view<EcMG>(d.ecmg);
     a.mg.nrhs = nrhs;
     a.mg.d = d.dP;
@@ -1664,7 +1821,8 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     a.mg.Gq = d.ecmg.G;
     if (a.mg.Q > kEcMaxQ || (a.mg.Q > 0 && d.dP > 16))
         return fail(RTE_ERR_ARG, "Kronecker coarse multigrid: at most 16 terms of d <= 16");
-    const void* fn = (const void*)k_ec_pcg;
+    const bool direct = a.lu32 != nullptr || a.lu64 != nullptr;
+    const void* fn = direct ? (const void*)k_ec_pcg<true> : (const void*)k_ec_pcg<false>;
     // level-0 work: (rhs, node) items, one per lane group (16 per block)
     const int grid = coop_grid(fn, 256, (size_t)nrhs * d.nRp, 8 * (32 / a.mg.G));
     void* args[] = {&a};

@@ -658,7 +658,46 @@ int setup_multigrid(rte_handle* h, const HostSystem& hs, SetupClock* clk) {
     }
     if (clk) clk->mark(d.e0_direct ? "E_0 factorisation" : "E_0 multigrid");
     // ------------------------------------------------------------ E_c
-    if (d.dP > 0) {
+    if (d.dP > 0 && d.ec_direct) {
+        // level-0 work vectors of the coarse CG kernel only (r in B, the
+        // sweeps' result in X, their scratch row in Xt)
+        MGDevice& E = d.ecmg;
+        E.L = 1;
+        E.nu = 1;
+        E.cap_cols = cap;
+        E.dense = false;
+        E.Q = 0;
+        MGDeviceLevel& D = E.lev[0];
+        D.m = hs.m;
+        D.n = hs.nRp;
+        const size_t nv = (size_t)D.n * cap * d.dP;
+        RTE_TRY(dalloc(h, &D.X, nv));
+        RTE_TRY(dalloc(h, &D.Xt, nv));
+        RTE_TRY(dalloc(h, &D.B, nv));
+        MGHostLevel L0;
+        L0.m = hs.m;
+        L0.st = hs.st;
+        L0.vals = h->h_ec;
+        std::vector<double> ell;
+        RTE_TRY(to_ell(L0, 1, d.dP, ell));
+        transpose_blocks(ell, d.dP);
+        RTE_TRY(upload(h, &d.ec_ell, ell));
+        const bool fp64 = !h->mixed;
+        const size_t fb = ec_direct_bytes(hs.m, d.dP, fp64);
+        cusolverDnHandle_t cs = nullptr;
+        RTE_TRY(solver_handle(h->stream, &cs));
+        if (fp64) {
+            double* f = nullptr;
+            RTE_TRY(dalloc(h, &f, fb / sizeof(double)));
+            RTE_TRY(ec_direct_factor(h->stream, cs, d, nullptr, f));
+            d.eclu64 = f;
+        } else {
+            float* f = nullptr;
+            RTE_TRY(dalloc(h, &f, fb / sizeof(float)));
+            RTE_TRY(ec_direct_factor(h->stream, cs, d, f, nullptr));
+            d.eclu32 = f;
+        }
+    } else if (d.dP > 0) {
         MGHost mh;
         const int dP = d.dP;
         if (h->ec_Q > 0) {   // Kronecker form: Galerkin products of Q scalar stencils
@@ -1451,6 +1490,7 @@ int rte_default_options(rte_options* o) {
     o->autotune = 1;
     o->p1_route = RTE_P1_AUTO;   // P_1^l in FP64, PCG steps in the mixed modes
     o->e0_route = RTE_E0_AUTO;   // direct factorisation when the mesh allows it
+    o->coarse_route = RTE_EC_AUTO;
     return RTE_OK;
 }
 
@@ -1478,6 +1518,19 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         return fail(RTE_ERR_ARG, "the direct E_0 route needs mesh_m <= 156");
     if (o.e0_route == RTE_E0_AUTO)
         o.e0_route = e0_direct_fits(prob->mesh_m) ? RTE_E0_DIRECT : RTE_E0_MULTIGRID;
+    if (o.coarse_route != RTE_EC_AUTO && o.coarse_route != RTE_EC_DIRECT &&
+        o.coarse_route != RTE_EC_MULTIGRID)
+        return fail(RTE_ERR_ARG, "unknown coarse route");
+    {
+        const int dPo = o.n_plus >= 0 ? (o.n_plus + 1) * (o.n_plus + 2) / 2 : 0;
+        if (o.coarse_route == RTE_EC_DIRECT && dPo > 0 && !ec_direct_fits(prob->mesh_m, dPo))
+            return fail(RTE_ERR_ARG, "the direct coarse route needs (mesh_m + 1) d^+ <= 2400");
+        // measured on the 128 x 128 / 512-triangle workload: a coarse solve
+        // takes 4.1 ms on the multigrid route (11 CG iterations to 0.1) and
+        // 9.9 ms on the direct route (one CG iteration, 514 grid-wide phases
+        // of its sweeps), whose FP64 set-up adds 3.6 s: multigrid by default
+        if (o.coarse_route == RTE_EC_AUTO) o.coarse_route = RTE_EC_MULTIGRID;
+    }
     if (o.mk_route != RTE_MK_EIGEN && o.mk_route != RTE_MK_PCG)
         return fail(RTE_ERR_ARG, "unknown (M^- - K^-)^{-1} route");
     // inner tolerances left at 0 follow the precision mode: the plain FP64
@@ -1503,6 +1556,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     };
     DevSystem& d = h->d;
     d.e0_direct = o.e0_route == RTE_E0_DIRECT;
+    d.ec_direct = o.coarse_route == RTE_EC_DIRECT;
     d.m = hs.m;
     d.nRp = hs.nRp; d.nRm = hs.nRm; d.nSp = hs.nSp; d.nSm = hs.nSm;
     d.dP = hs.dP; d.dM = hs.dM; d.nnz = (int)hs.st.col.size();
@@ -1906,7 +1960,7 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
     clk.mark("split FP64 operands");
     rc = setup_multigrid(h, hs, &clk);
     if (rc) return bail(rc);
-    clk.mark("E_c multigrid");
+    clk.mark(d.ec_direct ? "E_c factorisation" : "E_c multigrid");
     rc = alloc_workspace(h, o.max_rhs);
     if (rc) return bail(rc);
     clk.mark("workspace");

@@ -252,7 +252,16 @@ size_t rte_estimate_bytes(const rte_problem* p, const rte_options* o, int nrhs) 
         b += 7 * nRp * nSp * 4 * 4 / 3;        // multigrid coefficients
         b += r * nRp * nSp * 4 * 3 * 4 / 3;    // multigrid vectors
     }
-    b += 7 * nRp * (size_t)dP * dP * 12 * 4 / 3;   // E_c blocks
+    b += 7 * nRp * (size_t)dP * dP * 8;       // E_c blocks (FP64 level 0)
+    const bool ec_direct = dP > 0 && o && o->coarse_route == RTE_EC_DIRECT;
+    if (ec_direct) {
+        // the coarse factor and its set-up scratch (three FP64 row blocks)
+        const size_t Bd = (m + 1) * (size_t)dP, ld = (Bd + 3) & ~(size_t)3;
+        const bool fp64 = !o || o->precision == RTE_FP64;
+        b += (m + 1) * Bd * ld * (fp64 ? 8 : 4) + 3 * Bd * Bd * 8;
+    } else {
+        b += 7 * nRp * (size_t)dP * dP * 4 * 4 / 3;   // multigrid blocks
+    }
     b += r * nRp * dP * 8 * 10;                // coarse vectors
     b += 64ull << 20;                          // small arrays, allocator slack
     return b;

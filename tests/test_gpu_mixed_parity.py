@@ -13,7 +13,8 @@ each is judged on its own:
   (the CG's quad kernel) and 1280 columns (its kernel for more columns than
   the quad kernel's per-block tables hold; the direct route's sweeps of
   four right-hand sides with a ragged last one);
-* E_c^{-1} on mixed handles: relative residual in the oracle's E_c;
+* E_c^{-1} on mixed handles (direct and multigrid routes): relative
+  residual in the oracle's E_c;
 * E and E - K^+ in the mixed precision, element by element: max-norm error
   over the reference's max norm, against six unit roundoffs of the GEMM
   operand type (BF16 2^-9, TF32 2^-11), at 64, 256 and 1024 directions.
@@ -87,15 +88,18 @@ def test_mixed_e0_inverse_every_column(ncols, prec, route):
     assert res.max() <= 2e-5, res.max()
 
 
+@pytest.mark.parametrize('route', [1, 2], ids=['direct', 'multigrid'])
 @pytest.mark.parametrize('prec', [1, 2], ids=['fp32', 'bf16'])
-def test_mixed_coarse_inverse(prec):
-    # FP64 CG recurrences with an FP32 V-cycle preconditioner: the FP32
-    # multigrid must not limit the attainable accuracy
+def test_mixed_coarse_inverse(prec, route):
+    # FP64 CG recurrences with an FP32 preconditioner (the FP32 sweeps of
+    # E_c's factor, or an FP32 V-cycle): the FP32 preconditioner must not
+    # limit the attainable accuracy
     import paper_2102_09038_gb300 as rte
     p = problem(17, 2, 2)
     disc, ops = oracle_ops(p)
     for tol in (1e-5, 1e-10):
-        s = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, max_rhs=2, coarse_tol=tol)
+        s = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, max_rhs=2, coarse_tol=tol,
+                       coarse_route=route)
         d = s.d_plus
         W = s.export('WpN').reshape(disc.nSp, d)
         co = Coarse(ops, 2, W=W)

@@ -198,6 +198,23 @@ def test_e0_inverse_per_direction_cg(pair):
 
 
 @pytest.mark.parametrize('case', ['tiny', 'ragged', 'odd35'])
+def test_coarse_inverse_direct_route(case):
+    # the coarse CG preconditioned by E_c's exact row factorisation (the
+    # default is the V-cycle): residual to 1e-12
+    import paper_2102_09038_gb300 as rte
+    pr = Pair(case, coarse_route=rte.EC_DIRECT)
+    d = pr.gpu.d_plus
+    W = pr.gpu.export('WpN').reshape(pr.disc.nSp, d)
+    co = Coarse(pr.ops, 2, W=W)
+    qc = pr.rng.standard_normal((2, pr.disc.nRp, d))
+    uc = pr.run('EC_INV', qc, qc.shape)
+    pr.gpu.close()
+    for r in range(2):
+        res = co.Ec @ uc[r].ravel() - qc[r].ravel()
+        assert np.linalg.norm(res) / np.linalg.norm(qc[r]) < 2e-12
+
+
+@pytest.mark.parametrize('case', ['tiny', 'ragged', 'odd35'])
 def test_e0_inverse_multigrid_route(case):
     # the multigrid-PCG route of E_0^{-1} (the default takes the direct
     # factorisation on these meshes): every column to the 1e-12 tolerance
@@ -384,15 +401,16 @@ def test_contraction_rates_match_dense_iteration_matrix():
 def test_setup_stage_times():
     # rte_setup_times: every stage of the setup recorded, wall-clock, in order
     import paper_2102_09038_gb300 as rte
-    for route, stage in ((rte.E0_DIRECT, 'E_0 factorisation'),
-                         (rte.E0_MULTIGRID, 'E_0 multigrid')):
-        s = rte.Solver(CASES['ragged'](), n_plus=2, n_minus=3, e0_route=route)
+    for route, stage, cstage in ((rte.E0_DIRECT, 'E_0 factorisation', 'E_c factorisation'),
+                                 (rte.E0_MULTIGRID, 'E_0 multigrid', 'E_c multigrid')):
+        s = rte.Solver(CASES['ragged'](), n_plus=2, n_minus=3, e0_route=route,
+                       coarse_route=route)
         try:
             t = s.setup_times()
         finally:
             s.close()
         assert list(t)[0] == 'host assembly' and list(t)[-1] == 'launch tuning'
-        for name in ('eigenpairs of S+', 'eigenpairs of S-', stage, 'E_c multigrid'):
+        for name in ('eigenpairs of S+', 'eigenpairs of S-', stage, cstage):
             assert name in t
         assert all(v >= 0.0 for v in t.values())
 

@@ -175,6 +175,8 @@ def _setup_rc(problem_kw=None, **opts):
     ({}, dict(mk_route=3), 'route'),
     ({}, dict(e0_route=7), 'E_0 route'),
     (dict(m=157), dict(e0_route=1), 'mesh_m <= 156'),
+    ({}, dict(coarse_route=9), 'coarse route'),
+    (dict(m=160), dict(e0_route=2, coarse_route=1), 'd^+ <= 2400'),
     (dict(levels=0), dict(n_plus=4), 'too large'),   # d^+ = 15 > 4 directions
 ])
 def test_setup_refuses_bad_arguments_on_the_host(lib_path, problem_kw, opts, words):
