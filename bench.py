@@ -178,13 +178,23 @@ def fp64_peak_tflops(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
-# DRAM traffic of a kernel group from an ncu capture (the summary and the
-# command are in profiles/): dram__bytes_read.sum + dram__bytes_write.sum per
-# work unit of the captured launch (unit as in kernel_work's docstring), the
-# source file the kernel lives in and that file's SHA-256 prefix at the
-# capture.  The bench scales it to its own launch by the units processed, and
-# reports null once the source has changed since the capture.
-PROFILED_DRAM = {}
+# DRAM traffic of a timing scope's kernel from an ncu launch list of this
+# benchmark's own workload (`bench.py --profile-once`; the summary and the
+# command are in profiles/launches_checkerboard_128x128_T512_mixed_bf16.md):
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over the kernel's
+# launches in one solve, the source file the kernel lives in and that file's
+# SHA-256 prefix at the capture.  The bench reports it only for the workload
+# it was captured on, and null once the source has changed since.
+PROFILED_DRAM = {
+    'coarse_cg': dict(source='paper_2102_09038_gb300/csrc/mg.cu', sha='e29a65ac179f3b0b',
+                      workload='checkerboard_128x128_T512_g0.90_c0.99',
+                      bytes_per_launch=4.249e9,
+                      note='ncu launch list, 16 launches of k_ec_pcg<0> in one solve'),
+    'e0_direct': dict(source='paper_2102_09038_gb300/csrc/e0_direct.cu', sha='170f9aa09a001022',
+                      workload='checkerboard_128x128_T512_g0.90_c0.99',
+                      bytes_per_launch=4.744e9,
+                      note='ncu launch list, 64 launches of k_e0_direct_tma in one solve'),
+}
 
 
 def source_sha(rel):
@@ -364,12 +374,15 @@ def run_ours(args):
     avg_ms = top[1][0] / max(top[1][1], 1)
     traffic, traffic_note = None, 'no ncu capture of the current kernel source'
     prof = PROFILED_DRAM.get(top[0])
-    if prof and top[0] in ('e0_cg', 'e0_cg_lo'):
-        if source_sha(prof['source']) == prof['sha']:
-            traffic = prof['bytes_per_unit'] * e0_units(d, p.nrhs, last_info)[0]
-            traffic_note = prof['note']
-        else:
+    if prof:
+        if source_sha(prof['source']) != prof['sha']:
             traffic_note = 'kernel changed since its ncu capture'
+        elif (prof['workload'] != WORKLOAD['workload'] or args.mesh != WORKLOAD['mesh']
+              or 8 * 4 ** args.levels != WORKLOAD['sphere_triangles']):
+            traffic_note = 'ncu capture taken on another workload'
+        else:
+            traffic = prof['bytes_per_launch']
+            traffic_note = prof['note']
     roof = dict(kernel=top[0], bound=None, achieved=None, peak=None, unit=None,
                 frac=None, traffic=traffic, traffic_source=traffic_note, launches=top[1][1],
                 avg_ms=avg_ms)
