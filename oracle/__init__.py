@@ -17,3 +17,4 @@ from .geometry import square_mesh, sphere_reps, spherical_area, quad_rule
 from .assemble import Discretisation, hg_kernel
 from .operators import Operators
 from .richardson import Coarse, richardson, d_of
+from .h2 import H2Scattering
