@@ -63,6 +63,12 @@ def parse():
     ap.add_argument('--mk-routes', action='store_true',
                     help='time the eigenbasis and the PCG (Algorithm 1) routes of '
                          '(M^- - K^-)^{-1} on the 128x128 and 96x96 workloads and exit')
+    ap.add_argument('--h2', action='store_true',
+                    help='time the H^2-compressed S^+ apply against the dense products over '
+                         'n_S^+ = 1024 .. 65536 (the paper\'s compression table) and exit')
+    ap.add_argument('--h2-rows', type=int, default=2048,
+                    help='row vectors of the --h2 study (spatial nodes times right-hand sides)')
+    ap.add_argument('--h2-levels', default='4,5,6,7')
     ap.add_argument('--rates', action='store_true',
                     help='print the contraction rates rho and eta of the iteration matrix '
                          'over g, d_N and l (the paper\'s Section 6.2 study) and exit')
@@ -791,6 +797,81 @@ def mk_routes_study(args):
     return out
 
 
+def h2_study(args):
+    """Dense against H^2-compressed S^+ (Section 5.2; the compression table
+    of Section 6): for n_S^+ = 4 * 4^levels, g = 0.5 and the paper's
+    eta = 1.4, p = 4, the set-up time and device bytes of the H^2 matrices and
+    the time of Y = X S^+ for R row vectors (CUDA events on the handle's
+    stream, after a warm-up apply; inputs far larger than L2), in FP64 and
+    FP32, beside the dense products the solver uses for the same Y: the
+    split FP64 tensor-core GEMM and the BF16 tcgen05 GEMM, with a dense S^+ of
+    the same size (random values: their time does not depend on them).
+    The H^2 apply's flops count every 64 x 64 block product it performs
+    (leaf and transfer matrices, couplings, near blocks)."""
+    import torch
+    import paper_2102_09038_gb300 as rte
+    torch.cuda.set_device(0)
+    R = args.h2_rows
+    fp64_peak = fp64_peak_tflops(torch)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # FP32 SIMT peak: 128 FP32 lanes per SM, 2 flops per FMA, at the SM clock
+    # the run sees (sampled below)
+    out = []
+    for levels in [int(v) for v in args.h2_levels.split(',')]:
+        h = rte.H2Scattering(levels, 0.5, parities=1)
+        inf = h.info()
+        n = inf['n_plus']
+        gen = torch.Generator(device='cuda').manual_seed(levels)
+        X = torch.randn((R, n), dtype=torch.float64, device='cuda', generator=gen)
+        st = h.stream
+        blocks = (2 * inf['leaves'] + 2 * inf['transfers'] + sum(inf['far_blocks'])
+                  + inf['near_matrices'])
+        flops = 2.0 * R * 64 * 64 * blocks
+
+        def timed(fn, reps=3):
+            fn()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            st.synchronize()
+            e0.record(st)
+            for _ in range(reps):
+                fn()
+            e1.record(st)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / 1e3 / reps
+
+        with Clocks(0) as clk:
+            t64 = timed(lambda: h.apply(X, precision=rte.FP64), reps=2)
+            t32 = timed(lambda: h.apply(X, precision=rte.MIXED_FP32))
+        mhz = clk.summary().get('sm_mhz') or 2070.0
+        fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        row = dict(levels=levels, n_plus=n, rows=R, h2_setup_s=inf['setup_ms'] / 1e3,
+                   h2_bytes=inf['bytes'], far_blocks=inf['far_blocks'],
+                   near_matrices=inf['near_matrices'], block_products=blocks,
+                   h2_fp64_s=t64, h2_fp32_s=t32,
+                   h2_fp64_tflops=flops / t64 / 1e12, h2_fp64_frac=flops / t64 / 1e12 / fp64_peak,
+                   h2_fp32_tflops=flops / t32 / 1e12, h2_fp32_frac=flops / t32 / 1e12 / fp32_peak,
+                   fp64_peak_tflops=fp64_peak, fp32_simt_peak_tflops=fp32_peak,
+                   dense_bytes_fp64=8 * n * n)
+        h.close()
+        del X
+        torch.cuda.empty_cache()
+        # dense products of the same Y = X S (S symmetric: Bt = S)
+        try:
+            S = torch.randn((n, n), dtype=torch.float64, device='cuda', generator=gen)
+            Xd = torch.randn((R, n), dtype=torch.float64, device='cuda', generator=gen)
+            row['dense_split_fp64_s'] = timed(lambda: rte.dgemm_split(Xd, S, slices=5), reps=2)
+            Sb, Xb = S.to(torch.bfloat16), Xd.to(torch.bfloat16)
+            del S, Xd
+            row['dense_bf16_s'] = timed(lambda: rte.gemm_lowp(Xb, Sb))
+            del Sb, Xb
+        except (RuntimeError, rte.RteError) as e:
+            row['dense_note'] = str(e).splitlines()[0][:120]
+        torch.cuda.empty_cache()
+        out.append(row)
+        print(json.dumps(row), flush=True)
+    return out
+
+
 def rates_study(args):
     """rho (spectral radius) and eta (energy norm) of Algorithm 3's
     iteration matrix (I - P_G)(I - P_1^l (E - K^+)) by power iteration on the
@@ -809,7 +890,7 @@ def rates_study(args):
     for g in (0.1, 0.3, 0.5, 0.7, 0.9):
         p = workloads.checkerboard(m=24, levels=3, g=g, ratio=0.999, blocks=4, seed=0)
         for n_plus in (0, 2, 4):
-            for l in (1, 2, 3, 4):
+            for l in (1, 2, 3, 4, 5, 6):
                 s = rte.Solver(p, precision=rte.FP64, n_plus=n_plus, l=l,
                                p1_route=rte.P1_RICHARDSON)
                 rho, eta, steps = s.rates(maxit=300, tol=1e-7)
@@ -828,6 +909,9 @@ if __name__ == '__main__':
         sys.exit(0)
     if a.mk_routes:
         mk_routes_study(a)
+        sys.exit(0)
+    if a.h2:
+        h2_study(a)
         sys.exit(0)
     if a.impl == 'reference':
         run_reference(a)

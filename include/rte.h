@@ -484,6 +484,74 @@ int rte_solve_batch(const rte_problem* probs, const double* const* q_nodal, cons
                     double* const* u, int count, double tol, const rte_options* opts,
                     size_t hbm_budget_bytes, int slots, rte_stats* stats);
 
+/* ------------------------------------------------------------------------
+ * H^2-compressed scattering matrices (Section 5.2; the compression
+ * experiment of Section 6).  S^+ = 2 (D + M) and S^- = 2 (D - M) in the basis
+ * of the representatives, with D the direct part (kernel k(s.s') over
+ * K_k x K_k') and M the mirror part (k(-s.s'), K_k x (-K_k')); each part is
+ * approximated by interpolating the extension K(x~, y~) = k(x.y),
+ * x = x~/|x~| (eq. HGextension):
+ *   cluster tree   the refinement hierarchy of the representatives; leaves
+ *                  hold n_min = 64 of them (so levels >= 3);
+ *   boxes          bounding boxes of each cluster's far-rule quadrature
+ *                  points (negated for the mirror part's column cluster);
+ *   admissibility  max(diam B_t, diam B_c) <= eta dist(B_t, B_c);
+ *   interpolation  p Chebyshev points per coordinate (p^3 <= 64 per box),
+ *                  nested bases (leaf bases and transfer matrices);
+ *   near blocks    exact entries by the dense assembly's quadrature rules.
+ * Set-up runs on the device; the apply is a sequence of block-sparse
+ * products over 64-column blocks (leaf forward transform, upward transfers,
+ * couplings, downward transfers, leaf backward transform, near field).
+ * ------------------------------------------------------------------------ */
+typedef struct rte_h2 rte_h2;
+
+typedef struct {
+    int levels;        /* sphere refinement, n_S^+ = 4 * 4^levels; 3..8    */
+    double g;          /* Henyey-Greenstein asymmetry, 0 <= g < 1          */
+    double eta;        /* admissibility parameter (> 0; the paper: 1.4)    */
+    int p;             /* interpolation points per coordinate, 2..4        */
+    int parities;      /* bit 0: S^+, bit 1: S^- (at least one)            */
+    int precisions;    /* bit 0: FP64 apply, bit 1: FP32 apply             */
+} rte_h2_options;
+
+typedef struct {
+    int n_plus;               /* n_S^+                                      */
+    int leaves, clusters;     /* leaf clusters; clusters holding a basis    */
+    int far_blocks[2];        /* admissible blocks, direct / mirror part    */
+    int near_blocks[2];       /* inadmissible leaf pairs, direct / mirror   */
+    int near_matrices;        /* near blocks after merging the two parts    */
+    int transfers;            /* transfer matrices (clusters below the top) */
+    size_t bytes;             /* device bytes of the compressed matrices    */
+    double setup_ms;          /* wall time of rte_h2_create                 */
+} rte_h2_info;
+
+/* Fills the paper's parameters: eta = 1.4, p = 4, both parities, FP64 and
+ * FP32. */
+int rte_h2_default_options(rte_h2_options* opts);
+
+/* Builds the compressed S^+ and/or S^- on the current device (on `stream`,
+ * synchronised before returning).  RTE_ERR_ARG for options out of range;
+ * RTE_ERR_NOMEM when the matrices do not fit in free device memory (checked
+ * on the host before allocating). */
+int rte_h2_create(const rte_h2_options* opts, void* stream, rte_h2** out);
+
+/* Y = X S^+ (parity +1) or Y = X S^- (parity -1) for `rows` row vectors:
+ * X and Y are device arrays [rows][n] (n = n_S^+ for S^+, n_S^- = 3 n_S^+
+ * for S^-, row-major, caller-owned, not overlapping); precision RTE_FP64
+ * or RTE_MIXED_FP32 (FP32 products; X is rounded to FP32 and Y written back
+ * in FP64).  Work buffers grow on demand and are kept in the handle.
+ * Stream-ordered on `stream`; does not synchronise.  rows = 0 is a no-op. */
+int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* Y, int rows,
+                 void* stream);
+
+int rte_h2_get_info(const rte_h2* h, rte_h2_info* info);
+
+/* Dense S^+ or S^- (host, n x n row-major) assembled by the same device
+ * quadrature as rte_setup's; for comparisons at moderate n (n_S^+ <= 4096). */
+int rte_h2_dense(const rte_h2* h, int parity, double* host_out, size_t n);
+
+void rte_h2_destroy(rte_h2* h);
+
 /* Message of the calling thread's last error ("" if none). */
 const char* rte_last_error(void);
 

@@ -71,6 +71,19 @@ class _Stats(ctypes.Structure):
                 ('e0_active_vcycles', ctypes.c_double)]
 
 
+class _H2Options(ctypes.Structure):
+    _fields_ = [('levels', ctypes.c_int), ('g', ctypes.c_double), ('eta', ctypes.c_double),
+                ('p', ctypes.c_int), ('parities', ctypes.c_int), ('precisions', ctypes.c_int)]
+
+
+class _H2Info(ctypes.Structure):
+    _fields_ = [('n_plus', ctypes.c_int), ('leaves', ctypes.c_int), ('clusters', ctypes.c_int),
+                ('far_blocks', ctypes.c_int * 2), ('near_blocks', ctypes.c_int * 2),
+                ('near_matrices', ctypes.c_int), ('transfers', ctypes.c_int),
+                ('bytes', ctypes.c_size_t),
+                ('setup_ms', ctypes.c_double)]
+
+
 _lib = None
 EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs', 'rte_inflow',
             'rte_apply', 'rte_precond', 'rte_solve', 'rte_operator',
@@ -80,6 +93,8 @@ EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs', 'rte_inf
             'rte_server_submit', 'rte_server_wait', 'rte_server_destroy', 'rte_solve_batch',
             'rte_trace_read', 'rte_destroy', 'rte_set_wait_limit', 'rte_barrier_selftest',
             'rte_set_stream', 'rte_server_cache_stats',
+            'rte_h2_default_options', 'rte_h2_create', 'rte_h2_apply', 'rte_h2_get_info',
+            'rte_h2_dense', 'rte_h2_destroy',
             'rte_last_error']
 
 
@@ -142,10 +157,17 @@ def load(path=LIB_PATH):
     lib.rte_kernel_launches.restype = ctypes.c_longlong
     lib.rte_destroy.argtypes = [P]
     lib.rte_destroy.restype = V
+    lib.rte_h2_default_options.argtypes = [ctypes.POINTER(_H2Options)]
+    lib.rte_h2_create.argtypes = [ctypes.POINTER(_H2Options), P, ctypes.POINTER(P)]
+    lib.rte_h2_apply.argtypes = [P, I, I, P, P, I, P]
+    lib.rte_h2_get_info.argtypes = [P, ctypes.POINTER(_H2Info)]
+    lib.rte_h2_dense.argtypes = [P, I, ctypes.POINTER(D), ctypes.c_size_t]
+    lib.rte_h2_destroy.argtypes = [P]
+    lib.rte_h2_destroy.restype = V
     lib.rte_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ('rte_destroy', 'rte_last_error', 'rte_kernel_launches',
-                        'rte_estimate_bytes', 'rte_server_destroy'):
+                        'rte_estimate_bytes', 'rte_server_destroy', 'rte_h2_destroy'):
             getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -359,6 +381,75 @@ class Server:
     def close(self):
         if getattr(self, '_h', None):
             _lib.rte_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class H2Scattering:
+    """H^2-compressed S^+ and S^- (rte_h2_*) on the current CUDA device.
+
+    levels: sphere refinement (n_S^+ = 4 * 4^levels, levels >= 3); g: HG
+    asymmetry; eta, p: admissibility parameter and interpolation points per
+    coordinate (defaults: the paper's 1.4 and 4); parities: 1 (S^+), 2 (S^-)
+    or 3; precisions: 1 (FP64 apply), 2 (FP32 apply) or 3.
+    """
+
+    def __init__(self, levels, g, eta=1.4, p=4, parities=3, precisions=3, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError('librte needs a CUDA device; there is no CPU path')
+        lib = load()
+        o = _H2Options()
+        _check(lib.rte_h2_default_options(ctypes.byref(o)))
+        o.levels, o.g, o.eta, o.p = int(levels), float(g), float(eta), int(p)
+        o.parities, o.precisions = int(parities), int(precisions)
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.rte_h2_create(ctypes.byref(o), ctypes.c_void_p(self.stream.cuda_stream),
+                                 ctypes.byref(h)))
+        self._h = h
+        self.n_plus = self.info()['n_plus']
+
+    def info(self):
+        inf = _H2Info()
+        _check(_lib.rte_h2_get_info(self._h, ctypes.byref(inf)))
+        return dict(n_plus=inf.n_plus, leaves=inf.leaves, clusters=inf.clusters,
+                    far_blocks=tuple(inf.far_blocks), near_blocks=tuple(inf.near_blocks),
+                    near_matrices=inf.near_matrices, transfers=inf.transfers, bytes=inf.bytes,
+                    setup_ms=inf.setup_ms)
+
+    def apply(self, X, parity=1, precision=FP64, out=None):
+        """Y = X S^+ (parity +1) or X S^- (parity -1); X: float64 CUDA tensor
+        (rows, n) with n = n_S^+ or 3 n_S^+."""
+        torch = self.torch
+        n = self.n_plus * (1 if parity > 0 else 3)
+        if X.dtype != torch.float64 or not X.is_cuda or X.dim() != 2 or X.shape[1] != n:
+            raise ValueError('X must be a float64 CUDA tensor of shape (rows, %d)' % n)
+        X = X.contiguous()
+        Y = out if out is not None else torch.empty_like(X)
+        _check(_lib.rte_h2_apply(self._h, int(parity), int(precision), _ptr(X), _ptr(Y),
+                                 int(X.shape[0]), ctypes.c_void_p(self.stream.cuda_stream)))
+        return Y
+
+    def dense(self, parity=1):
+        """The dense S^+ or S^- by the library's quadrature (levels <= 5)."""
+        import numpy as np
+        n = self.n_plus * (1 if parity > 0 else 3)
+        out = np.empty((n, n))
+        _check(_lib.rte_h2_dense(self._h, int(parity),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+        return out
+
+    def close(self):
+        if getattr(self, '_h', None):
+            self.stream.synchronize()
+            _lib.rte_h2_destroy(self._h)
             self._h = None
 
     def __del__(self):

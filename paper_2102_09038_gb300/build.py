@@ -13,7 +13,11 @@ OUT = os.path.join(HERE, '_build')
 LIB = os.path.join(OUT, 'librte.so')
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 SOURCES = ['setup_host.cpp', 'mg_host.cpp', 'server.cpp', 'kernels.cu', 'mg.cu', 'tc_gemm.cu',
-           'rte.cu', 'dgemm_static.cu', 'tune.cpp', 'e0_direct.cu', 'ec_direct.cu']
+           'rte.cu', 'dgemm_static.cu', 'tune.cpp', 'e0_direct.cu', 'ec_direct.cu', 'h2.cu',
+           'h2_build.cpp']
+# host files whose floating point must round the same on every host (no
+# contraction into fused multiply-adds)
+NO_CONTRACT = ('h2_build.cpp',)
 
 
 def nvcc():
@@ -28,6 +32,8 @@ def _compile(src, extra):
     cmd = [nvcc(), '-O3', '-std=c++17', '-lineinfo', '-Xcompiler', '-fPIC',
            '-I' + os.path.join(HERE, '..', 'include'), '-c', src, '-o', obj]
     cmd += ARCH if src.endswith('.cu') else ['-x', 'c++']
+    if os.path.basename(src) in NO_CONTRACT:
+        cmd += ['-Xcompiler', '-ffp-contract=off']
     cmd += extra
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

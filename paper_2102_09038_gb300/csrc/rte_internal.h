@@ -46,6 +46,14 @@ struct SphereMesh {
     std::vector<int> tri;            // 3 vertex ids per representative
 };
 SphereMesh make_sphere(int levels);
+// Level-r rule on one spherical triangle (refine r times, one node per
+// sub-triangle at its normalised vertex mean, weight its exact area); appends
+// 4^r points (3 doubles each) and weights at index `count`.
+void quad_one(const double* a, const double* b, const double* c, int r, double* pts, double* w,
+              int& count);
+bool inv3(const double* A, double* Ai);
+// Pairs (k, k') where K_k' or -K_k' shares a vertex with K_k (sorted per k).
+void sphere_near_pairs(const SphereMesh& S, std::vector<int>& ptr, std::vector<int>& idx);
 
 // Sparse 7-point node stencil (row = node, sorted columns, diagonal index).
 struct Stencil {

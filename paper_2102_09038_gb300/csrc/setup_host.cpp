@@ -102,8 +102,8 @@ static double sph_area(const double* a, const double* b, const double* c) {
 // Level-r rule on one spherical triangle: refine r times (normalised edge
 // midpoints), one node per sub-triangle at its normalised vertex mean with
 // the sub-triangle's exact area as weight.
-static void quad_one(const double* a, const double* b, const double* c, int r,
-                     double* pts, double* w, int& count) {
+void quad_one(const double* a, const double* b, const double* c, int r, double* pts, double* w,
+              int& count) {
     if (r == 0) {
         double p[3] = {a[0] + b[0] + c[0], a[1] + b[1] + c[1], a[2] + b[2] + c[2]};
         normalise3(p);
@@ -123,7 +123,7 @@ static void quad_one(const double* a, const double* b, const double* c, int r,
     quad_one(ab, bc, ca, r - 1, pts, w, count);
 }
 
-static bool inv3(const double* A, double* Ai) {
+bool inv3(const double* A, double* Ai) {
     const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) -
                        A[1] * (A[3] * A[8] - A[5] * A[6]) +
                        A[2] * (A[3] * A[7] - A[4] * A[6]);
@@ -138,6 +138,41 @@ static bool inv3(const double* A, double* Ai) {
     Ai[7] = (A[1] * A[6] - A[0] * A[7]) / det;
     Ai[8] = (A[0] * A[4] - A[1] * A[3]) / det;
     return true;
+}
+
+// Pairs (k, k') where K_k' or -K_k' shares a vertex with K_k: the pairs whose
+// double integrals take the near rule.
+void sphere_near_pairs(const SphereMesh& S, std::vector<int>& ptr, std::vector<int>& idx) {
+    const int n = S.n;
+    std::map<std::tuple<long long, long long, long long>, int> vid;
+    auto key = [](const double* v) {
+        return std::make_tuple(std::llround(v[0] * 1e9), std::llround(v[1] * 1e9),
+                               std::llround(v[2] * 1e9));
+    };
+    const int nv = (int)S.verts.size() / 3;
+    for (int v = 0; v < nv; ++v) vid[key(&S.verts[3 * v])] = v;
+    std::vector<int> anti(nv, -1);
+    for (int v = 0; v < nv; ++v) {
+        const double w[3] = {-S.verts[3 * v], -S.verts[3 * v + 1], -S.verts[3 * v + 2]};
+        auto it = vid.find(key(w));
+        if (it != vid.end()) anti[v] = it->second;
+    }
+    std::vector<std::vector<int>> owners(nv);
+    for (int k = 0; k < n; ++k)
+        for (int a = 0; a < 3; ++a) owners[S.tri[3 * k + a]].push_back(k);
+    ptr.assign(n + 1, 0);
+    idx.clear();
+    for (int k = 0; k < n; ++k) {
+        std::set<int> s;
+        for (int a = 0; a < 3; ++a) {
+            const int v = S.tri[3 * k + a];
+            for (int kk : owners[v]) s.insert(kk);
+            if (anti[v] >= 0)
+                for (int kk : owners[anti[v]]) s.insert(kk);
+        }
+        idx.insert(idx.end(), s.begin(), s.end());
+        ptr[k + 1] = (int)idx.size();
+    }
 }
 
 int build_host_system(const rte_problem& p, const rte_options& o, HostSystem& hs) {
@@ -335,36 +370,7 @@ int build_host_system(const rte_problem& p, const rte_options& o, HostSystem& hs
         hs.e0s[6 * k + 4] = oy;
         hs.e0s[6 * k + 5] = hs.m_[k];
     }
-    // pairs (k, k') where K_k' or -K_k' shares a vertex with K_k
-    std::map<std::tuple<long long, long long, long long>, int> vid;
-    auto key = [](const double* v) {
-        return std::make_tuple(std::llround(v[0] * 1e9), std::llround(v[1] * 1e9),
-                               std::llround(v[2] * 1e9));
-    };
-    const int nv = (int)S.verts.size() / 3;
-    for (int v = 0; v < nv; ++v) vid[key(&S.verts[3 * v])] = v;
-    std::vector<int> anti(nv, -1);
-    for (int v = 0; v < nv; ++v) {
-        const double w[3] = {-S.verts[3 * v], -S.verts[3 * v + 1], -S.verts[3 * v + 2]};
-        auto it = vid.find(key(w));
-        if (it != vid.end()) anti[v] = it->second;
-    }
-    std::vector<std::vector<int>> owners(nv);
-    for (int k = 0; k < n; ++k)
-        for (int a = 0; a < 3; ++a) owners[S.tri[3 * k + a]].push_back(k);
-    hs.near_ptr.assign(n + 1, 0);
-    hs.near_idx.clear();
-    for (int k = 0; k < n; ++k) {
-        std::set<int> s;
-        for (int a = 0; a < 3; ++a) {
-            const int v = S.tri[3 * k + a];
-            for (int kk : owners[v]) s.insert(kk);
-            if (anti[v] >= 0)
-                for (int kk : owners[anti[v]]) s.insert(kk);
-        }
-        hs.near_idx.insert(hs.near_idx.end(), s.begin(), s.end());
-        hs.near_ptr[k + 1] = (int)hs.near_idx.size();
-    }
+    sphere_near_pairs(S, hs.near_ptr, hs.near_idx);
     return RTE_OK;
 }
 

@@ -113,7 +113,9 @@ def _c_layout(struct, fields, tmp_path):
 
 @pytest.mark.parametrize('struct, mirror', [('rte_options', '_Options'),
                                             ('rte_stats', '_Stats'),
-                                            ('rte_problem', '_Problem')])
+                                            ('rte_problem', '_Problem'),
+                                            ('rte_h2_options', '_H2Options'),
+                                            ('rte_h2_info', '_H2Info')])
 def test_binding_structs_match_the_header_layout(struct, mirror, tmp_path):
     # the ctypes mirrors of the binding have the header's field order,
     # offsets and size (a field added on one side only would shift the rest)
@@ -204,3 +206,27 @@ def test_memory_estimate_grows_with_the_problem(lib_path):
     assert e(small, precision=rte.MIXED_BF16) == pcg          # the mixed default
     assert e(small, precision=rte.FP64) == e(small, precision=rte.FP64,
                                              p1_route=rte.P1_RICHARDSON)
+
+
+@pytest.mark.parametrize('field, value, words', [
+    ('levels', 2, 'levels must be in [3, 8]'),
+    ('levels', 9, 'levels must be in [3, 8]'),
+    ('g', 1.0, 'g must satisfy'),
+    ('eta', 0.0, 'eta must be positive'),
+    ('p', 5, 'p must be in [2, 4]'),
+    ('parities', 0, 'parities'),
+    ('precisions', 4, 'precisions')])
+def test_h2_create_refuses_bad_options_on_the_host(lib_path, field, value, words):
+    # rte_h2_create checks every option before touching the device
+    import ctypes
+    import paper_2102_09038_gb300 as rte
+    lib = rte.load()
+    o = rte._H2Options()
+    assert lib.rte_h2_default_options(ctypes.byref(o)) == 0
+    assert (o.eta, o.p, o.parities, o.precisions) == (1.4, 4, 3, 3)
+    setattr(o, field, value)
+    h = ctypes.c_void_p()
+    rc = lib.rte_h2_create(ctypes.byref(o), None, ctypes.byref(h))
+    assert rte.ERRORS[rc] == 'RTE_ERR_ARG'
+    assert words in lib.rte_last_error().decode()
+    assert not h.value
