@@ -813,6 +813,7 @@ def h2_study(args):
     torch.cuda.set_device(0)
     R = args.h2_rows
     fp64_peak = fp64_peak_tflops(torch)
+    peaks, _ = load_peaks()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     # FP32 SIMT peak: 128 FP32 lanes per SM, 2 flops per FMA, at the SM clock
     # the run sees (sampled below)
@@ -842,6 +843,7 @@ def h2_study(args):
         with Clocks(0) as clk:
             t64 = timed(lambda: h.apply(X, precision=rte.FP64), reps=2)
             t32 = timed(lambda: h.apply(X, precision=rte.MIXED_FP32))
+            tbf = timed(lambda: h.apply(X, precision=rte.MIXED_BF16))
         mhz = clk.summary().get('sm_mhz') or 2070.0
         fp32_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
         row = dict(levels=levels, n_plus=n, rows=R, h2_setup_s=inf['setup_ms'] / 1e3,
@@ -850,6 +852,8 @@ def h2_study(args):
                    h2_fp64_s=t64, h2_fp32_s=t32,
                    h2_fp64_tflops=flops / t64 / 1e12, h2_fp64_frac=flops / t64 / 1e12 / fp64_peak,
                    h2_fp32_tflops=flops / t32 / 1e12, h2_fp32_frac=flops / t32 / 1e12 / fp32_peak,
+                   h2_bf16_s=tbf, h2_bf16_tflops=flops / tbf / 1e12,
+                   h2_bf16_frac=flops / tbf / 1e12 / peaks['bf16_tflops'],
                    fp64_peak_tflops=fp64_peak, fp32_simt_peak_tflops=fp32_peak,
                    dense_bytes_fp64=8 * n * n)
         h.close()

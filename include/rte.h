@@ -511,7 +511,8 @@ typedef struct {
     double eta;        /* admissibility parameter (> 0; the paper: 1.4)    */
     int p;             /* interpolation points per coordinate, 2..4        */
     int parities;      /* bit 0: S^+, bit 1: S^- (at least one)            */
-    int precisions;    /* bit 0: FP64 apply, bit 1: FP32 apply             */
+    int precisions;    /* bit 0: FP64 apply, bit 1: FP32 apply, bit 2: BF16
+                          tensor-core apply                                */
 } rte_h2_options;
 
 typedef struct {
@@ -525,8 +526,8 @@ typedef struct {
     double setup_ms;          /* wall time of rte_h2_create                 */
 } rte_h2_info;
 
-/* Fills the paper's parameters: eta = 1.4, p = 4, both parities, FP64 and
- * FP32. */
+/* Fills the paper's parameters: eta = 1.4, p = 4, both parities, every
+ * precision. */
 int rte_h2_default_options(rte_h2_options* opts);
 
 /* Builds the compressed S^+ and/or S^- on the current device (on `stream`,
@@ -537,10 +538,16 @@ int rte_h2_create(const rte_h2_options* opts, void* stream, rte_h2** out);
 
 /* Y = X S^+ (parity +1) or Y = X S^- (parity -1) for `rows` row vectors:
  * X and Y are device arrays [rows][n] (n = n_S^+ for S^+, n_S^- = 3 n_S^+
- * for S^-, row-major, caller-owned, not overlapping); precision RTE_FP64
- * or RTE_MIXED_FP32 (FP32 products; X is rounded to FP32 and Y written back
- * in FP64).  Work buffers grow on demand and are kept in the handle.
- * Stream-ordered on `stream`; does not synchronise.  rows = 0 is a no-op. */
+ * for S^-, row-major, caller-owned, not overlapping, 16-byte aligned).
+ * precision: RTE_FP64 (FP64 products on the FP64 units); RTE_MIXED_FP32
+ * (FP32 products; X rounded to FP32, Y written back in FP64);
+ * RTE_MIXED_BF16 (tcgen05 products with BF16 operands and FP32
+ * accumulation; X, the bases, the coupling and near matrices and the
+ * cluster coefficients rounded to BF16, Y accumulated in FP32).  Work
+ * buffers grow on demand and are kept in the handle.  Stream-ordered on
+ * `stream`; the FP64 and FP32 applies do not synchronise, the BF16 apply
+ * synchronises to read its pipelines' timeout flag (RTE_ERR_TIMEOUT).
+ * rows = 0 is a no-op. */
 int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* Y, int rows,
                  void* stream);
 

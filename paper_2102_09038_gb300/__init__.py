@@ -396,10 +396,11 @@ class H2Scattering:
     levels: sphere refinement (n_S^+ = 4 * 4^levels, levels >= 3); g: HG
     asymmetry; eta, p: admissibility parameter and interpolation points per
     coordinate (defaults: the paper's 1.4 and 4); parities: 1 (S^+), 2 (S^-)
-    or 3; precisions: 1 (FP64 apply), 2 (FP32 apply) or 3.
+    or 3; precisions: a mask of 1 (FP64 apply), 2 (FP32) and 4 (BF16 on the
+    tensor cores).
     """
 
-    def __init__(self, levels, g, eta=1.4, p=4, parities=3, precisions=3, stream=None):
+    def __init__(self, levels, g, eta=1.4, p=4, parities=3, precisions=7, stream=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError('librte needs a CUDA device; there is no CPU path')

@@ -13,6 +13,8 @@
 // interpolation points when a tile needs it (4096 kernel values against the
 // tile's 2 * 64^3 multiply-adds), so that the far field costs no HBM
 // traffic beyond the coefficient vectors.
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +26,7 @@
 #include "device.h"
 #include "h2.h"
 #include "rte_internal.h"
+#include "tcgen05.cuh"
 
 namespace rte {
 
@@ -380,6 +383,194 @@ k_h2_bsr(int rows, int rtiles, int nout, int k, int parity, const T* __restrict_
     }
 }
 
+// ------------------------------------------------- tensor-core apply
+// The same block-sparse products on the tensor cores (tcgen05, BF16
+// operands, FP32 accumulation in tensor memory) for the BF16 apply.  One
+// block of 128 threads per (128-row tile, output block): warp 0 lane 0 loads
+// the A tile (128 rows x 64 columns of In, one 128-byte swizzled row per
+// matrix row) and the B tile (the 64 x 64 matrix, stored K-major as
+// Bt[output][input]) by TMA into a 4-stage ring, warp 1 lane 0 issues four
+// 128 x 64 x 16 MMAs per entry, and the four warps drain the 64 accumulator
+// columns.  Every wait is bounded (tc::mbar_wait).
+constexpr int kTcRows = 128;
+constexpr int kTcStages = 4;
+constexpr uint32_t kTcABytes = kTcRows * tc::kRowBytes;   // 16 KB
+constexpr uint32_t kTcBBytes = kH2B * tc::kRowBytes;      // 8 KB
+
+constexpr size_t tc_smem_bytes() {
+    return 1024 + (size_t)kTcStages * (kTcABytes + kTcBBytes) + (2 * kTcStages + 1) * 8 + 16;
+}
+
+template <bool kAccum, typename TOut>
+__global__ void __launch_bounds__(128, 1)
+k_h2_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+        int rows, int rtiles, int nout, TOut* __restrict__ Out, long long ldo,
+        const int* __restrict__ out_blk, const int* __restrict__ ptr,
+        const int* __restrict__ in_blk, const int* __restrict__ mat) {
+    using namespace tc;
+    constexpr uint32_t kTmemCols = kH2B;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kTcStages * kTcABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kTcStages * kTcBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 1);
+
+    const long long bid = blockIdx.x;
+    const long long per = (long long)kGroup * rtiles;
+    const int grp = (int)(bid / per);
+    const long long rem = bid % per;
+    const int rt = (int)(rem / kGroup);
+    const int j = grp * kGroup + (int)(rem % kGroup);
+    if (j >= nout) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = rt * kTcRows;
+    const int e0 = ptr[j], steps = ptr[j + 1] - e0;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kTcStages),
+                   done = smem_u32(bars + 2 * kTcStages);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        for (int st = 0; st < steps && ok; ++st) {
+            const int s = st % kTcStages;
+            const uint32_t ph = (st / kTcStages) & 1;
+            if (!mbar_wait(empty0 + 8 * s, ph ^ 1)) { ok = false; break; }
+            mbar_expect_tx(full0 + 8 * s, kTcABytes + kTcBBytes);
+            tma_load_2d(smem_u32(sA + s * kTcABytes), &mapA, full0 + 8 * s, in_blk[e0 + st] * kH2B,
+                        r0);
+            tma_load_2d(smem_u32(sB + s * kTcBBytes), &mapB, full0 + 8 * s, 0, mat[e0 + st] * kH2B);
+        }
+    } else if (warp == 1 && lane == 0) {
+        const uint32_t idesc = (1u << 4)                               // D: FP32
+                               | (1u << 7) | (1u << 10)                // A, B: BF16
+                               | ((uint32_t)(kH2B >> 3) << 17)         // N = 64
+                               | ((uint32_t)(kTcRows >> 4) << 24);     // M = 128
+        for (int st = 0; st < steps && ok; ++st) {
+            const int s = st % kTcStages;
+            const uint32_t ph = (st / kTcStages) & 1;
+            if (!mbar_wait(full0 + 8 * s, ph)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * kTcABytes), b0 = smem_u32(sB + s * kTcBBytes);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_issue(false, tmem, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), idesc,
+                          (st > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+    ok = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row = r0 + warp * 32 + lane;
+    const int ob = out_blk[j];
+    for (int c0 = 0; c0 < kH2B; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (!ok || row >= rows) continue;
+        if (steps == 0)
+            for (int i = 0; i < 16; ++i) v[i] = 0.f;
+        TOut* dst = Out + (size_t)row * ldo + (size_t)ob * kH2B + c0;
+        if constexpr (sizeof(TOut) == 4) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 w = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                if (kAccum) {
+                    const float4 o = d4[i];
+                    w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+                }
+                d4[i] = w;
+            }
+        } else {
+            uint4* d4 = reinterpret_cast<uint4*>(dst);
+            uint32_t w[8];
+            if (kAccum) {
+                const uint4 o0 = d4[0], o1 = d4[1];
+                const uint32_t ow[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&ow[i]));
+                    v[2 * i] += f.x;
+                    v[2 * i + 1] += f.y;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                w[i] = *reinterpret_cast<uint32_t*>(&hv);
+            }
+            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kTmemCols));
+}
+
+// Matrices of the tensor-core pool in the K-major layout Bt[output][input]
+// (BF16): entry e copies FP64 pool matrix src[e], transposed when tr[e].
+__global__ void k_h2_tc_copy(const double* __restrict__ pool, const long long* __restrict__ src,
+                             const long long* __restrict__ dst, const unsigned char* __restrict__ tr,
+                             __nv_bfloat16* __restrict__ out) {
+    const long long e = blockIdx.x;
+    const double* S = pool + src[e] * (kH2B * kH2B);
+    __nv_bfloat16* D = out + dst[e] * (kH2B * kH2B);
+    const bool t = tr[e];
+    for (int x = threadIdx.x; x < kH2B * kH2B; x += blockDim.x) {
+        const int r = x / kH2B, c = x % kH2B;
+        D[x] = __float2bfloat16_rn((float)(t ? S[c * kH2B + r] : S[x]));
+    }
+}
+
+// Coupling matrices in the K-major layout: Bt[nu][mu] = 2 f k(s xi^t_nu .
+// xi^c_mu) (f = 1 for S^+, s for S^-), entry e of the coupling list, whose
+// row cluster is out_of[e].
+__global__ void k_h2_tc_couple(int k, int parity, double g, const double* __restrict__ xi,
+                               const int* __restrict__ out_of, const int* __restrict__ in_blk,
+                               const int* __restrict__ sgn, __nv_bfloat16* __restrict__ out,
+                               long long first) {
+    const long long e = blockIdx.x;
+    const double* xo = xi + (size_t)out_of[e] * kH2B * 3;
+    const double* xc = xi + (size_t)in_blk[e] * kH2B * 3;
+    const double s = sgn[e] > 0 ? 1.0 : -1.0;
+    const double f = 2.0 * (parity > 0 ? 1.0 : s);
+    const double c0 = (1.0 - g * g) / (4.0 * kPi);
+    __nv_bfloat16* D = out + (first + e) * (kH2B * kH2B);
+    for (int x = threadIdx.x; x < kH2B * kH2B; x += blockDim.x) {
+        const int nu = x / kH2B, mu = x % kH2B;
+        double v = 0.0;
+        if (nu < k && mu < k) {
+            const double d = xo[3 * nu] * xc[3 * mu] + xo[3 * nu + 1] * xc[3 * mu + 1] +
+                             xo[3 * nu + 2] * xc[3 * mu + 2];
+            v = f * hg(s * d, g, c0);
+        }
+        D[x] = __float2bfloat16_rn((float)v);
+    }
+}
+
 struct DevList {
     int nout = 0, nnz = 0;
     int *out_blk = nullptr, *ptr = nullptr, *in_blk = nullptr, *mat = nullptr;
@@ -393,7 +584,55 @@ struct H2Parity {
     float* pool32 = nullptr;
     DevList up_leaf, couple, down_leaf, near;
     std::vector<DevList> up, down;
+    // tensor-core (BF16) apply: matrices in the K-major layout and the same
+    // lists with matrix indices into that pool
+    __nv_bfloat16* tcpool = nullptr;
+    long long tc_total = 0;
+    DevList tc_up_leaf, tc_couple, tc_down_leaf, tc_near;
+    std::vector<DevList> tc_up, tc_down;
 };
+
+int run_tc(cudaStream_t s, const DevList& L, int rows, const void* In, long long ldi,
+           const __nv_bfloat16* tcpool, long long tc_total, void* Out, long long ldo, bool out_f32,
+           bool accum) {
+    if (L.nout == 0 || rows == 0) return RTE_OK;
+    CUtensorMap ma, mb;
+    RTE_TRY(tc::make_map(&ma, In, false, rows, (int)ldi, kTcRows));
+    RTE_TRY(tc::make_map(&mb, tcpool, false, (int)(tc_total * kH2B), kH2B, kH2B));
+    const int rtiles = (rows + kTcRows - 1) / kTcRows;
+    const long long grid = (long long)((L.nout + kGroup - 1) / kGroup) * kGroup * rtiles;
+    if (grid > 0x7fffffffLL) return fail(RTE_ERR_ARG, "H2 apply: too many rows for one launch");
+    const size_t sm = tc_smem_bytes();
+    static const bool attr = [sm] {
+        cudaFuncSetAttribute(k_h2_tc<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_h2_tc<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_h2_tc<false, __nv_bfloat16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_h2_tc<true, __nv_bfloat16>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        return true;
+    }();
+    (void)attr;
+    if (out_f32) {
+        float* o = static_cast<float*>(Out);
+        if (accum)
+            k_h2_tc<true, float><<<(unsigned)grid, 128, sm, s>>>(ma, mb, rows, rtiles, L.nout, o, ldo,
+                                                                 L.out_blk, L.ptr, L.in_blk, L.mat);
+        else
+            k_h2_tc<false, float><<<(unsigned)grid, 128, sm, s>>>(ma, mb, rows, rtiles, L.nout, o, ldo,
+                                                                  L.out_blk, L.ptr, L.in_blk, L.mat);
+    } else {
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(Out);
+        if (accum)
+            k_h2_tc<true, __nv_bfloat16><<<(unsigned)grid, 128, sm, s>>>(
+                ma, mb, rows, rtiles, L.nout, o, ldo, L.out_blk, L.ptr, L.in_blk, L.mat);
+        else
+            k_h2_tc<false, __nv_bfloat16><<<(unsigned)grid, 128, sm, s>>>(
+                ma, mb, rows, rtiles, L.nout, o, ldo, L.out_blk, L.ptr, L.in_blk, L.mat);
+    }
+    count_launches(1);
+    return RTE_OK;
+}
 
 template <typename T, int kMode, bool kAccum>
 int run_list(cudaStream_t s, const DevList& L, int rows, int k, int parity, const T* In,
@@ -513,6 +752,83 @@ int h2_apply_t(rte_h2* h, int q, const T* X, T* Y, int rows, T* Xh, T* Yh, cudaS
 
 }  // namespace
 
+namespace {
+
+// Tensor-core pool of one parity (K-major Bt[output][input] matrices, BF16):
+// [leaf V^T | leaf V | E^T | E | couplings | near blocks^T] and the lists
+// with matrix indices into it.
+int build_tc(rte_h2* h, int q, const rte::H2Lists& lists, cudaStream_t s) {
+    using namespace rte;
+    const H2Plan& P = h->plan;
+    H2Parity& hp = h->par[q];
+    const H2Pool& pl = hp.pool;
+    const long long Lc = pl.transfer0 - pl.leaf0, T = pl.near0 - pl.transfer0,
+                    N = pl.total - pl.near0, F = (long long)lists.couple.in_blk.size();
+    const long long Vt0 = 0, V0 = Lc, Et0 = 2 * Lc, E0 = 2 * Lc + T, C0 = 2 * Lc + 2 * T,
+                    N0 = C0 + F;
+    hp.tc_total = N0 + N;
+    hp.tcpool = dalloc<__nv_bfloat16>(h, (size_t)hp.tc_total * kH2B * kH2B);
+    if (!hp.tcpool) return fail(RTE_ERR_NOMEM, "H2 tensor-core matrices");
+    std::vector<long long> src, dst;
+    std::vector<unsigned char> tr;
+    auto add = [&](long long a, long long b, bool t) {
+        src.push_back(a);
+        dst.push_back(b);
+        tr.push_back(t ? 1 : 0);
+    };
+    for (long long i = 0; i < Lc; ++i) {
+        add(pl.leaf0 + i, Vt0 + i, true);
+        add(pl.leaf0 + i, V0 + i, false);
+    }
+    for (long long i = 0; i < T; ++i) {
+        add(pl.transfer0 + i, Et0 + i, true);
+        add(pl.transfer0 + i, E0 + i, false);
+    }
+    for (long long i = 0; i < N; ++i) add(pl.near0 + i, N0 + i, true);
+    std::vector<int> out_of(F);
+    for (size_t r = 0; r + 1 < lists.couple.ptr.size(); ++r)
+        for (int e = lists.couple.ptr[r]; e < lists.couple.ptr[r + 1]; ++e)
+            out_of[e] = lists.couple.out_blk[r];
+    long long* dsrc = upload(h, src, s);
+    long long* ddst = upload(h, dst, s);
+    unsigned char* dtr = upload(h, tr, s);
+    int* dout = upload(h, out_of, s);
+    if (!dsrc || !ddst || !dtr || !dout) return fail(RTE_ERR_NOMEM, "H2 tensor-core set-up");
+    if (!src.empty()) k_h2_tc_copy<<<(unsigned)src.size(), 256, 0, s>>>(hp.pool64, dsrc, ddst, dtr,
+                                                                        hp.tcpool);
+    if (F > 0)
+        k_h2_tc_couple<<<(unsigned)F, 256, 0, s>>>(P.k, q == 0 ? 1 : -1, h->g, h->xi64, dout,
+                                                   hp.couple.in_blk, hp.couple.mat, hp.tcpool, C0);
+    count_launches((src.empty() ? 0 : 1) + (F > 0 ? 1 : 0));
+    // the lists with tensor-core matrix indices
+    auto remap = [&](const H2List& l, long long base, long long from, DevList& d) {
+        H2List c = l;
+        for (size_t e = 0; e < c.mat.size(); ++e)
+            c.mat[e] = (int)(base + (from < 0 ? (long long)e : c.mat[e] - from));
+        return upload_list(h, c, d, s);
+    };
+    RTE_TRY(remap(lists.up_leaf, Vt0, pl.leaf0, hp.tc_up_leaf));
+    RTE_TRY(remap(lists.down_leaf, V0, pl.leaf0, hp.tc_down_leaf));
+    RTE_TRY(remap(lists.couple, C0, -1, hp.tc_couple));
+    RTE_TRY(remap(lists.near, N0, pl.near0, hp.tc_near));
+    hp.tc_up.resize(lists.up.size());
+    hp.tc_down.resize(lists.down.size());
+    for (size_t d = 0; d < lists.up.size(); ++d) {
+        RTE_TRY(remap(lists.up[d], Et0, pl.transfer0, hp.tc_up[d]));
+        RTE_TRY(remap(lists.down[d], E0, pl.transfer0, hp.tc_down[d]));
+    }
+    return RTE_OK;
+}
+
+}  // namespace
+
+namespace rte {
+int h2_set_wait_cycles(long long cycles) {
+    RTE_CUDA_TRY(cudaMemcpyToSymbol(tc::g_tc_wait_cycles, &cycles, sizeof(cycles)));
+    return RTE_OK;
+}
+}  // namespace rte
+
 extern "C" {
 
 int rte_h2_default_options(rte_h2_options* o) {
@@ -522,7 +838,7 @@ int rte_h2_default_options(rte_h2_options* o) {
     o->eta = 1.4;
     o->p = 4;
     o->parities = 3;
-    o->precisions = 3;
+    o->precisions = 7;
     return RTE_OK;
 }
 
@@ -536,8 +852,8 @@ int rte_h2_create(const rte_h2_options* o, void* stream, rte_h2** out) {
     if (!(o->eta > 0.0 && o->eta < 1e6)) return fail(RTE_ERR_ARG, "H2: eta must be positive");
     if (o->p < 2 || o->p > 4) return fail(RTE_ERR_ARG, "H2: p must be in [2, 4]");
     if (o->parities < 1 || o->parities > 3) return fail(RTE_ERR_ARG, "H2: parities must be 1, 2 or 3");
-    if (o->precisions < 1 || o->precisions > 3)
-        return fail(RTE_ERR_ARG, "H2: precisions must be 1, 2 or 3");
+    if (o->precisions < 1 || o->precisions > 7)
+        return fail(RTE_ERR_ARG, "H2: precisions must be a mask of 1 (FP64), 2 (FP32), 4 (BF16)");
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
@@ -581,7 +897,7 @@ int rte_h2_create(const rte_h2_options* o, void* stream, rte_h2** out) {
     h->precisions = o->precisions;
     h->qf = qf;
     h->qn = qn;
-    const bool f64 = o->precisions & 1, f32 = o->precisions & 2;
+    const bool f64 = o->precisions & 1, f32 = o->precisions & 2, tcb = o->precisions & 4;
 
     // pools and lists per parity; memory check before any allocation
     H2Lists lists[2];
@@ -594,6 +910,8 @@ int rte_h2_create(const rte_h2_options* o, void* stream, rte_h2** out) {
         hp.pool = h2_pool(P, hp.m);
         h2_lists(P, hp.pool, lists[q]);
         need += (size_t)hp.pool.total * kH2B * kH2B * (8 + (f32 ? 4 : 0));
+        if (tcb)
+            need += (size_t)(2 * hp.pool.total + lists[q].couple.in_blk.size()) * kH2B * kH2B * 2;
     }
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
@@ -682,6 +1000,7 @@ int rte_h2_create(const rte_h2_options* o, void* stream, rte_h2** out) {
             rc = upload_list(h, lists[q].up[d], hp.up[d], s);
             if (rc == RTE_OK) rc = upload_list(h, lists[q].down[d], hp.down[d], s);
         }
+        if (rc == RTE_OK && tcb) rc = build_tc(h, q, lists[q], s);
     }
     if (rc == RTE_OK) {
         const cudaError_t e = cudaStreamSynchronize(s);
@@ -725,11 +1044,11 @@ int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* 
     if (parity != 1 && parity != -1) return fail(RTE_ERR_ARG, "H2 apply: parity must be +1 or -1");
     const int q = parity > 0 ? 0 : 1;
     if (!h->par[q].on) return fail(RTE_ERR_ARG, "H2 apply: this parity was not built");
-    if (precision != RTE_FP64 && precision != RTE_MIXED_FP32)
-        return fail(RTE_ERR_ARG, "H2 apply: precision must be RTE_FP64 or RTE_MIXED_FP32");
-    const bool fp64 = precision == RTE_FP64;
-    if ((fp64 && !(h->precisions & 1)) || (!fp64 && !(h->precisions & 2)))
-        return fail(RTE_ERR_ARG, "H2 apply: this precision was not built");
+    if (precision != RTE_FP64 && precision != RTE_MIXED_FP32 && precision != RTE_MIXED_BF16)
+        return fail(RTE_ERR_ARG, "H2 apply: precision must be RTE_FP64, RTE_MIXED_FP32 or RTE_MIXED_BF16");
+    const bool fp64 = precision == RTE_FP64, bf16 = precision == RTE_MIXED_BF16;
+    const int bit = fp64 ? 1 : (bf16 ? 4 : 2);
+    if (!(h->precisions & bit)) return fail(RTE_ERR_ARG, "H2 apply: this precision was not built");
     if (rows < 0) return fail(RTE_ERR_ARG, "H2 apply: rows must be >= 0");
     if (rows == 0) return RTE_OK;
     if (!X || !Y) return fail(RTE_ERR_ARG, "H2 apply: NULL array");
@@ -738,8 +1057,9 @@ int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const H2Plan& P = h->plan;
     const size_t ncols = (size_t)P.n * h->par[q].m, nh = (size_t)P.ncl * kH2B;
-    const size_t w = fp64 ? 8 : 4;
-    size_t need = 2 * (size_t)rows * nh * w + (fp64 ? 0 : 2 * (size_t)rows * ncols * 4) + 256;
+    const size_t w = fp64 ? 8 : (bf16 ? 2 : 4);
+    size_t need = 2 * (size_t)rows * nh * w + 1024;
+    if (!fp64) need += (size_t)rows * ncols * (bf16 ? 2 : 4) + (size_t)rows * ncols * 4;
     if (need > h->work_bytes) {
         if (h->work) {
             cudaStreamSynchronize(s);
@@ -754,7 +1074,39 @@ int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* 
         h->work_bytes = need;
     }
     char* wb = static_cast<char*>(h->work);
-    if (fp64) {
+    if (bf16) {
+        const H2Parity& hp = h->par[q];
+        __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(wb);
+        __nv_bfloat16* Yh = Xh + (size_t)rows * nh;
+        __nv_bfloat16* Xb = Yh + (size_t)rows * nh;
+        float* Y32 = reinterpret_cast<float*>(
+            wb + ((2 * (size_t)rows * nh + (size_t)rows * ncols) * 2 + 255) / 256 * 256);
+        const long long ldx = (long long)ncols, ldh = (long long)nh;
+        convert(s, X, Xb, (size_t)rows * ncols);
+        RTE_TRY(run_tc(s, hp.tc_up_leaf, rows, Xb, ldx, hp.tcpool, hp.tc_total, Xh, ldh, false, false));
+        for (int d = P.ld - 1; d >= P.dmin; --d)
+            RTE_TRY(run_tc(s, hp.tc_up[d - P.dmin], rows, Xh, ldh, hp.tcpool, hp.tc_total, Xh, ldh,
+                           false, false));
+        cudaMemsetAsync(Yh, 0, (size_t)rows * nh * 2, s);
+        RTE_TRY(run_tc(s, hp.tc_couple, rows, Xh, ldh, hp.tcpool, hp.tc_total, Yh, ldh, false, false));
+        for (int d = P.dmin; d < P.ld; ++d)
+            RTE_TRY(run_tc(s, hp.tc_down[d - P.dmin], rows, Yh, ldh, hp.tcpool, hp.tc_total, Yh, ldh,
+                           false, true));
+        RTE_TRY(run_tc(s, hp.tc_down_leaf, rows, Yh, ldh, hp.tcpool, hp.tc_total, Y32, ldx, true,
+                       false));
+        RTE_TRY(run_tc(s, hp.tc_near, rows, Xb, ldx, hp.tcpool, hp.tc_total, Y32, ldx, true, true));
+        convert(s, Y32, Y, (size_t)rows * ncols);
+        // the pipelines' bounded waits: read the timeout flag (synchronises)
+        int flag = 0;
+        RTE_CUDA_TRY(cudaMemcpyFromSymbolAsync(&flag, tc::g_tc_error, sizeof(int), 0,
+                                               cudaMemcpyDeviceToHost, s));
+        RTE_CUDA_TRY(cudaStreamSynchronize(s));
+        if (flag) {
+            const int zero = 0;
+            cudaMemcpyToSymbolAsync(tc::g_tc_error, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s);
+            return fail(RTE_ERR_TIMEOUT, "H2 apply: a tensor-core pipeline wait timed out");
+        }
+    } else if (fp64) {
         double* Xh = reinterpret_cast<double*>(wb);
         double* Yh = Xh + (size_t)rows * nh;
         RTE_TRY(h2_apply_t<double>(h, q, X, Y, rows, Xh, Yh, s));

@@ -68,4 +68,7 @@ struct H2Lists {
 };
 void h2_lists(const H2Plan& P, const H2Pool& pool, H2Lists& L);
 
+// Limit of one mbarrier wait of the tensor-core H^2 products (SM cycles).
+int h2_set_wait_cycles(long long cycles);
+
 }  // namespace rte

@@ -15,6 +15,7 @@
 #include "mg_host.h"
 #include "rte_internal.h"
 #include "tc_gemm.h"
+#include "h2.h"
 #include "tune.h"
 
 namespace rte {
@@ -2341,6 +2342,7 @@ int rte_set_wait_limit(double seconds) {
     RTE_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
     const long long cycles = (long long)(seconds * 1e3 * std::max(khz, 1));
     RTE_TRY(e0_set_wait_cycles(cycles));
+    RTE_TRY(h2_set_wait_cycles(cycles));
     return tc_set_wait_cycles(cycles);
 }
 

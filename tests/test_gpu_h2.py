@@ -3,7 +3,10 @@ oracle's H^2 approximation.
 
 * the block tree the library builds has the oracle's far and near blocks;
 * Y = X S^+ and Y = X S^- element by element against the oracle's
-  approximated matrix: FP64 to 1e-12, FP32 to 2e-5 (relative to max|Y|), at
+  approximated matrix: FP64 to 1e-12, FP32 to 2e-5, BF16 on the tensor
+  cores to 16 unit roundoffs of BF16 (about ten roundings in sequence along
+  the far-field path: operands, bases, coefficients per level), relative
+  to max|Y|, at
   n_S^+ = 1024 (far blocks at the leaf depth only) and n_S^+ = 4096 (far
   blocks on two depths: the transfer matrices), ragged row counts;
 * n_S^+ = 256 has no admissible block: the apply is the dense matrix;
@@ -68,9 +71,11 @@ def test_apply_matches_oracle(h2lib, levels, parity, rows):
     xt = torch.tensor(X, dtype=torch.float64, device='cuda')
     y64 = h.apply(xt, parity=parity, precision=rte.FP64).cpu().numpy()
     y32 = h.apply(xt, parity=parity, precision=rte.MIXED_FP32).cpu().numpy()
+    ybf = h.apply(xt, parity=parity, precision=rte.MIXED_BF16).cpu().numpy()
     scale = np.abs(ref).max()
     assert np.abs(y64 - ref).max() <= 1e-12 * scale
     assert np.abs(y32 - ref).max() <= 2e-5 * scale
+    assert np.abs(ybf - ref).max() <= 16 * 2.0 ** -9 * scale
 
 
 def test_no_admissible_block_is_dense(h2lib):
@@ -110,6 +115,8 @@ def test_rows_zero_and_refusals(h2lib):
         x = torch.zeros((4, h.n_plus), dtype=torch.float64, device='cuda')
         with pytest.raises(rte.RteError, match='precision was not built'):
             h.apply(x, precision=rte.MIXED_FP32)
+        with pytest.raises(rte.RteError, match='precision was not built'):
+            h.apply(x, precision=rte.MIXED_BF16)
         big = torch.zeros((4 * h.n_plus + 1,), dtype=torch.float64, device='cuda')
         xm = big[1:].view(4, h.n_plus)
         with pytest.raises(rte.RteError, match='16-byte aligned'):

@@ -215,7 +215,7 @@ def test_memory_estimate_grows_with_the_problem(lib_path):
     ('eta', 0.0, 'eta must be positive'),
     ('p', 5, 'p must be in [2, 4]'),
     ('parities', 0, 'parities'),
-    ('precisions', 4, 'precisions')])
+    ('precisions', 8, 'precisions')])
 def test_h2_create_refuses_bad_options_on_the_host(lib_path, field, value, words):
     # rte_h2_create checks every option before touching the device
     import ctypes
@@ -223,7 +223,7 @@ def test_h2_create_refuses_bad_options_on_the_host(lib_path, field, value, words
     lib = rte.load()
     o = rte._H2Options()
     assert lib.rte_h2_default_options(ctypes.byref(o)) == 0
-    assert (o.eta, o.p, o.parities, o.precisions) == (1.4, 4, 3, 3)
+    assert (o.eta, o.p, o.parities, o.precisions) == (1.4, 4, 3, 7)
     setattr(o, field, value)
     h = ctypes.c_void_p()
     rc = lib.rte_h2_create(ctypes.byref(o), None, ctypes.byref(h))
