@@ -63,6 +63,9 @@ def parse():
     ap.add_argument('--mk-routes', action='store_true',
                     help='time the eigenbasis and the PCG (Algorithm 1) routes of '
                          '(M^- - K^-)^{-1} on the 128x128 and 96x96 workloads and exit')
+    ap.add_argument('--params', action='store_true',
+                    help='time to 1e-6 on the benchmark workload (mixed BF16) over the method '
+                         'parameters N^+, l and the coarse tolerance, and exit')
     ap.add_argument('--h2', action='store_true',
                     help='time the H^2-compressed S^+ apply against the dense products over '
                          'n_S^+ = 1024 .. 65536 (the paper\'s compression table) and exit')
@@ -797,6 +800,39 @@ def mk_routes_study(args):
     return out
 
 
+def params_study(args):
+    """Time to 1e-6 on the benchmark workload (128 x 128 mesh, 512 triangles,
+    g = 0.9, c = 0.99, mixed BF16) over the method's parameters: the degree
+    N^+ of the subspace correction (d^+ = 1, 6, 15), the steps l of P_1 and
+    the tolerance of the coarse CG; each solve from u = 0, CUDA-event timed
+    after one untimed solve, its oracle-free residual the library's FP64
+    one."""
+    import torch
+    import workloads
+    import paper_2102_09038_gb300 as rte
+    torch.cuda.set_device(0)
+    p = workloads.checkerboard(m=args.mesh, levels=args.levels, g=0.9, ratio=0.99, seed=0)
+    qn = torch.tensor(p.q_nodal, dtype=torch.float64, device='cuda')
+    out = []
+    for n_plus in (0, 2, 4):
+        for l in (2, 3, 4, 6):
+            for ctol in (0.1, 0.3):
+                s = rte.Solver(p, precision=rte.MIXED_BF16, n_plus=n_plus, l=l, coarse_tol=ctol,
+                               max_iter=400)
+                try:
+                    t, info, _ = timed_solve(s, s.rhs(qn), p.tol)
+                    row = dict(n_plus=n_plus, d_plus=s.d_plus, l=l, coarse_tol=ctol,
+                               time_to_tol_s=t, iterations=info['iterations'],
+                               coarse_iters_last=info['coarse_iters'],
+                               rel_residual=info['rel_residual'])
+                except RuntimeError as e:
+                    row = dict(n_plus=n_plus, l=l, coarse_tol=ctol, failed=str(e)[:100])
+                s.close()
+                out.append(row)
+                print(json.dumps(row), flush=True)
+    return out
+
+
 def h2_study(args):
     """Dense against H^2-compressed S^+ (Section 5.2; the compression table
     of Section 6): for n_S^+ = 4 * 4^levels, g = 0.5 and the paper's
@@ -916,6 +952,9 @@ if __name__ == '__main__':
         sys.exit(0)
     if a.h2:
         h2_study(a)
+        sys.exit(0)
+    if a.params:
+        params_study(a)
         sys.exit(0)
     if a.impl == 'reference':
         run_reference(a)
