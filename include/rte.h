@@ -130,10 +130,12 @@ typedef struct {
 } rte_problem;
 
 /* Method parameters.  Defaults (rte_default_options) follow Section 6:
- * l = 4 inner steps for P_1^l, N^+ = 4 (d^+ = 15) for the subspace
- * correction, N^- = 5 (d^- = 21) for the preconditioner of (M^- - K^-). */
+ * l = 4 inner steps for P_1^l (2 for the PCG realisation of P_1), N^+ = 4
+ * (d^+ = 15) for the subspace correction, N^- = 5 (d^- = 21) for the
+ * preconditioner of (M^- - K^-). */
 typedef struct {
-    int l;                  /* steps of P_1^l, eq. (applyP1)                 */
+    int l;                  /* steps of P_1 (eq. applyP1); 0: 4 for P_1^l
+                               (Section 6), 2 for the PCG steps              */
     int n_plus;             /* even degree N^+ (0, 2, 4, ...); -1: no P_2    */
     int n_minus;            /* odd degree N^- (1, 3, 5, ...)                 */
     int precision;          /* RTE_FP64 | RTE_MIXED_FP32 | RTE_MIXED_BF16    */
@@ -145,7 +147,7 @@ typedef struct {
                                0: 1e-12 (FP64) or 0.3 (mixed modes)          */
     int e0_maxit;
     double coarse_tol;      /* relative residual of the E_c CG;
-                               0: 1e-12 (FP64) or 0.1 (mixed modes)          */
+                               0: 1e-12 (FP64) or 0.3 (mixed modes)          */
     int coarse_maxit;
     int max_iter;           /* outer Richardson iterations                   */
     int max_rhs;            /* workspace is sized for this many RHS          */

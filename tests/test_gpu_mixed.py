@@ -76,7 +76,7 @@ def mixed(request):
     p = CASES[name]()
     disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
     ops = oracle.Operators(disc, n_plus=2, n_minus=3)
-    s = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, max_rhs=3)
+    s = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, max_rhs=3, l=4)
     yield p, disc, ops, s, prec
     s.close()
 
@@ -150,7 +150,8 @@ def test_autotuned_launch_shapes(prec):
 @pytest.mark.parametrize('prec', [0, 2])
 def test_p1_pcg_route_solves(prec):
     # Algorithm 3 with P_1 as l PCG steps (RTE_P1_PCG) reaches the FP64
-    # residual in FP64 and in the mixed BF16 mode
+    # residual in FP64 and in the mixed BF16 mode; l left at 0 resolves to
+    # two steps on this route (two E_0^{-1} per P_1)
     import paper_2102_09038_gb300 as rte
     p = workloads.checkerboard(m=24, levels=2, g=0.8, ratio=0.97, blocks=4, nrhs=2)
     disc = oracle.Discretisation(p.m, p.levels, p.sigma_t, p.sigma_s, p.g)
@@ -160,7 +161,7 @@ def test_p1_pcg_route_solves(prec):
     u, info = s.solve(q, tol=1e-10)
     s.close()
     assert info['status'] == 0, info
-    assert info['e0_launches'] == 4 * info['iterations'], info
+    assert info['e0_launches'] == 2 * info['iterations'], info
     u = u.cpu().numpy()
     for r in range(p.nrhs):
         qr = disc.source(p.q_nodal[r])

@@ -256,7 +256,7 @@ def test_p1_pcg_route(case):
     # against the oracle's PCG, and Algorithm 3 with it against the oracle's
     # Algorithm 3 with the same P_1
     import paper_2102_09038_gb300 as rte
-    pr = Pair(case, p1_route=rte.P1_PCG)
+    pr = Pair(case, p1_route=rte.P1_PCG, l=4)
     try:
         ops, p = pr.ops, pr.p
         b = pr.even(2)

@@ -42,7 +42,8 @@ def test_binding_loads_without_gpu(lib_path):
     for name in declared_symbols():
         assert hasattr(lib, name)
     o = rte.default_options()
-    assert (o.l, o.n_plus, o.n_minus) == (4, 4, 5)   # Section 6 defaults
+    # Section 6 defaults; l = 0 resolves per P_1 route at set-up
+    assert (o.l, o.n_plus, o.n_minus) == (0, 4, 5)
 
 
 def test_solver_refuses_without_cuda(lib_path):
@@ -168,7 +169,7 @@ def _setup_rc(problem_kw=None, **opts):
     (dict(g=1.0), {}, 'g must'),
     (dict(sigma_s=1.0), {}, 'sigma_s < sigma_t'),
     (dict(sigma_t=-1.0, sigma_s=0.0), {}, 'sigma_s < sigma_t'),
-    ({}, dict(l=0), 'invalid options'),
+    ({}, dict(l=-1), 'invalid options'),
     ({}, dict(n_minus=4), 'invalid options'),
     ({}, dict(n_plus=3), 'invalid options'),
     ({}, dict(max_rhs=0), 'invalid options'),
