@@ -197,12 +197,13 @@ def fp64_peak_tflops(torch):
 PROFILED_DRAM = {
     'coarse_cg': dict(source='paper_2102_09038_gb300/csrc/mg.cu', sha='e29a65ac179f3b0b',
                       workload='checkerboard_128x128_T512_g0.90_c0.99',
-                      bytes_per_launch=4.249e9,
-                      note='ncu launch list, 16 launches of k_ec_pcg<0> in one solve'),
+                      bytes_per_launch=1.829e9, coarse_iters=5,
+                      note='ncu launch list, 16 launches of k_ec_pcg<0> in one solve '
+                           '(5 CG iterations each)'),
     'e0_direct': dict(source='paper_2102_09038_gb300/csrc/e0_direct.cu', sha='170f9aa09a001022',
                       workload='checkerboard_128x128_T512_g0.90_c0.99',
-                      bytes_per_launch=4.744e9,
-                      note='ncu launch list, 64 launches of k_e0_direct_tma in one solve'),
+                      bytes_per_launch=4.736e9,
+                      note='ncu launch list, 32 launches of k_e0_direct_tma in one solve'),
 }
 
 
@@ -389,6 +390,8 @@ def run_ours(args):
         elif (prof['workload'] != WORKLOAD['workload'] or args.mesh != WORKLOAD['mesh']
               or 8 * 4 ** args.levels != WORKLOAD['sphere_triangles']):
             traffic_note = 'ncu capture taken on another workload'
+        elif prof.get('coarse_iters') not in (None, last_info.get('coarse_iters')):
+            traffic_note = 'ncu capture taken at another coarse iteration count'
         else:
             traffic = prof['bytes_per_launch']
             traffic_note = prof['note']
