@@ -27,6 +27,8 @@ struct DevLow {
     const void* VmT;           // GEMM 1 second operand (N x K = V^T)
     const void* Vm;            // GEMM 2 second operand (N x K = V)
     const void* Sp;            // scattering second operand (S^+, symmetric)
+    const float* WpN;          // [nSp][dP]: restriction to the coarse space
+    const float* WpNT;         // [dP][nSp]: prolongation
     bool bf16;                 // operand type: BF16, else FP32 (TF32 MMA)
 };
 
@@ -138,6 +140,15 @@ void axpby_per_rhs(cudaStream_t s, const float* x, float* y, size_t len, int nrh
 // x uniform in [-1, 1), a counter-based function of (seed, index)
 void fill_uniform(cudaStream_t s, double* x, size_t n, unsigned long long seed);
 void convert(cudaStream_t s, const double* x, float* y, size_t n);
+
+// Restriction qc = x W (rows x nSp times nSp x dP) and prolongation
+// x = beta x + uc W^T, one warp per row, for dP <= 16 (false otherwise: the
+// caller falls back to the general GEMM); W, WT in FP64 or FP32 (products and
+// sums in that type, FP64 vectors at the interface).
+bool restrict_rows(cudaStream_t s, int rows, int nSp, int dP, const double* x, const double* W,
+                   const float* W32, double* qc);
+bool prolong_rows(cudaStream_t s, int rows, int nSp, int dP, const double* uc, const double* WT,
+                  const float* WT32, double* x, double beta);
 void convert(cudaStream_t s, const float* x, double* y, size_t n);
 void convert(cudaStream_t s, const float* x, __nv_bfloat16* y, size_t n);
 void convert(cudaStream_t s, const double* x, __nv_bfloat16* y, size_t n);

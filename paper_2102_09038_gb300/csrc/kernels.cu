@@ -725,6 +725,87 @@ void fill_uniform(cudaStream_t s, double* x, size_t n, unsigned long long seed) 
     k_fill_uniform<<<grid_for(n), kThreads, 0, s>>>(x, n, seed);
 }
 
+
+// ------------------------------------------ restriction and prolongation
+// qc[row][j] = sum_k x[row][k] W[k][j], one warp per row: lanes stride over
+// k with 16 partial sums each, reduced across the warp by halving exchanges
+// (31 shuffles leave lane j holding the sum of column j mod 16).
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(int rows, int nSp, int dP, const double* __restrict__ x,
+                                                  const T* __restrict__ W, double* __restrict__ qc) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    T v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = T(0);
+    const double* xr = x + (size_t)row * nSp;
+    for (int k = lane; k < nSp; k += 32) {
+        const T xv = (T)__ldg(xr + k);
+        const T* w = W + (size_t)k * dP;
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < dP) v[j] = fma(xv, __ldg(w + j), v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
+#pragma unroll
+    for (int o = 8; o >= 1; o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const T send = up ? v[i] : v[i + o];
+            const T keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    if (lane < dP) qc[(size_t)row * dP + lane] = (double)v[0];
+}
+
+// x[row][k] = beta x[row][k] + sum_j uc[row][j] WT[j][k], one warp per row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(int rows, int nSp, int dP, const double* __restrict__ uc,
+                                                 const T* __restrict__ WT, double* __restrict__ x,
+                                                 double beta) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const T mine = lane < dP ? (T)uc[(size_t)row * dP + lane] : T(0);
+    T u[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) u[j] = __shfl_sync(0xffffffffu, mine, j);
+    double* xr = x + (size_t)row * nSp;
+    for (int k = lane; k < nSp; k += 32) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < dP) acc = fma(u[j], __ldg(WT + (size_t)j * nSp + k), acc);
+        xr[k] = beta == 0.0 ? (double)acc : beta * xr[k] + (double)acc;
+    }
+}
+
+bool restrict_rows(cudaStream_t s, int rows, int nSp, int dP, const double* x, const double* W,
+                   const float* W32, double* qc) {
+    if (dP < 1 || dP > 16 || rows <= 0) return false;
+    const unsigned blocks = (unsigned)(((size_t)rows * 32 + 255) / 256);
+    count_launches(1);
+    if (W32)
+        k_restrict<float><<<blocks, 256, 0, s>>>(rows, nSp, dP, x, W32, qc);
+    else
+        k_restrict<double><<<blocks, 256, 0, s>>>(rows, nSp, dP, x, W, qc);
+    return true;
+}
+
+bool prolong_rows(cudaStream_t s, int rows, int nSp, int dP, const double* uc, const double* WT,
+                  const float* WT32, double* x, double beta) {
+    if (dP < 1 || dP > 16 || rows <= 0) return false;
+    const unsigned blocks = (unsigned)(((size_t)rows * 32 + 255) / 256);
+    count_launches(1);
+    if (WT32)
+        k_prolong<float><<<blocks, 256, 0, s>>>(rows, nSp, dP, uc, WT32, x, beta);
+    else
+        k_prolong<double><<<blocks, 256, 0, s>>>(rows, nSp, dP, uc, WT, x, beta);
+    return true;
+}
+
 void convert(cudaStream_t s, const double* x, float* y, size_t n) {
     count_launches(1);
     k_convert<double, float><<<grid_for(n), kThreads, 0, s>>>(x, y, n);

@@ -1422,19 +1422,27 @@ int apply_P1(rte_handle* h, const double* b, double* z, int nrhs) {
     return RTE_OK;
 }
 
+// The restriction and prolongation of the coarse correction: one warp per
+// row (d^+ <= 16), in FP32 products on mixed handles (a preconditioner step:
+// its coarse solve stops at coarse_tol), in FP64 otherwise; the general
+// FP64 GEMM for larger d^+.
 int restrict_(rte_handle* h, const double* x, double* qc, int nrhs) {
     const DevSystem& d = h->d;
     Scope sc(h, "restrict");
-    gemm_f64(h->stream, nrhs * d.nRp, d.dP, d.nSp, x, d.nSp, d.WpN, d.dP, qc, d.dP, 1.0, 0.0,
-             0, nullptr, nullptr, nullptr, 1);
+    if (!restrict_rows(h->stream, nrhs * d.nRp, d.nSp, d.dP, x, d.WpN, h->mixed ? d.lo.WpN : nullptr,
+                       qc))
+        gemm_f64(h->stream, nrhs * d.nRp, d.dP, d.nSp, x, d.nSp, d.WpN, d.dP, qc, d.dP, 1.0, 0.0,
+                 0, nullptr, nullptr, nullptr, 1);
     return RTE_OK;
 }
 
 int prolong_add(rte_handle* h, const double* uc, double* x, int nrhs, double beta) {
     const DevSystem& d = h->d;
     Scope sc(h, "prolong");
-    gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.dP, uc, d.dP, d.WpNT, d.nSp, x, d.nSp, 1.0, beta,
-             0, nullptr, nullptr, nullptr, 1);
+    if (!prolong_rows(h->stream, nrhs * d.nRp, d.nSp, d.dP, uc, d.WpNT,
+                      h->mixed ? d.lo.WpNT : nullptr, x, beta))
+        gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.dP, uc, d.dP, d.WpNT, d.nSp, x, d.nSp, 1.0,
+                 beta, 0, nullptr, nullptr, nullptr, 1);
     return RTE_OK;
 }
 
@@ -1916,6 +1924,13 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
         UPF(A2, hs.A2);
         UPF(e0s, hs.e0s);
         UPF(lamM, h->h_lamM);
+        UPF(WpN, h->h_WpN);
+        {
+            std::vector<double> wt((size_t)std::max(dP, 1) * n, 0.0);
+            for (int k = 0; k < n; ++k)
+                for (int a = 0; a < dP; ++a) wt[(size_t)a * n + k] = h->h_WpN[(size_t)k * dP + a];
+            UPF(WpNT, wt);
+        }
 #undef UPF
         // GEMM second operands, K-major: GEMM 1 multiplies by V (needs V^T),
         // GEMM 2 by V^T (needs V), the scattering product by S^+ = (S^+)^T

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -233,15 +234,21 @@ int tc_gemm_error(cudaStream_t s) {
 // splitting of the operands, after Ozaki, Ogita, Oishi and Rump).
 //
 // Every row of A (and of the K-major second operand Bt) is scaled by a power
-// of two 2^e so that its entries lie in (-1, 1), then cut into S digit
-// slices: r <- r * 2^7, d = rint(r), r <- r - d.  The digits are integers
-// with |d| <= 128, exact in BF16, and A = 2^e sum_s d_s 2^{-7(s+1)} up to a
-// remainder below 2^{-7S-1}.  A product of two digit slices summed over at
-// most 1024 terms is an integer below 2^24, so the tensor cores' FP32
-// accumulation of it is exact.  The kernel accumulates the slice pairs
-// (s, t) with s + t <= S - 1 (the others lie below the truncation level),
-// each in a tensor-memory buffer, into FP64 registers with its weight
-// 2^{-7(s+t+2)}, and finally applies the row and column scales.
+// of two 2^e so that its entries lie in (-1, 1), then cut into S balanced
+// base-128 digits d_s (|d_0| <= 128, |d_s| <= 64 for s > 0): A = 2^e sum_s
+// d_s 2^{-7(s+1)} up to a remainder below 2^{-7S-1}.  Slice s is stored
+// scaled, d_s 2^{-7s} (exact in BF16), so that the slice-pair products carry
+// their relative weights themselves:
+//   A Bt^T = 2^(ea + eb - 14) (P0 + P1 + P2 + P3),
+//   P0 = A_0 B_0,  P1 = A_0 B_1 + A_1 B_0,  P2 = A_0 B_2 + A_1 B_1 + A_2 B_0,
+//   P3 = sum_{3 <= s + t <= S-1} A_s B_t
+// (pairs with s + t >= S lie below the truncation level).  Over at most 512
+// terms of K, P0 is an integer below 2^23, P1 an integer multiple of 2^-7
+// below 2^16 and P2 one of 2^-14 below 2^10 (each term of P2 at most
+// 20480 2^-14), so the tensor cores' FP32 accumulation of each is exact;
+// they are folded into FP64 registers once per 512 of K.  P3 is 2^-21 of the
+// result or less and accumulates in FP32 over the whole K: its rounding
+// stays near 2^-45 of the result.
 // ======================================================================
 namespace rte {
 
@@ -249,13 +256,10 @@ namespace {
 
 using namespace tc;
 
-constexpr int kOzBM = 128, kOzBN = 128, kOzStages = 4, kOzKChunk = 16;   // 16 x 64 = 1024
-constexpr int kOzMaxPairs = 64;
-
-struct OzPairs {
-    int n;
-    unsigned char s[kOzMaxPairs], t[kOzMaxPairs];
-};
+constexpr int kOzBM = 128, kOzBN = 128, kOzKChunk = 8;    // 8 x 64 = 512 of K per fold
+constexpr int kOzMaxS = 9;
+constexpr uint32_t kOzTile = kOzBM * kRowBytes;            // 16 KB: one slice tile
+constexpr uint32_t kOzTmemCols = 512;                       // P0 .. P3: 4 x 128 columns
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -263,56 +267,53 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // 18 warps: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..17 drain
 // the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the
-// quarter (w - 2) / 4 of the 128 columns), so the producer and the MMA
-// issuer never wait on the epilogue's own arrivals.
+// quarter (w - 2) / 4 of the 128 columns of each accumulator).
 constexpr int kOzThreads = 576;
 constexpr int kOzEpiWarps = 16;
 
+// Per 64-wide K block the producer loads the S slices of the B tile into one
+// of nB resident sets, then streams the S slices of the A tile through a
+// ring of nA slots; the MMA issuer multiplies A slice s with B slices
+// t = 0 .. S-1-s into P0 .. P3.  Each tile of A and B is read once per
+// K block (the pair products reuse them from shared memory).
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-        int M, int N, int K, const OzPairs pairs, const int* __restrict__ ea,
+        int M, int N, int K, int S, int nA, int nB, const int* __restrict__ ea,
         const int* __restrict__ eb, double* __restrict__ C, int ldc, int epi,
         const double* __restrict__ at, const double* __restrict__ as,
         const double* __restrict__ lam, int rows) {
-    constexpr uint32_t kABytes = kOzBM * kRowBytes, kBBytes = kOzBN * kRowBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + kOzStages * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kOzStages * kBBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kOzStages + 4);
+    uint8_t* sB = smem;                                  // nB sets of S tiles
+    uint8_t* sA = smem + (size_t)nB * S * kOzTile;       // nA tiles
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)nA * kOzTile);
+    // fullA[4], emptyA[4], fullB[2], emptyB[2], accf, acce
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kOzBM, n0 = blockIdx.x * kOzBN;
     const int kblocks = (K + 63) / 64;
     const int nchunks = (kblocks + kOzKChunk - 1) / kOzKChunk;
-    const int jobs = pairs.n * nchunks;
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kOzStages),
-                   accf0 = smem_u32(bars + 2 * kOzStages), acce0 = smem_u32(bars + 2 * kOzStages + 2);
-    // slice-pair table in shared memory (a dynamically indexed kernel
-    // parameter would live in local memory)
-    __shared__ int s_ya[kOzMaxPairs], s_yb[kOzMaxPairs];
-    __shared__ float s_w[kOzMaxPairs];
-    for (int p = threadIdx.x; p < pairs.n; p += blockDim.x) {
-        s_ya[p] = pairs.s[p] * M + m0;
-        s_yb[p] = pairs.t[p] * N + n0;
-        s_w[p] = ldexpf(1.0f, -7 * (pairs.s[p] + pairs.t[p] + 2));
-    }
+    const uint32_t fullA0 = smem_u32(bars), emptyA0 = smem_u32(bars + 4),
+                   fullB0 = smem_u32(bars + 8), emptyB0 = smem_u32(bars + 10),
+                   accf = smem_u32(bars + 12), acce = smem_u32(bars + 13);
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kOzStages; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+        for (int i = 0; i < 4; ++i) {
+            mbar_init(fullA0 + 8 * i, 1);
+            mbar_init(emptyA0 + 8 * i, 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(accf0 + 8 * b, 1);
-            mbar_init(acce0 + 8 * b, kOzEpiWarps);   // one arrival per epilogue warp
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(fullB0 + 8 * i, 1);
+            mbar_init(emptyB0 + 8 * i, 1);
         }
+        mbar_init(accf, 1);
+        mbar_init(acce, kOzEpiWarps);   // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(256));
+                     "r"(kOzTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -323,46 +324,65 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
 
     if (warp == 0 && lane == 0) {
         // --------------------------------------------- TMA producer
-        int g = 0;
-        for (int j = 0; j < jobs && ok; ++j) {
-            const int p = j / nchunks, ch = j % nchunks;
-            const int ya = s_ya[p], yb = s_yb[p];
-            const int kb1 = min(kblocks, (ch + 1) * kOzKChunk);
-            for (int kb = ch * kOzKChunk; kb < kb1; ++kb, ++g) {
-                const int st = g % kOzStages;
-                const uint32_t ph = (g / kOzStages) & 1;
-                if (!mbar_wait(empty0 + 8 * st, ph ^ 1)) { ok = false; break; }
-                mbar_expect_tx(full0 + 8 * st, kABytes + kBBytes);
-                tma_load_2d(smem_u32(sA + st * kABytes), &mapA, full0 + 8 * st, kb * 64, ya);
-                tma_load_2d(smem_u32(sB + st * kBBytes), &mapB, full0 + 8 * st, kb * 64, yb);
+        int ga = 0;
+        for (int kb = 0; kb < kblocks && ok; ++kb) {
+            const int sb = kb % nB;
+            const uint32_t phb = (kb / nB) & 1;
+            if (!mbar_wait(emptyB0 + 8 * sb, phb ^ 1)) { ok = false; break; }
+            mbar_expect_tx(fullB0 + 8 * sb, (uint32_t)S * kOzTile);
+            for (int t = 0; t < S; ++t)
+                tma_load_2d(smem_u32(sB + ((size_t)sb * S + t) * kOzTile), &mapB, fullB0 + 8 * sb,
+                            kb * 64, t * N + n0);
+            for (int s = 0; s < S && ok; ++s, ++ga) {
+                const int sa = ga % nA;
+                const uint32_t pha = (ga / nA) & 1;
+                if (!mbar_wait(emptyA0 + 8 * sa, pha ^ 1)) { ok = false; break; }
+                mbar_expect_tx(fullA0 + 8 * sa, kOzTile);
+                tma_load_2d(smem_u32(sA + (size_t)sa * kOzTile), &mapA, fullA0 + 8 * sa, kb * 64,
+                            s * M + m0);
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------- MMA issuer
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                ((uint32_t)(kOzBN >> 3) << 17) | ((uint32_t)(kOzBM >> 4) << 24);
-        int g = 0;
-        for (int j = 0; j < jobs && ok; ++j) {
-            const int b = j & 1;
-            const uint32_t bph = (j >> 1) & 1;
-            if (!mbar_wait(acce0 + 8 * b, bph ^ 1)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dtm = tmem + (uint32_t)(b * kOzBN);
-            const int ch = j % nchunks;
-            const int kb0 = ch * kOzKChunk, kb1 = min(kblocks, kb0 + kOzKChunk);
-            for (int kb = kb0; kb < kb1 && ok; ++kb, ++g) {
-                const int st = g % kOzStages;
-                const uint32_t ph = (g / kOzStages) & 1;
-                if (!mbar_wait(full0 + 8 * st, ph)) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(sA + st * kABytes), b0 = smem_u32(sB + st * kBBytes);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    mma_issue(false, dtm, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk), idesc,
-                              (kb > kb0 || kk > 0) ? 1u : 0u);
-                mma_commit(empty0 + 8 * st);
+        int ga = 0;
+        unsigned started = 0;   // bit a: accumulator a holds a partial sum
+        for (int kb = 0; kb < kblocks && ok; ++kb) {
+            const int chunk = kb / kOzKChunk;
+            if (kb % kOzKChunk == 0) {
+                if (chunk > 0) {
+                    // P0, P1, P2 of the previous chunk drained by the epilogue
+                    if (!mbar_wait(acce, (chunk - 1) & 1)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                }
+                started &= 8u;
             }
-            mma_commit(accf0 + 8 * b);
+            const int sb = kb % nB;
+            const uint32_t phb = (kb / nB) & 1;
+            if (!mbar_wait(fullB0 + 8 * sb, phb)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t b0 = smem_u32(sB + (size_t)sb * S * kOzTile);
+            for (int s = 0; s < S && ok; ++s, ++ga) {
+                const int sa = ga % nA;
+                const uint32_t pha = (ga / nA) & 1;
+                if (!mbar_wait(fullA0 + 8 * sa, pha)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(sA + (size_t)sa * kOzTile);
+                for (int t = 0; s + t <= S - 1; ++t) {
+                    const int acc = s + t < 3 ? s + t : 3;
+                    const uint32_t dtm = tmem + (uint32_t)(acc * kOzBN);
+                    const uint32_t bt = b0 + (uint32_t)t * kOzTile;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_issue(false, dtm, sw128_desc(a0 + 32 * kk), sw128_desc(bt + 32 * kk),
+                                  idesc, (((started >> acc) & 1u) || kk > 0) ? 1u : 0u);
+                    started |= 1u << acc;
+                }
+                mma_commit(emptyA0 + 8 * sa);   // frees the A slot once its MMAs have read it
+            }
+            mma_commit(emptyB0 + 8 * sb);
+            if (kb % kOzKChunk == kOzKChunk - 1 || kb == kblocks - 1) mma_commit(accf);
         }
     }
     __syncwarp();
@@ -372,45 +392,33 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         __syncthreads();
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                         "r"(256));
+                         "r"(kOzTmemCols));
         return;
     }
     // ------------------------------------------------------------ epilogue
     const int wq = warp & 3, quarter = (warp - 2) >> 2;
-    // Double-float accumulators (hi + lo, about 48 significant bits): every
-    // job adds v 2^-7(s+t+2) with v an integer below 2^24, exact in FP32; the
-    // two-sum keeps the rounding error of each addition in lo.  FP32 runs at
-    // many times the FP64 rate of this GPU.
-    float hi[32], lo[32];
+    const uint32_t lanebase = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(quarter * 32);
+    double acc64[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-        hi[i] = 0.f;
-        lo[i] = 0.f;
-    }
-    for (int j = 0; j < jobs; ++j) {
-        const int b = j & 1;
-        const uint32_t bph = (j >> 1) & 1;
-        if (ok) ok = mbar_wait(accf0 + 8 * b, bph);
+    for (int i = 0; i < 32; ++i) acc64[i] = 0.0;
+    for (int c = 0; c < nchunks; ++c) {
+        if (ok) ok = mbar_wait(accf, c & 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float w = s_w[j / nchunks];
+        const bool last = c == nchunks - 1;
+        // P_a exists for S > a (an accumulator no MMA wrote is not read); P3
+        // is read once, after the last chunk
+        const int nacc = last ? (S < 4 ? S : 4) : (S < 3 ? S : 3);
 #pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * kOzBN + quarter * 32 + c0), v);
+        for (int c0 = 0; c0 < 32; c0 += 16)
+            for (int a = 0; a < nacc; ++a) {
+                float v[16];
+                tmem_ld16(lanebase + (uint32_t)(a * kOzBN + c0), v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float x = v[i] * w;                 // exact
-                const float sum = __fadd_rn(hi[c0 + i], x);
-                const float bb = __fsub_rn(sum, hi[c0 + i]);
-                const float err = __fadd_rn(__fsub_rn(hi[c0 + i], __fsub_rn(sum, bb)),
-                                            __fsub_rn(x, bb));
-                hi[c0 + i] = sum;
-                lo[c0 + i] = __fadd_rn(lo[c0 + i], err);
+                for (int i = 0; i < 16; ++i) acc64[c0 + i] += (double)v[i];
             }
-        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(acce0 + 8 * b);
+        if (lane == 0) mbar_arrive(acce);
     }
     const int row = m0 + wq * 32 + lane;
     if (ok && row < M) {
@@ -425,7 +433,7 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         for (int i = 0; i < 32; ++i) {
             const int col = n0 + quarter * 32 + i;
             if (col < N) {
-                double x = ldexp((double)hi[i] + (double)lo[i], er + eb[col]);
+                double x = ldexp(acc64[i], er + eb[col] - 14);
                 if (epi == 1) x = x / (fat - lam[col] * fas);
                 dst[col] = x;
             }
@@ -475,7 +483,8 @@ __global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int S,
         for (int s = S - 1; s >= 1; --s) {
             const long long d = ((v + 64) & 127) - 64;
             v = (v - d) >> 7;
-            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn((float)d);
+            // slice s stored as d 2^{-7s} (exact: a power-of-two scaling)
+            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn(ldexpf((float)d, -7 * s));
         }
         out[(size_t)row * K + k] = __float2bfloat16_rn((float)v);
     }
@@ -502,26 +511,35 @@ int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const 
                const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
                const double* as, const double* lam, int rows, int SB) {
     if (M <= 0 || N <= 0 || K <= 0) return RTE_OK;
-    if (S < 1 || S * (S + 1) / 2 > kOzMaxPairs) return fail(RTE_ERR_ARG, "bad slice count");
+    if (S < 1 || S > kOzMaxS) return fail(RTE_ERR_ARG, "bad slice count");
     if (SB == 0) SB = S;
     if (SB < S) return fail(RTE_ERR_ARG, "second operand has fewer slices than used");
-    OzPairs pairs{};
-    for (int a = 0; a < S; ++a)
-        for (int b = 0; a + b <= S - 1; ++b) {
-            pairs.s[pairs.n] = (unsigned char)a;
-            pairs.t[pairs.n] = (unsigned char)b;
-            ++pairs.n;
-        }
     CUtensorMap ma, mb;
     RTE_TRY(make_map(&ma, Aslices, false, S * M, K, kOzBM));
     RTE_TRY(make_map(&mb, Bslices, false, SB * N, K, kOzBN));
-    const size_t sm = 1024 + (size_t)kOzStages * (kOzBM + kOzBN) * kRowBytes +
-                      (2 * kOzStages + 4) * 8 + 16;
-    RTE_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)sm));
+    // resident B slice sets and A ring slots within the shared-memory limit:
+    // two B sets when they fit beside at least two A slots, else one
+    constexpr size_t kLimit = 227 * 1024 - 1024 - 16 * 8 - 64;
+    int nB = 2, nA = 4;
+    while (nA > 2 && (size_t)(nB * S + nA) * kOzTile > kLimit) --nA;
+    if ((size_t)(nB * S + nA) * kOzTile > kLimit) {
+        nB = 1;
+        nA = 4;
+        while (nA > 2 && (size_t)(nB * S + nA) * kOzTile > kLimit) --nA;
+    }
+    // at least half of the SM's shared memory, so that one block (and its 512
+    // tensor-memory columns) runs per SM
+    const size_t sm = std::max<size_t>(1024 + (size_t)(nB * S + nA) * kOzTile + 16 * 8 + 16,
+                                       116 * 1024);
+    static const bool attr = [] {
+        cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(227 * 1024));
+        return true;
+    }();
+    (void)attr;
     dim3 grid((N + kOzBN - 1) / kOzBN, (M + kOzBM - 1) / kOzBM);
     count_launches(1);
-    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, pairs, ea, eb, C, ldc, epi, at, as,
+    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, S, nA, nB, ea, eb, C, ldc, epi, at, as,
                                          lam, rows);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
