@@ -52,9 +52,8 @@ extern "C" {
  * are computed: RTE_DGEMM_AUTO picks SIMT in RTE_FP64 mode and SPLIT in the
  * mixed modes; RTE_DGEMM_SIMT uses FP64 arithmetic units; RTE_DGEMM_SPLIT
  * cuts the FP64 operands into exact BF16 digit slices whose tensor-core
- * products are summed in FP64 (truncation about S 2^-7S relative to the
- * operand scales for S slices; the FP32 sum of the lowest digit pairs adds
- * about 2^-45 of the scales, so 7 or more slices reach about 1e-14). */
+ * products are summed in FP64 (about S 2^-7S relative to the operand scales
+ * for S slices: 2^-47 with the default 7). */
 #define RTE_DGEMM_AUTO 0
 #define RTE_DGEMM_SIMT 1
 #define RTE_DGEMM_SPLIT 2

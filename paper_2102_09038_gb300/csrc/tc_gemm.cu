@@ -237,18 +237,18 @@ int tc_gemm_error(cudaStream_t s) {
 // of two 2^e so that its entries lie in (-1, 1), then cut into S balanced
 // base-128 digits d_s (|d_0| <= 128, |d_s| <= 64 for s > 0): A = 2^e sum_s
 // d_s 2^{-7(s+1)} up to a remainder below 2^{-7S-1}.  Slice s is stored
-// scaled, d_s 2^{-7s} (exact in BF16), so that the slice-pair products carry
-// their relative weights themselves:
-//   A Bt^T = 2^(ea + eb - 14) (P0 + P1 + P2 + P3),
-//   P0 = A_0 B_0,  P1 = A_0 B_1 + A_1 B_0,  P2 = A_0 B_2 + A_1 B_1 + A_2 B_0,
-//   P3 = sum_{3 <= s + t <= S-1} A_s B_t
-// (pairs with s + t >= S lie below the truncation level).  Over at most 512
-// terms of K, P0 is an integer below 2^23, P1 an integer multiple of 2^-7
-// below 2^16 and P2 one of 2^-14 below 2^10 (each term of P2 at most
-// 20480 2^-14), so the tensor cores' FP32 accumulation of each is exact;
-// they are folded into FP64 registers once per 512 of K.  P3 is 2^-21 of the
-// result or less and accumulates in FP32 over the whole K: its rounding
-// stays near 2^-45 of the result.
+// scaled, d_s 2^{-7s} (exact in BF16), so that a slice-pair product carries
+// its weight 2^{-7(s+t)} itself and
+//   A Bt^T = 2^(ea + eb - 14) sum_w P_w,   P_w = sum_{s + t = w} A_s B_t
+// over w <= S - 1 (pairs with s + t >= S lie below the truncation level).
+// The tensor cores add each 16-term product group to an FP32 accumulator
+// with a truncating rounding, whose bias grows with the number of additions:
+// so each weight w <= 4 has its own accumulator, in which every partial sum
+// over at most 512 terms of K is an exact multiple of 2^{-7w} below 2^{24-7w}
+// (each term of P_w at most 28672 2^{-7w}); these are folded into FP64
+// registers once per 512 of K.  The weights w >= 5 (S >= 6) share one FP32
+// accumulator over the whole K: at most 2^{-35} of the result, so its
+// rounding stays near 2^{-58}.
 // ======================================================================
 namespace rte {
 
@@ -256,10 +256,12 @@ namespace {
 
 using namespace tc;
 
-constexpr int kOzBM = 128, kOzBN = 128, kOzKChunk = 8;    // 8 x 64 = 512 of K per fold
+constexpr int kOzBM = 128, kOzBN = 64, kOzKChunk = 8;     // 8 x 64 = 512 of K per fold
 constexpr int kOzMaxS = 9;
-constexpr uint32_t kOzTile = kOzBM * kRowBytes;            // 16 KB: one slice tile
-constexpr uint32_t kOzTmemCols = 512;                       // P0 .. P3: 4 x 128 columns
+constexpr int kOzAcc = 6;                                   // P_0 .. P_4 exact, P_5+ FP32
+constexpr uint32_t kOzATile = kOzBM * kRowBytes;            // 16 KB: one A slice tile
+constexpr uint32_t kOzBTile = kOzBN * kRowBytes;            // 8 KB: one B slice tile
+constexpr uint32_t kOzTmemCols = 512;                       // 6 x 64 columns used
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -267,14 +269,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // 18 warps: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..17 drain
 // the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the
-// quarter (w - 2) / 4 of the 128 columns of each accumulator).
+// quarter (w - 2) / 4 of the 64 columns of each accumulator).
 constexpr int kOzThreads = 576;
 constexpr int kOzEpiWarps = 16;
 
 // Per 64-wide K block the producer loads the S slices of the B tile into one
 // of nB resident sets, then streams the S slices of the A tile through a
 // ring of nA slots; the MMA issuer multiplies A slice s with B slices
-// t = 0 .. S-1-s into P0 .. P3.  Each tile of A and B is read once per
+// t = 0 .. S-1-s into P_{min(s+t, 5)}.  Each tile of A and B is read once per
 // K block (the pair products reuse them from shared memory).
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -285,9 +287,9 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sB = smem;                                  // nB sets of S tiles
-    uint8_t* sA = smem + (size_t)nB * S * kOzTile;       // nA tiles
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + (size_t)nA * kOzTile);
+    uint8_t* sA = smem;                                  // nA tiles of 16 KB
+    uint8_t* sB = smem + (size_t)nA * kOzATile;          // nB sets of S tiles of 8 KB
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)nB * S * kOzBTile);
     // fullA[4], emptyA[4], fullB[2], emptyB[2], accf, acce
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -329,16 +331,16 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
             const int sb = kb % nB;
             const uint32_t phb = (kb / nB) & 1;
             if (!mbar_wait(emptyB0 + 8 * sb, phb ^ 1)) { ok = false; break; }
-            mbar_expect_tx(fullB0 + 8 * sb, (uint32_t)S * kOzTile);
+            mbar_expect_tx(fullB0 + 8 * sb, (uint32_t)S * kOzBTile);
             for (int t = 0; t < S; ++t)
-                tma_load_2d(smem_u32(sB + ((size_t)sb * S + t) * kOzTile), &mapB, fullB0 + 8 * sb,
-                            kb * 64, t * N + n0);
+                tma_load_2d(smem_u32(sB + ((size_t)sb * S + t) * kOzBTile), &mapB,
+                            fullB0 + 8 * sb, kb * 64, t * N + n0);
             for (int s = 0; s < S && ok; ++s, ++ga) {
                 const int sa = ga % nA;
                 const uint32_t pha = (ga / nA) & 1;
                 if (!mbar_wait(emptyA0 + 8 * sa, pha ^ 1)) { ok = false; break; }
-                mbar_expect_tx(fullA0 + 8 * sa, kOzTile);
-                tma_load_2d(smem_u32(sA + (size_t)sa * kOzTile), &mapA, fullA0 + 8 * sa, kb * 64,
+                mbar_expect_tx(fullA0 + 8 * sa, kOzATile);
+                tma_load_2d(smem_u32(sA + (size_t)sa * kOzATile), &mapA, fullA0 + 8 * sa, kb * 64,
                             s * M + m0);
             }
         }
@@ -352,27 +354,27 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
             const int chunk = kb / kOzKChunk;
             if (kb % kOzKChunk == 0) {
                 if (chunk > 0) {
-                    // P0, P1, P2 of the previous chunk drained by the epilogue
+                    // the exact accumulators of the previous chunk drained
                     if (!mbar_wait(acce, (chunk - 1) & 1)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
-                started &= 8u;
+                started &= 1u << (kOzAcc - 1);
             }
             const int sb = kb % nB;
             const uint32_t phb = (kb / nB) & 1;
             if (!mbar_wait(fullB0 + 8 * sb, phb)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t b0 = smem_u32(sB + (size_t)sb * S * kOzTile);
+            const uint32_t b0 = smem_u32(sB + (size_t)sb * S * kOzBTile);
             for (int s = 0; s < S && ok; ++s, ++ga) {
                 const int sa = ga % nA;
                 const uint32_t pha = (ga / nA) & 1;
                 if (!mbar_wait(fullA0 + 8 * sa, pha)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(sA + (size_t)sa * kOzTile);
+                const uint32_t a0 = smem_u32(sA + (size_t)sa * kOzATile);
                 for (int t = 0; s + t <= S - 1; ++t) {
-                    const int acc = s + t < 3 ? s + t : 3;
+                    const int acc = s + t < kOzAcc - 1 ? s + t : kOzAcc - 1;
                     const uint32_t dtm = tmem + (uint32_t)(acc * kOzBN);
-                    const uint32_t bt = b0 + (uint32_t)t * kOzTile;
+                    const uint32_t bt = b0 + (uint32_t)t * kOzBTile;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
                         mma_issue(false, dtm, sw128_desc(a0 + 32 * kk), sw128_desc(bt + 32 * kk),
@@ -397,25 +399,23 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
     }
     // ------------------------------------------------------------ epilogue
     const int wq = warp & 3, quarter = (warp - 2) >> 2;
-    const uint32_t lanebase = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(quarter * 32);
-    double acc64[32];
+    const uint32_t lanebase = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(quarter * 16);
+    double acc64[16];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc64[i] = 0.0;
+    for (int i = 0; i < 16; ++i) acc64[i] = 0.0;
+    // exact accumulators P_0 .. P_{min(S,5)-1} after every chunk; P_5+ (S >= 6)
+    // once, after the last (an accumulator no MMA wrote is not read)
+    const int nexact = S < kOzAcc - 1 ? S : kOzAcc - 1;
     for (int c = 0; c < nchunks; ++c) {
         if (ok) ok = mbar_wait(accf, c & 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool last = c == nchunks - 1;
-        // P_a exists for S > a (an accumulator no MMA wrote is not read); P3
-        // is read once, after the last chunk
-        const int nacc = last ? (S < 4 ? S : 4) : (S < 3 ? S : 3);
+        const int nacc = (c == nchunks - 1 && S >= kOzAcc) ? kOzAcc : nexact;
+        for (int a = 0; a < nacc; ++a) {
+            float v[16];
+            tmem_ld16(lanebase + (uint32_t)(a * kOzBN), v);
 #pragma unroll
-        for (int c0 = 0; c0 < 32; c0 += 16)
-            for (int a = 0; a < nacc; ++a) {
-                float v[16];
-                tmem_ld16(lanebase + (uint32_t)(a * kOzBN + c0), v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) acc64[c0 + i] += (double)v[i];
-            }
+            for (int i = 0; i < 16; ++i) acc64[i] += (double)v[i];
+        }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) mbar_arrive(acce);
@@ -430,8 +430,8 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         }
         double* dst = C + (size_t)row * ldc;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int col = n0 + quarter * 32 + i;
+        for (int i = 0; i < 16; ++i) {
+            const int col = n0 + quarter * 16 + i;
             if (col < N) {
                 double x = ldexp(acc64[i], er + eb[col] - 14);
                 if (epi == 1) x = x / (fat - lam[col] * fas);
@@ -520,17 +520,17 @@ int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const 
     // resident B slice sets and A ring slots within the shared-memory limit:
     // two B sets when they fit beside at least two A slots, else one
     constexpr size_t kLimit = 227 * 1024 - 1024 - 16 * 8 - 64;
+    auto bytes = [S](int nb, int na) { return (size_t)nb * S * kOzBTile + (size_t)na * kOzATile; };
     int nB = 2, nA = 4;
-    while (nA > 2 && (size_t)(nB * S + nA) * kOzTile > kLimit) --nA;
-    if ((size_t)(nB * S + nA) * kOzTile > kLimit) {
+    while (nA > 2 && bytes(nB, nA) > kLimit) --nA;
+    if (bytes(nB, nA) > kLimit) {
         nB = 1;
         nA = 4;
-        while (nA > 2 && (size_t)(nB * S + nA) * kOzTile > kLimit) --nA;
+        while (nA > 2 && bytes(nB, nA) > kLimit) --nA;
     }
     // at least half of the SM's shared memory, so that one block (and its 512
     // tensor-memory columns) runs per SM
-    const size_t sm = std::max<size_t>(1024 + (size_t)(nB * S + nA) * kOzTile + 16 * 8 + 16,
-                                       116 * 1024);
+    const size_t sm = std::max<size_t>(1024 + bytes(nB, nA) + 16 * 8 + 16, 116 * 1024);
     static const bool attr = [] {
         cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(227 * 1024));
