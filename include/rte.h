@@ -52,8 +52,8 @@ extern "C" {
  * are computed: RTE_DGEMM_AUTO picks SIMT in RTE_FP64 mode and SPLIT in the
  * mixed modes; RTE_DGEMM_SIMT uses FP64 arithmetic units; RTE_DGEMM_SPLIT
  * cuts the FP64 operands into exact BF16 digit slices whose tensor-core
- * products are summed in FP64 (about S 2^-7S relative to the operand scales
- * for S slices: 2^-47 with the default 7). */
+ * products are summed in FP64 (about 2^-49 relative to the operand scales
+ * with the default 7 slices). */
 #define RTE_DGEMM_AUTO 0
 #define RTE_DGEMM_SIMT 1
 #define RTE_DGEMM_SPLIT 2

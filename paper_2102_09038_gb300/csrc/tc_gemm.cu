@@ -18,7 +18,6 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
-#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -234,21 +233,22 @@ int tc_gemm_error(cudaStream_t s) {
 // splitting of the operands, after Ozaki, Ogita, Oishi and Rump).
 //
 // Every row of A (and of the K-major second operand Bt) is scaled by a power
-// of two 2^e so that its entries lie in (-1, 1), then cut into S balanced
-// base-128 digits d_s (|d_0| <= 128, |d_s| <= 64 for s > 0): A = 2^e sum_s
-// d_s 2^{-7(s+1)} up to a remainder below 2^{-7S-1}.  Slice s is stored
-// scaled, d_s 2^{-7s} (exact in BF16), so that a slice-pair product carries
-// its weight 2^{-7(s+t)} itself and
-//   A Bt^T = 2^(ea + eb - 14) sum_w P_w,   P_w = sum_{s + t = w} A_s B_t
-// over w <= S - 1 (pairs with s + t >= S lie below the truncation level).
-// The tensor cores add each 16-term product group to an FP32 accumulator
-// with a truncating rounding, whose bias grows with the number of additions:
-// so each weight w <= 4 has its own accumulator, in which every partial sum
-// over at most 512 terms of K is an exact multiple of 2^{-7w} below 2^{24-7w}
-// (each term of P_w at most 28672 2^{-7w}); these are folded into FP64
-// registers once per 512 of K.  The weights w >= 5 (S >= 6) share one FP32
-// accumulator over the whole K: at most 2^{-35} of the result, so its
-// rounding stays near 2^{-58}.
+// of two 2^e so that its entries lie in (-1, 1), then cut into S digit
+// slices: r <- r * 2^7, d = rint(r), r <- r - d.  The digits are integers
+// with |d| <= 128, exact in BF16, and A = 2^e sum_s d_s 2^{-7(s+1)} up to a
+// remainder below 2^{-7S-1}.  A product of two digit slices summed over at
+// most 1024 terms is an integer below 2^24, so the tensor cores' FP32
+// accumulation of it is exact.  The kernel accumulates the slice pairs
+// (s, t) with s + t <= S - 1 (the others lie below the truncation level)
+// in groups of one weight 2^{-7(s+t+2)} each: a group shares a tensor-memory
+// buffer over 512 terms of K, and holds pairs whose digit bounds add up to
+// at most 2^15 per term (|d_0 d_0| <= 2^14, |d_0 d_t| <= 2^13, |d_s d_t| <=
+// 2^12 for s, t > 0), so its sum stays an integer of magnitude at most
+// 2^15 * 512 = 2^24 and the FP32 accumulation is exact (the tensor cores
+// truncate when they add, so only exact sums are safe).  A weight with more
+// pairs than that takes two groups.  Each buffer is folded into the
+// double-float registers with its weight; the row and column scales come
+// last.
 // ======================================================================
 namespace rte {
 
@@ -256,12 +256,17 @@ namespace {
 
 using namespace tc;
 
-constexpr int kOzBM = 128, kOzBN = 64, kOzKChunk = 8;     // 8 x 64 = 512 of K per fold
-constexpr int kOzMaxS = 9;
-constexpr int kOzAcc = 6;                                   // P_0 .. P_4 exact, P_5+ FP32
-constexpr uint32_t kOzATile = kOzBM * kRowBytes;            // 16 KB: one A slice tile
-constexpr uint32_t kOzBTile = kOzBN * kRowBytes;            // 8 KB: one B slice tile
-constexpr uint32_t kOzTmemCols = 512;                       // 6 x 64 columns used
+constexpr int kOzBM = 128, kOzBN = 128, kOzStages = 6, kOzKChunk = 8;    // 8 x 64 = 512
+constexpr int kOzMaxPairs = 64;
+
+// slice pairs ordered by weight w = s + t; pairs of weight w at
+// first[w] .. first[w + 1] - 1
+struct OzPairs {
+    int n, groups;
+    unsigned char s[kOzMaxPairs], t[kOzMaxPairs];
+    unsigned char first[20];   // group g: pairs first[g] .. first[g + 1] - 1
+    unsigned char wgt[20];     // and its weight w = s + t
+};
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -269,53 +274,59 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 
 // 18 warps: warp 0 issues TMA loads, warp 1 issues MMAs, warps 2..17 drain
 // the accumulators (warp w reads TMEM lanes 32 (w % 4) .. + 31 and the
-// quarter (w - 2) / 4 of the 64 columns of each accumulator).
+// quarter (w - 2) / 4 of the 128 columns), so the producer and the MMA
+// issuer never wait on the epilogue's own arrivals.
 constexpr int kOzThreads = 576;
 constexpr int kOzEpiWarps = 16;
 
-// Per 64-wide K block the producer loads the S slices of the B tile into one
-// of nB resident sets, then streams the S slices of the A tile through a
-// ring of nA slots; the MMA issuer multiplies A slice s with B slices
-// t = 0 .. S-1-s into P_{min(s+t, 5)}.  Each tile of A and B is read once per
-// K block (the pair products reuse them from shared memory).
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-        int M, int N, int K, int S, int nA, int nB, const int* __restrict__ ea,
+        int M, int N, int K, const OzPairs pairs, const int* __restrict__ ea,
         const int* __restrict__ eb, double* __restrict__ C, int ldc, int epi,
         const double* __restrict__ at, const double* __restrict__ as,
         const double* __restrict__ lam, int rows) {
+    constexpr uint32_t kABytes = kOzBM * kRowBytes, kBBytes = kOzBN * kRowBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t* sA = smem;                                  // nA tiles of 16 KB
-    uint8_t* sB = smem + (size_t)nA * kOzATile;          // nB sets of S tiles of 8 KB
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)nB * S * kOzBTile);
-    // fullA[4], emptyA[4], fullB[2], emptyB[2], accf, acce
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + kOzStages * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kOzStages * kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kOzStages + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kOzBM, n0 = blockIdx.x * kOzBN;
     const int kblocks = (K + 63) / 64;
     const int nchunks = (kblocks + kOzKChunk - 1) / kOzKChunk;
-    const uint32_t fullA0 = smem_u32(bars), emptyA0 = smem_u32(bars + 4),
-                   fullB0 = smem_u32(bars + 8), emptyB0 = smem_u32(bars + 10),
-                   accf = smem_u32(bars + 12), acce = smem_u32(bars + 13);
+    const int jobs = pairs.groups * nchunks;   // (weight group, chunk of K)
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kOzStages),
+                   accf0 = smem_u32(bars + 2 * kOzStages), acce0 = smem_u32(bars + 2 * kOzStages + 2);
+    // slice-pair table in shared memory (a dynamically indexed kernel
+    // parameter would live in local memory)
+    __shared__ int s_ya[kOzMaxPairs], s_yb[kOzMaxPairs];
+    __shared__ int s_first[20], s_wgt[20];
+    for (int p = threadIdx.x; p < pairs.n; p += blockDim.x) {
+        s_ya[p] = pairs.s[p] * M + m0;
+        s_yb[p] = pairs.t[p] * N + n0;
+    }
+    for (int g = threadIdx.x; g <= pairs.groups; g += blockDim.x) {
+        s_first[g] = pairs.first[g];
+        s_wgt[g] = pairs.wgt[g];
+    }
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) {
-            mbar_init(fullA0 + 8 * i, 1);
-            mbar_init(emptyA0 + 8 * i, 1);
+        for (int s = 0; s < kOzStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
         }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(fullB0 + 8 * i, 1);
-            mbar_init(emptyB0 + 8 * i, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, kOzEpiWarps);   // one arrival per epilogue warp
         }
-        mbar_init(accf, 1);
-        mbar_init(acce, kOzEpiWarps);   // one arrival per epilogue warp
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(kOzTmemCols));
+                     "r"(256));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -326,65 +337,51 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
 
     if (warp == 0 && lane == 0) {
         // --------------------------------------------- TMA producer
-        int ga = 0;
-        for (int kb = 0; kb < kblocks && ok; ++kb) {
-            const int sb = kb % nB;
-            const uint32_t phb = (kb / nB) & 1;
-            if (!mbar_wait(emptyB0 + 8 * sb, phb ^ 1)) { ok = false; break; }
-            mbar_expect_tx(fullB0 + 8 * sb, (uint32_t)S * kOzBTile);
-            for (int t = 0; t < S; ++t)
-                tma_load_2d(smem_u32(sB + ((size_t)sb * S + t) * kOzBTile), &mapB,
-                            fullB0 + 8 * sb, kb * 64, t * N + n0);
-            for (int s = 0; s < S && ok; ++s, ++ga) {
-                const int sa = ga % nA;
-                const uint32_t pha = (ga / nA) & 1;
-                if (!mbar_wait(emptyA0 + 8 * sa, pha ^ 1)) { ok = false; break; }
-                mbar_expect_tx(fullA0 + 8 * sa, kOzATile);
-                tma_load_2d(smem_u32(sA + (size_t)sa * kOzATile), &mapA, fullA0 + 8 * sa, kb * 64,
-                            s * M + m0);
-            }
+        int g = 0;
+        for (int j = 0; j < jobs && ok; ++j) {
+            const int grp = j / nchunks, ch = j % nchunks;
+            const int p0 = s_first[grp], p1 = s_first[grp + 1];
+            const int kb1 = min(kblocks, (ch + 1) * kOzKChunk);
+            for (int kb = ch * kOzKChunk; kb < kb1 && ok; ++kb)
+                for (int p = p0; p < p1; ++p, ++g) {
+                    const int st = g % kOzStages;
+                    const uint32_t ph = (g / kOzStages) & 1;
+                    if (!mbar_wait(empty0 + 8 * st, ph ^ 1)) { ok = false; break; }
+                    mbar_expect_tx(full0 + 8 * st, kABytes + kBBytes);
+                    tma_load_2d(smem_u32(sA + st * kABytes), &mapA, full0 + 8 * st, kb * 64, s_ya[p]);
+                    tma_load_2d(smem_u32(sB + st * kBBytes), &mapB, full0 + 8 * st, kb * 64, s_yb[p]);
+                }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------- MMA issuer
         const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                ((uint32_t)(kOzBN >> 3) << 17) | ((uint32_t)(kOzBM >> 4) << 24);
-        int ga = 0;
-        unsigned started = 0;   // bit a: accumulator a holds a partial sum
-        for (int kb = 0; kb < kblocks && ok; ++kb) {
-            const int chunk = kb / kOzKChunk;
-            if (kb % kOzKChunk == 0) {
-                if (chunk > 0) {
-                    // the exact accumulators of the previous chunk drained
-                    if (!mbar_wait(acce, (chunk - 1) & 1)) { ok = false; break; }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                }
-                started &= 1u << (kOzAcc - 1);
-            }
-            const int sb = kb % nB;
-            const uint32_t phb = (kb / nB) & 1;
-            if (!mbar_wait(fullB0 + 8 * sb, phb)) { ok = false; break; }
+        int g = 0;
+        for (int j = 0; j < jobs && ok; ++j) {
+            const int b = j & 1;
+            const uint32_t bph = (j >> 1) & 1;
+            if (!mbar_wait(acce0 + 8 * b, bph ^ 1)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t b0 = smem_u32(sB + (size_t)sb * S * kOzBTile);
-            for (int s = 0; s < S && ok; ++s, ++ga) {
-                const int sa = ga % nA;
-                const uint32_t pha = (ga / nA) & 1;
-                if (!mbar_wait(fullA0 + 8 * sa, pha)) { ok = false; break; }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t a0 = smem_u32(sA + (size_t)sa * kOzATile);
-                for (int t = 0; s + t <= S - 1; ++t) {
-                    const int acc = s + t < kOzAcc - 1 ? s + t : kOzAcc - 1;
-                    const uint32_t dtm = tmem + (uint32_t)(acc * kOzBN);
-                    const uint32_t bt = b0 + (uint32_t)t * kOzBTile;
+            const uint32_t dtm = tmem + (uint32_t)(b * kOzBN);
+            const int grp = j / nchunks, ch = j % nchunks;
+            const int np = s_first[grp + 1] - s_first[grp];
+            const int kb0 = ch * kOzKChunk, kb1 = min(kblocks, kb0 + kOzKChunk);
+            bool first = true;   // the job's first MMA overwrites the buffer
+            for (int kb = kb0; kb < kb1 && ok; ++kb)
+                for (int p = 0; p < np; ++p, ++g) {
+                    const int st = g % kOzStages;
+                    const uint32_t ph = (g / kOzStages) & 1;
+                    if (!mbar_wait(full0 + 8 * st, ph)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + st * kABytes), b0 = smem_u32(sB + st * kBBytes);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
-                        mma_issue(false, dtm, sw128_desc(a0 + 32 * kk), sw128_desc(bt + 32 * kk),
-                                  idesc, (((started >> acc) & 1u) || kk > 0) ? 1u : 0u);
-                    started |= 1u << acc;
+                        mma_issue(false, dtm, sw128_desc(a0 + 32 * kk), sw128_desc(b0 + 32 * kk),
+                                  idesc, (!first || kk > 0) ? 1u : 0u);
+                    first = false;
+                    mma_commit(empty0 + 8 * st);
                 }
-                mma_commit(emptyA0 + 8 * sa);   // frees the A slot once its MMAs have read it
-            }
-            mma_commit(emptyB0 + 8 * sb);
-            if (kb % kOzKChunk == kOzKChunk - 1 || kb == kblocks - 1) mma_commit(accf);
+            mma_commit(accf0 + 8 * b);
         }
     }
     __syncwarp();
@@ -394,31 +391,45 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         __syncthreads();
         if (warp == 0)
             asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                         "r"(kOzTmemCols));
+                         "r"(256));
         return;
     }
     // ------------------------------------------------------------ epilogue
     const int wq = warp & 3, quarter = (warp - 2) >> 2;
-    const uint32_t lanebase = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(quarter * 16);
-    double acc64[16];
+    // Double-float accumulators (hi + lo, about 48 significant bits): every
+    // job adds v 2^-7(s+t+2) with v an integer below 2^24, exact in FP32; the
+    // two-sum keeps the rounding error of each addition in lo.  FP32 runs at
+    // many times the FP64 rate of this GPU.
+    float hi[32], lo[32];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc64[i] = 0.0;
-    // exact accumulators P_0 .. P_{min(S,5)-1} after every chunk; P_5+ (S >= 6)
-    // once, after the last (an accumulator no MMA wrote is not read)
-    const int nexact = S < kOzAcc - 1 ? S : kOzAcc - 1;
-    for (int c = 0; c < nchunks; ++c) {
-        if (ok) ok = mbar_wait(accf, c & 1);
+    for (int i = 0; i < 32; ++i) {
+        hi[i] = 0.f;
+        lo[i] = 0.f;
+    }
+    for (int j = 0; j < jobs; ++j) {
+        const int b = j & 1;
+        const uint32_t bph = (j >> 1) & 1;
+        if (ok) ok = mbar_wait(accf0 + 8 * b, bph);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int nacc = (c == nchunks - 1 && S >= kOzAcc) ? kOzAcc : nexact;
-        for (int a = 0; a < nacc; ++a) {
-            float v[16];
-            tmem_ld16(lanebase + (uint32_t)(a * kOzBN), v);
+        const float w = ldexpf(1.0f, -7 * (s_wgt[j / nchunks] + 2));   // the group's weight
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc64[i] += (double)v[i];
+        for (int c0 = 0; c0 < 32; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(b * kOzBN + quarter * 32 + c0), v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const float x = v[i] * w;                 // exact
+                const float sum = __fadd_rn(hi[c0 + i], x);
+                const float bb = __fsub_rn(sum, hi[c0 + i]);
+                const float err = __fadd_rn(__fsub_rn(hi[c0 + i], __fsub_rn(sum, bb)),
+                                            __fsub_rn(x, bb));
+                hi[c0 + i] = sum;
+                lo[c0 + i] = __fadd_rn(lo[c0 + i], err);
+            }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(acce);
+        if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
     const int row = m0 + wq * 32 + lane;
     if (ok && row < M) {
@@ -430,10 +441,10 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         }
         double* dst = C + (size_t)row * ldc;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int col = n0 + quarter * 16 + i;
+        for (int i = 0; i < 32; ++i) {
+            const int col = n0 + quarter * 32 + i;
             if (col < N) {
-                double x = ldexp(acc64[i], er + eb[col] - 14);
+                double x = ldexp((double)hi[i] + (double)lo[i], er + eb[col]);
                 if (epi == 1) x = x / (fat - lam[col] * fas);
                 dst[col] = x;
             }
@@ -483,8 +494,7 @@ __global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int S,
         for (int s = S - 1; s >= 1; --s) {
             const long long d = ((v + 64) & 127) - 64;
             v = (v - d) >> 7;
-            // slice s stored as d 2^{-7s} (exact: a power-of-two scaling)
-            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn(ldexpf((float)d, -7 * s));
+            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn((float)d);
         }
         out[(size_t)row * K + k] = __float2bfloat16_rn((float)v);
     }
@@ -511,35 +521,40 @@ int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const 
                const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
                const double* as, const double* lam, int rows, int SB) {
     if (M <= 0 || N <= 0 || K <= 0) return RTE_OK;
-    if (S < 1 || S > kOzMaxS) return fail(RTE_ERR_ARG, "bad slice count");
+    if (S < 1 || S > 9 || S * (S + 1) / 2 > kOzMaxPairs) return fail(RTE_ERR_ARG, "bad slice count");
     if (SB == 0) SB = S;
     if (SB < S) return fail(RTE_ERR_ARG, "second operand has fewer slices than used");
+    // pairs by weight, cut into groups whose per-term digit bounds add up to
+    // at most 2^15 (see the comment above k_ozaki)
+    OzPairs pairs{};
+    for (int w = 0; w < S; ++w) {
+        int cost = 1 << 16;   // forces a new group
+        for (int a = 0; a <= w; ++a) {
+            const int b = w - a;
+            const int c = (a == 0 && b == 0) ? 1 << 14 : (a == 0 || b == 0) ? 1 << 13 : 1 << 12;
+            if (cost + c > (1 << 15)) {
+                pairs.first[pairs.groups] = (unsigned char)pairs.n;
+                pairs.wgt[pairs.groups] = (unsigned char)w;
+                ++pairs.groups;
+                cost = 0;
+            }
+            cost += c;
+            pairs.s[pairs.n] = (unsigned char)a;
+            pairs.t[pairs.n] = (unsigned char)b;
+            ++pairs.n;
+        }
+    }
+    pairs.first[pairs.groups] = (unsigned char)pairs.n;
     CUtensorMap ma, mb;
     RTE_TRY(make_map(&ma, Aslices, false, S * M, K, kOzBM));
     RTE_TRY(make_map(&mb, Bslices, false, SB * N, K, kOzBN));
-    // resident B slice sets and A ring slots within the shared-memory limit:
-    // two B sets when they fit beside at least two A slots, else one
-    constexpr size_t kLimit = 227 * 1024 - 1024 - 16 * 8 - 64;
-    auto bytes = [S](int nb, int na) { return (size_t)nb * S * kOzBTile + (size_t)na * kOzATile; };
-    int nB = 2, nA = 4;
-    while (nA > 2 && bytes(nB, nA) > kLimit) --nA;
-    if (bytes(nB, nA) > kLimit) {
-        nB = 1;
-        nA = 4;
-        while (nA > 2 && bytes(nB, nA) > kLimit) --nA;
-    }
-    // at least half of the SM's shared memory, so that one block (and its 512
-    // tensor-memory columns) runs per SM
-    const size_t sm = std::max<size_t>(1024 + bytes(nB, nA) + 16 * 8 + 16, 116 * 1024);
-    static const bool attr = [] {
-        cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(227 * 1024));
-        return true;
-    }();
-    (void)attr;
+    const size_t sm = 1024 + (size_t)kOzStages * (kOzBM + kOzBN) * kRowBytes +
+                      (2 * kOzStages + 4) * 8 + 16;
+    RTE_CUDA_TRY(cudaFuncSetAttribute(k_ozaki, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm));
     dim3 grid((N + kOzBN - 1) / kOzBN, (M + kOzBM - 1) / kOzBM);
     count_launches(1);
-    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, S, nA, nB, ea, eb, C, ldc, epi, at, as,
+    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, pairs, ea, eb, C, ldc, epi, at, as,
                                          lam, rows);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
