@@ -670,7 +670,7 @@ def serving_sweep(args, torch, rte, seq_rate):
     reqs = serving_requests(args.serve_requests, seed=3)
     free, _ = torch.cuda.mem_get_info()
     out = []
-    for mult in (0.5, 1.0, 2.0, 4.0, 8.0):
+    for mult in (1.0, 2.0, 4.0, 8.0):
         lat, _, wall, hits, misses = run_stream(rte, reqs, mult * seq_rate, int(free * 0.6), 8,
                                                 dict(precision=rte.MIXED_BF16), 4)
         out.append(dict(rate_per_s=mult * seq_rate, rate_over_sequential_fp64=mult,
