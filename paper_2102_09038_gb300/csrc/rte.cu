@@ -1153,61 +1153,6 @@ int mk_inv_pcg(rte_handle* h, const double* B, double* X, int nrhs) {
     return RTE_OK;
 }
 
-// The same loop with the host reading ||r||^2 every iteration (the form
-// before the graph loop; kept for comparison).
-[[maybe_unused]] int mk_inv_pcg_host(rte_handle* h, const double* B, double* X, int nrhs) {
-    const DevSystem& d = h->d;
-    if (!h->z5) return fail(RTE_ERR_ARG, "PCG route needs mk_route = RTE_MK_PCG at setup");
-    const size_t len = (size_t)d.nRm * d.nSm;
-    double *R = h->z3, *P = h->z4, *AP = h->z5, *Zb = h->z6, *G = h->z7, *tmp = h->zsk;
-    const int n = nrhs;
-    // sc: [0,n) rz, [n,2n) scratch, [2n,3n) alpha, [3n,4n) rr, [4n,5n) bb, [5n,6n) beta
-    double* sc = h->sc;
-    cudaStream_t s = h->stream;
-    RTE_CUDA_TRY(cudaMemcpyAsync(R, B, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
-    RTE_CUDA_TRY(cudaMemsetAsync(X, 0, sizeof(double) * n * len, s));
-    dot_per_rhs(s, B, B, len, n, h->partial, sc + 4 * n);
-    RTE_TRY(mk_prec(h, R, Zb, tmp, n));
-    RTE_CUDA_TRY(cudaMemcpyAsync(P, Zb, sizeof(double) * n * len, cudaMemcpyDeviceToDevice, s));
-    dot_per_rhs(s, R, Zb, len, n, h->partial, sc);
-    std::vector<double> hb(n), hr(n);
-    RTE_CUDA_TRY(cudaMemcpyAsync(hb.data(), sc + 4 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    RTE_CUDA_TRY(cudaStreamSynchronize(s));
-    bool allzero = true;
-    for (double v : hb) allzero = allzero && v == 0.0;
-    int it = 0;
-    if (!allzero) {
-        for (it = 1; it <= h->opt.mk_maxit; ++it) {
-            RTE_TRY(mk_apply(h, P, AP, G, n));
-            dot_per_rhs(s, P, AP, len, n, h->partial, sc + n);
-            k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc, sc + n, sc + 2 * n, n, 1.0);
-            axpby_per_rhs(s, P, X, len, n, sc + 2 * n, 0.0, nullptr, 1.0);
-            k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc, sc + n, sc + 2 * n, n, -1.0);
-            count_launches(2);
-            axpby_per_rhs(s, AP, R, len, n, sc + 2 * n, 0.0, nullptr, 1.0);
-            dot_per_rhs(s, R, R, len, n, h->partial, sc + 3 * n);
-            RTE_CUDA_TRY(cudaMemcpyAsync(hr.data(), sc + 3 * n, sizeof(double) * n,
-                                         cudaMemcpyDeviceToHost, s));
-            RTE_CUDA_TRY(cudaStreamSynchronize(s));
-            bool done = true;
-            for (int r = 0; r < n; ++r) {
-                if (!std::isfinite(hr[r])) return fail(RTE_ERR_DIVERGED, "PCG residual is NaN");
-                done = done && hr[r] <= h->opt.mk_tol * h->opt.mk_tol * hb[r];
-            }
-            if (done) break;
-            RTE_TRY(mk_prec(h, R, Zb, tmp, n));
-            dot_per_rhs(s, R, Zb, len, n, h->partial, sc + n);       // rz_new
-            k_ratio<<<(n + 63) / 64, 64, 0, s>>>(sc + n, sc, sc + 5 * n, n, 1.0);
-            count_launches(1);
-            RTE_CUDA_TRY(cudaMemcpyAsync(sc, sc + n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-            axpby_per_rhs(s, Zb, P, len, n, nullptr, 1.0, sc + 5 * n, 0.0);   // p = z + beta p
-        }
-        if (it > h->opt.mk_maxit) it = h->opt.mk_maxit;
-    }
-    h->mk_iters = it;
-    return RTE_OK;
-}
-
 int mk_inv(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
     if (h->opt.mk_route == RTE_MK_PCG) return mk_inv_pcg(h, Z1, Z2, nrhs);
     return mk_inv_eigen(h, Z1, Z2, nrhs);

@@ -142,3 +142,36 @@ def test_mixed_applies_element_by_element(levels, prec):
         err = np.abs(got - ref).max() / np.abs(ref).max()
         assert err <= BOUND[prec], (op, err)
     s.close()
+
+
+@pytest.mark.parametrize('prec', [1, 2], ids=['fp32', 'bf16'])
+def test_mixed_restriction_and_prolongation(prec):
+    # on mixed handles the coarse restriction W^T x and prolongation W u_c
+    # run in FP32 products (a preconditioner step): every entry within the
+    # standard rounding bound (n + 1) u sum |x_k| |W_kj| of an n-term FP32
+    # dot product (u = 2^-24; the operands' FP32 rounding included)
+    import paper_2102_09038_gb300 as rte
+    p = problem(9, 2, 2)
+    disc, ops = oracle_ops(p)
+    s = rte.Solver(p, n_plus=2, n_minus=3, precision=prec, max_rhs=2)
+    d = s.d_plus
+    W = s.export('WpN').reshape(disc.nSp, d)
+    co = Coarse(ops, 2, W=W)
+    u = 2.0 ** -24
+    x = np.random.default_rng(11).standard_normal((2, disc.nRp, disc.nSp))
+    qc = torch.zeros((2, disc.nRp, d), dtype=torch.float64, device='cuda')
+    s.operator('RESTRICT', torch.tensor(x, device='cuda'), qc)
+    got = qc.cpu().numpy()
+    for r in range(2):
+        ref = co.restrict(x[r]).reshape(disc.nRp, d)
+        bound = (disc.nSp + 1) * u * (np.abs(x[r]) @ np.abs(W))
+        assert np.all(np.abs(got[r] - ref) <= bound + 1e-300)
+    uc = np.random.default_rng(12).standard_normal((2, disc.nRp, d))
+    out = torch.zeros((2, disc.nRp, disc.nSp), dtype=torch.float64, device='cuda')
+    s.operator('PROLONG', torch.tensor(uc, device='cuda'), out)
+    got = out.cpu().numpy()
+    s.close()
+    for r in range(2):
+        ref = co.prolong(uc[r]).reshape(disc.nRp, disc.nSp)
+        bound = (d + 1) * u * (np.abs(uc[r]) @ np.abs(W).T)
+        assert np.all(np.abs(got[r] - ref) <= bound + 1e-300)
