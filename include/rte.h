@@ -555,6 +555,11 @@ int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* 
 
 int rte_h2_get_info(const rte_h2* h, rte_h2_info* info);
 
+/* The host half of rte_h2_create alone: the cluster and block trees of the
+ * options (no device call; bytes and setup_ms are 0).  RTE_ERR_ARG as in
+ * rte_h2_create. */
+int rte_h2_plan_info(const rte_h2_options* opts, rte_h2_info* info);
+
 /* Dense S^+ or S^- (host, n x n row-major) assembled by the same device
  * quadrature as rte_setup's; for comparisons at moderate n (n_S^+ <= 4096). */
 int rte_h2_dense(const rte_h2* h, int parity, double* host_out, size_t n);

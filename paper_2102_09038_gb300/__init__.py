@@ -94,7 +94,7 @@ EXPORTED = ['rte_default_options', 'rte_setup', 'rte_sizes', 'rte_rhs', 'rte_inf
             'rte_trace_read', 'rte_destroy', 'rte_set_wait_limit', 'rte_barrier_selftest',
             'rte_set_stream', 'rte_server_cache_stats',
             'rte_h2_default_options', 'rte_h2_create', 'rte_h2_apply', 'rte_h2_get_info',
-            'rte_h2_dense', 'rte_h2_destroy',
+            'rte_h2_dense', 'rte_h2_destroy', 'rte_h2_plan_info',
             'rte_last_error']
 
 
@@ -161,6 +161,7 @@ def load(path=LIB_PATH):
     lib.rte_h2_create.argtypes = [ctypes.POINTER(_H2Options), P, ctypes.POINTER(P)]
     lib.rte_h2_apply.argtypes = [P, I, I, P, P, I, P]
     lib.rte_h2_get_info.argtypes = [P, ctypes.POINTER(_H2Info)]
+    lib.rte_h2_plan_info.argtypes = [ctypes.POINTER(_H2Options), ctypes.POINTER(_H2Info)]
     lib.rte_h2_dense.argtypes = [P, I, ctypes.POINTER(D), ctypes.c_size_t]
     lib.rte_h2_destroy.argtypes = [P]
     lib.rte_h2_destroy.restype = V
@@ -388,6 +389,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def h2_plan_info(levels, eta=1.4, p=4):
+    """Block counts of the H^2 compression for the sphere of 8 * 4^levels
+    triangles, from the library's host plan alone (no GPU needed)."""
+    lib = load()
+    o = _H2Options()
+    _check(lib.rte_h2_default_options(ctypes.byref(o)))
+    o.levels, o.eta, o.p = int(levels), float(eta), int(p)
+    inf = _H2Info()
+    _check(lib.rte_h2_plan_info(ctypes.byref(o), ctypes.byref(inf)))
+    return dict(n_plus=inf.n_plus, leaves=inf.leaves, clusters=inf.clusters,
+                far_blocks=tuple(inf.far_blocks), near_blocks=tuple(inf.near_blocks),
+                near_matrices=inf.near_matrices, transfers=inf.transfers)
 
 
 class H2Scattering:

@@ -1124,6 +1124,35 @@ int rte_h2_apply(rte_h2* h, int parity, int precision, const double* X, double* 
     return RTE_OK;
 }
 
+int rte_h2_plan_info(const rte_h2_options* o, rte_h2_info* info) {
+    using namespace rte;
+    if (!o || !info) return fail(RTE_ERR_ARG, "NULL argument");
+    if (o->levels < 3 || o->levels > 8)
+        return fail(RTE_ERR_ARG, "H2: levels must be in [3, 8] (leaves of 64 representatives)");
+    if (!(o->eta > 0.0 && o->eta < 1e6)) return fail(RTE_ERR_ARG, "H2: eta must be positive");
+    if (o->p < 2 || o->p > 4) return fail(RTE_ERR_ARG, "H2: p must be in [2, 4]");
+    const SphereMesh S = make_sphere(o->levels);
+    const int qf = 1 << (2 * kRFar);
+    std::vector<double> fp((size_t)S.n * qf * 3), fw((size_t)S.n * qf);
+    for (int t = 0; t < S.n; ++t) {
+        int cnt = 0;
+        quad_one(&S.verts[3 * S.tri[3 * t]], &S.verts[3 * S.tri[3 * t + 1]],
+                 &S.verts[3 * S.tri[3 * t + 2]], kRFar, &fp[(size_t)t * qf * 3],
+                 &fw[(size_t)t * qf], cnt);
+    }
+    H2Plan P;
+    if (!h2_plan(o->levels, o->eta, o->p, fp, qf, P)) return fail(RTE_ERR_ARG, "H2: degenerate cluster box");
+    std::memset(info, 0, sizeof(*info));
+    info->n_plus = P.n;
+    info->leaves = P.leaves();
+    info->clusters = P.ncl;
+    for (const auto& b : P.far) info->far_blocks[b.sign > 0 ? 0 : 1]++;
+    for (const auto& b : P.near) info->near_blocks[b.sign > 0 ? 0 : 1]++;
+    info->near_matrices = (int)P.nearm.size();
+    info->transfers = P.ncl - P.count(P.dmin);
+    return RTE_OK;
+}
+
 int rte_h2_get_info(const rte_h2* h, rte_h2_info* info) {
     using namespace rte;
     if (!h || !info) return fail(RTE_ERR_ARG, "NULL argument");
