@@ -101,6 +101,7 @@ struct DevSystem {
     const int* ex_Sp;
     const void* sl_Sm;         // S^- (the PCG route's K^- in the mixed modes)
     const int* ex_Sm;
+    const double* mk_rinv;     // [nRm][nSm] 1 / (at - lam as), eigenbasis route
     MGDevice e0mg;             // multigrid of the E_0 direction blocks
     MGDevice ecmg;             // multigrid of E_c
 };
@@ -218,10 +219,14 @@ bool ec_direct_fits(int m, int d);
 int ec_direct_factor(cudaStream_t s, void* solver, const DevSystem& d, float* out32,
                      double* out64);
 
-// E_c^{-1} B by one persistent block-Jacobi CG per RHS.
+// E_c^{-1} B by one persistent preconditioned CG per RHS (a V-cycle of the
+// multigrid, or the factor's sweeps on the direct route).  f32_products: the
+// CG's own E_c products in FP32 from the multigrid's level 0 (multigrid
+// route only; for loose tolerances, where their rounding is far below the
+// tolerance), the recurrences staying FP64.
 int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X,
               int nrhs, double tol, int maxit, void* work, size_t work_bytes,
-              SolveStatus* status_dev);
+              SolveStatus* status_dev, bool f32_products = false);
 size_t coarse_cg_work_bytes(const DevSystem& d, int nrhs);
 
 // y = E_c x

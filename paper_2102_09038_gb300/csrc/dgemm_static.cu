@@ -62,7 +62,6 @@ extern "C" int rte_dgemm_split_static(const double* A, const double* Bt, double*
     int *ea = nullptr, *eb = nullptr;
     RTE_TRY(ozaki_split(s, A, M, K, slices, base, &ea));
     RTE_TRY(ozaki_split(s, Bt, N, K, slices, base + off_b, &eb));
-    RTE_TRY(ozaki_gemm(s, base, ea, M, base + off_b, eb, N, K, slices, C, N, 0, nullptr, nullptr,
-                       nullptr, 1));
+    RTE_TRY(ozaki_gemm(s, base, ea, M, base + off_b, eb, N, K, slices, C, N, 0, nullptr, 1));
     return tc_gemm_error(s);
 }

@@ -1366,6 +1366,9 @@ struct EcArgs {
     double* R;
     double* P;
     double* AP;
+    // FP32 copy of P when the CG's own products run in FP32 on the level-0
+    // form of the multigrid (inexact coarse solves), else null
+    float* P32;
     double* acc;        // [3][3][nrhs]
     double* bb;
     GridBar* bar;
@@ -1524,6 +1527,7 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
     const int d = a.d, G = mg.G, gpw = 32 / G;
     const int lane = threadIdx.x & 31, grp = lane / G, gl = lane % G;
     float* B0 = mg.lev[0].B;
+    float* const P32 = kDirect ? nullptr : a.P32;   // FP32 products: multigrid route only
     auto sl = [&](int s, int q) { return a.acc + ((size_t)s * 3 + q) * a.nrhs; };
     RhsSum sum;
     GROUP_LOOP(a.nRp)
@@ -1552,6 +1556,7 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
         if (ok && gl < d) {
             const double zv = ldg2(z + base + gl);
             a.P[base + gl] = zv;
+            if (P32) P32[base + gl] = (float)zv;
             sum.add(ldg2(a.R + base + gl) * zv, r, sl(2, 1));
         }
     }}
@@ -1567,7 +1572,15 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
                 a.acc[(size_t)next * 3 * a.nrhs + c] = 0.0;
         GROUP_LOOP(a.nRp)
             const bool act = ok && gl < d && ldg2(sl(prev, 2) + r) > a.tol2 * ldg2(a.bb + r);
-            if (act) {
+            if (P32) {
+                // every lane of the warp takes part (the Kronecker form shuffles)
+                const float yf = mg.Q ? ec_apply_kron(mg.lev[0], sG, mg.Q, P32, r, i, d, G, gl, act)
+                                      : ec_apply(mg.lev[0], P32, r, i, d, gl, act);
+                if (act) {
+                    a.AP[base + gl] = (double)yf;
+                    sum.add((double)yf * ldg2(a.P + base + gl), r, sl(cur, 0));
+                }
+            } else if (act) {
                 double y = 0.0;
                 const double* Pr = a.P + (size_t)r * a.nRp * d;
 #pragma unroll
@@ -1618,7 +1631,9 @@ __global__ void __launch_bounds__(256, 4) k_ec_pcg(EcArgs a) {
                 } else if (gl < d && ldg2(sl(cur, 2) + r) > a.tol2 * ldg2(a.bb + r)) {
                     const double rzo = ldg2(sl(prev, 1) + r);
                     const double beta = rzo != 0.0 ? ldg2(sl(cur, 1) + r) / rzo : 0.0;
-                    a.P[base + gl] = (double)ldg2(z + base + gl) + beta * ldg2(a.P + base + gl);
+                    const double pv = (double)ldg2(z + base + gl) + beta * ldg2(a.P + base + gl);
+                    a.P[base + gl] = pv;
+                    if (P32) P32[base + gl] = (float)pv;
                 }
             }
         }}
@@ -1777,12 +1792,14 @@ int e0_cg_lo(cudaStream_t s, const DevSystem& d, const double* B, double* X, int
 
 size_t coarse_cg_work_bytes(const DevSystem& d, int nrhs) {
     const size_t n = (size_t)nrhs * d.nRp * d.dP;
-    return 3 * (((n * 8) + 255) / 256 * 256) + ((9 * (size_t)nrhs * 8 + 255) / 256 * 256) +
-           (((size_t)nrhs * 8 + 255) / 256 * 256) + 256;
+    return 3 * (((n * 8) + 255) / 256 * 256) + (((n * 4) + 255) / 256 * 256) +
+           ((9 * (size_t)nrhs * 8 + 255) / 256 * 256) + (((size_t)nrhs * 8 + 255) / 256 * 256) +
+           256;
 }
 
 int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, int nrhs,
-              double tol, int maxit, void* work, size_t work_bytes, SolveStatus* status_dev) {
+              double tol, int maxit, void* work, size_t work_bytes, SolveStatus* status_dev,
+              bool f32_products) {
     if (d.dP < 1 || d.dP > 32) return fail(RTE_ERR_ARG, "coarse CG supports 1 <= d^+ <= 32");
     if (work_bytes < coarse_cg_work_bytes(d, nrhs))
         return fail(RTE_ERR_ARG, "coarse CG workspace too small");
@@ -1793,6 +1810,7 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     a.R = carve<double>(p, n);
     a.P = carve<double>(p, n);
     a.AP = carve<double>(p, n);
+    a.P32 = carve<float>(p, n);
     a.acc = carve<double>(p, 9 * (size_t)nrhs);
     a.bb = carve<double>(p, nrhs);
     a.bar = carve<GridBar>(p, 1);
@@ -1822,6 +1840,9 @@ int coarse_cg(cudaStream_t s, const DevSystem& d, const double* B, double* X, in
     if (a.mg.Q > kEcMaxQ || (a.mg.Q > 0 && d.dP > 16))
         return fail(RTE_ERR_ARG, "Kronecker coarse multigrid: at most 16 terms of d <= 16");
     const bool direct = a.lu32 != nullptr || a.lu64 != nullptr;
+    // FP32 products need the multigrid's level 0 (the same E_c, checked at
+    // set-up to 1e-10 in its Kronecker form)
+    if (!f32_products || direct || d.ecmg.L < 1 || d.ecmg.lev[0].n != d.nRp) a.P32 = nullptr;
     const void* fn = direct ? (const void*)k_ec_pcg<true> : (const void*)k_ec_pcg<false>;
     // level-0 work: (rhs, node) items, one per lane group (16 per block)
     const int grid = coop_grid(fn, 256, (size_t)nrhs * d.nRp, 8 * (32 / a.mg.G));

@@ -935,8 +935,7 @@ int mk_inv_eigen(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
         {
             Scope sc(h, "dgemm_split_mk1");
             RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_VmT, d.ex_VmT, d.nSm, d.nSm,
-                               S, h->z4, d.nSm, 1, d.cell_at, d.cell_as, d.lamM, d.nRm,
-                               d.split_S));
+                               S, h->z4, d.nSm, 1, d.mk_rinv, d.nRm, d.split_S));
         }
         {
             Scope sc(h, "split_digits");
@@ -944,7 +943,7 @@ int mk_inv_eigen(rte_handle* h, const double* Z1, double* Z2, int nrhs) {
         }
         Scope sc(h, "dgemm_split_mk2");
         RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, rows, d.sl_Vm, d.ex_Vm, d.nSm, d.nSm, S,
-                           Z2, d.nSm, 0, nullptr, nullptr, nullptr, 1, d.split_S));
+                           Z2, d.nSm, 0, nullptr, 1, d.split_S));
         return RTE_OK;
     }
     {
@@ -999,7 +998,7 @@ int mk_apply_split(rte_handle* h, const double* Z, double* Y, double* G, int nrh
     const int S = split_slices_now(h);
     RTE_TRY(ozaki_split(h->stream, Z, nrhs * d.nRm, d.nSm, S, h->slices, &ea));
     RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRm, d.sl_Sm, d.ex_Sm, d.nSm, d.nSm, S,
-                       G, d.nSm, 0, nullptr, nullptr, nullptr, 1, d.split_S));
+                       G, d.nSm, 0, nullptr, 1, d.split_S));
     mk_combine(h->stream, d, Z, G, Y, nrhs);
     return RTE_OK;
 }
@@ -1175,7 +1174,7 @@ int apply_E(rte_handle* h, const double* x, double* y, int nrhs, bool with_k) {
             const int S = split_slices_now(h);
             RTE_TRY(ozaki_split(h->stream, x, nrhs * d.nRp, d.nSp, S, h->slices, &ea));
             RTE_TRY(ozaki_gemm(h->stream, h->slices, ea, nrhs * d.nRp, d.sl_Sp, d.ex_Sp, d.nSp,
-                               d.nSp, S, V, d.nSp, 0, nullptr, nullptr, nullptr, 1, d.split_S));
+                               d.nSp, S, V, d.nSp, 0, nullptr, 1, d.split_S));
         } else {
             Scope sc(h, "gemm_kplus");
             gemm_f64(h->stream, nrhs * d.nRp, d.nSp, d.nSp, x, d.nSp, d.Sp, d.nSp, V, d.nSp, 1.0,
@@ -1281,11 +1280,18 @@ int e0_inv(rte_handle* h, const double* b, double* x, int nrhs) {
     return RTE_OK;
 }
 
+// coarse tolerances from which the mixed modes run the coarse CG's own
+// products in FP32
+constexpr double kCoarseF32Tol = 1e-2;
+
 int coarse_inv(rte_handle* h, const double* b, double* x, int nrhs) {
     {
         Scope sc(h, "coarse_cg");
+        // mixed modes at a loose tolerance (the default 0.3): the CG's E_c
+        // products in FP32, whose rounding lies orders below the tolerance
+        const bool f32 = h->mixed && h->opt.coarse_tol >= kCoarseF32Tol;
         RTE_TRY(coarse_cg(h->stream, h->d, b, x, nrhs, h->opt.coarse_tol, h->opt.coarse_maxit,
-                          h->cowork, h->cobytes, h->status));
+                          h->cowork, h->cobytes, h->status, f32));
     }
     SolveStatus st;
     RTE_TRY(read_status(h, st));
@@ -1922,6 +1928,16 @@ int rte_setup(const rte_problem* prob, const rte_options* opts, void* stream,
                 *sr.sl = p;
                 *sr.ex = ex;
             }
+            if (o.mk_route != RTE_MK_PCG) {
+                // the eigenbasis route's diagonal 1 / (at - lam as), per cell
+                // and eigenvalue, for the first contraction's epilogue
+                double* t = nullptr;
+                rc = dalloc(h, &t, (size_t)d.nRm * nm);
+                if (rc) return bail(rc);
+                rc = ozaki_recip_table(h->stream, d.cell_at, d.cell_as, d.lamM, d.nRm, nm, t);
+                if (rc) return bail(rc);
+                d.mk_rinv = t;
+            }
         }
     }
 #undef UP
@@ -2359,8 +2375,7 @@ int rte_dgemm_split(const double* A, const double* Bt, double* C, int M, int N, 
     int *ea = nullptr, *eb = nullptr;
     int rc = ozaki_split(s, A, M, K, slices, pa, &ea);
     if (!rc) rc = ozaki_split(s, Bt, N, K, slices, pb, &eb);
-    if (!rc) rc = ozaki_gemm(s, pa, ea, M, pb, eb, N, K, slices, C, N, 0, nullptr, nullptr,
-                             nullptr, 1);
+    if (!rc) rc = ozaki_gemm(s, pa, ea, M, pb, eb, N, K, slices, C, N, 0, nullptr, 1);
     cudaFreeAsync(pa, s);
     cudaFreeAsync(pb, s);
     if (rc) return rc;

@@ -238,6 +238,10 @@ size_t rte_estimate_bytes(const rte_problem* p, const rte_options* o, int nrhs) 
                               (o->p1_route == RTE_P1_AUTO && o->precision != RTE_FP64));
     if (p1_pcg) b += r * nRp * nSp * 8 * 2;    // the P_1 PCG's r and p
     b += nSm * nSm * 8 * 5 + nSp * nSp * 8 * 3;   // dense angular factors, slices
+    const bool split = o && (o->dgemm == RTE_DGEMM_SPLIT ||
+                             (o->dgemm == RTE_DGEMM_AUTO && o->precision != RTE_FP64));
+    if (split && o->mk_route != RTE_MK_PCG)
+        b += nRm * nSm * 8;                    // the split GEMM's reciprocal table
     b += 7 * nRp * nSp * 8;                    // E_0 stencil coefficients
     const bool direct = o ? (o->e0_route == RTE_E0_DIRECT ||
                              (o->e0_route == RTE_E0_AUTO && m <= 156))

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -278,13 +279,52 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // issuer never wait on the epilogue's own arrivals.
 constexpr int kOzThreads = 576;
 constexpr int kOzEpiWarps = 16;
+// row pitch (in float2) of the staged (hi, lo) tile: 129 keeps the
+// column-wise writes of a warp (one row per lane) free of bank conflicts
+constexpr int kOzPitch = kOzBN + 1;
+static_assert((size_t)kOzBM * kOzPitch * 8 <= (size_t)kOzStages * (kOzBM + kOzBN) * 128,
+              "the staged tile must fit in the pipeline buffers");
+
+// f 2^E as an FP64 bit pattern built with integer operations (sign, the
+// exponent rebased and shifted by E, the 23 mantissa bits moved up): exact,
+// and no FP64 instruction, which this GPU issues at a small fraction of its
+// FP32 and integer rates.  False where f is subnormal, infinite or NaN or
+// f 2^E leaves the normal FP64 range.
+__device__ __forceinline__ bool f32_scaled_to_f64(float f, int E, double* out) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t mag = b & 0x7FFFFFFFu;
+    if (mag == 0) {
+        *out = __longlong_as_double((long long)(b & 0x80000000u) << 32);
+        return true;
+    }
+    const int e8 = (int)(mag >> 23);
+    const int e11 = e8 + (1023 - 127) + E;
+    if (e8 == 0 || e8 == 255 || e11 < 1 || e11 > 2046) return false;
+    const uint64_t bits = ((uint64_t)(b & 0x80000000u) << 32) | ((uint64_t)e11 << 52) |
+                          ((uint64_t)(mag & 0x7FFFFFu) << 29);
+    *out = __longlong_as_double((long long)bits);
+    return true;
+}
+
+// (hi + lo) 2^E rounded once to FP64: both parts widened and scaled exactly,
+// then one FP64 add; out-of-range cases take the FP64 route
+__device__ __forceinline__ double df_scaled_to_f64(float hi, float lo, int E) {
+    double a, b;
+    if (f32_scaled_to_f64(hi, E, &a) && f32_scaled_to_f64(lo, E, &b)) return a + b;
+    return ldexp((double)hi + (double)lo, E);
+}
+
+// named barrier 1 over the epilogue warps alone (the producer and MMA warps
+// wait at the block barrier)
+__device__ __forceinline__ void epi_bar_sync() {
+    asm volatile("barrier.sync 1, %0;" ::"n"(kOzEpiWarps * 32) : "memory");
+}
 
 __global__ void __launch_bounds__(kOzThreads, 1)
 k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
         int M, int N, int K, const OzPairs pairs, const int* __restrict__ ea,
         const int* __restrict__ eb, double* __restrict__ C, int ldc, int epi,
-        const double* __restrict__ at, const double* __restrict__ as,
-        const double* __restrict__ lam, int rows) {
+        const double* __restrict__ rinv, int rows) {
     constexpr uint32_t kABytes = kOzBM * kRowBytes, kBBytes = kOzBN * kRowBytes;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -304,6 +344,7 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
     // parameter would live in local memory)
     __shared__ int s_ya[kOzMaxPairs], s_yb[kOzMaxPairs];
     __shared__ int s_first[20], s_wgt[20];
+    __shared__ int s_fail;   // set by an epilogue thread whose wait timed out
     for (int p = threadIdx.x; p < pairs.n; p += blockDim.x) {
         s_ya[p] = pairs.s[p] * M + m0;
         s_yb[p] = pairs.t[p] * N + n0;
@@ -313,6 +354,7 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         s_wgt[g] = pairs.wgt[g];
     }
     if (threadIdx.x == 0) {
+        s_fail = 0;
         for (int s = 0; s < kOzStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
@@ -431,27 +473,58 @@ k_ozaki(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtens
         __syncwarp();
         if (lane == 0) mbar_arrive(acce0 + 8 * b);
     }
-    const int row = m0 + wq * 32 + lane;
-    if (ok && row < M) {
-        const int er = ea[row];
-        double fat = 0.0, fas = 0.0;
-        if (epi == 1) {
-            fat = at[row % rows];
-            fas = as[row % rows];
-        }
-        double* dst = C + (size_t)row * ldc;
+    // Finish through shared memory: every thread parks its (hi, lo) pairs
+    // (one row, 32 columns) in the pipeline buffers, which the last MMA has
+    // finished reading; then each warp converts and stores whole rows, so
+    // the loads of eb, of the reciprocal table and the FP64 stores are
+    // coalesced.  The block writes all or nothing: if any epilogue wait
+    // timed out (an MMA may then still be reading the buffers), none.
+    if (!ok) s_fail = 1;
+    epi_bar_sync();
+    const bool write = s_fail == 0;
+    float2* stage = reinterpret_cast<float2*>(smem);   // [kOzBM][kOzPitch]
+    if (write) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        float2* mine = stage + (wq * 32 + lane) * kOzPitch + quarter * 32;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            const int col = n0 + quarter * 32 + i;
-            if (col < N) {
-                double x = ldexp((double)hi[i] + (double)lo[i], er + eb[col]);
-                if (epi == 1) x = x / (fat - lam[col] * fas);
-                dst[col] = x;
+        for (int i = 0; i < 32; ++i) mine[i] = make_float2(hi[i], lo[i]);
+    }
+    epi_bar_sync();
+    if (write) {
+        for (int rl = warp - 2; rl < kOzBM; rl += kOzEpiWarps) {
+            const int row = m0 + rl;
+            if (row >= M) break;
+            const int er = ea[row];
+            const double* rr = epi == 1 ? rinv + (size_t)(row % rows) * N : nullptr;
+            double* dst = C + (size_t)row * ldc;
+#pragma unroll
+            for (int j = 0; j < kOzBN / 32; ++j) {
+                const int c = lane + 32 * j, col = n0 + c;
+                if (col < N) {
+                    const float2 v = stage[rl * kOzPitch + c];
+                    double x = df_scaled_to_f64(v.x, v.y, er + eb[col]);
+                    if (epi == 1) x *= rr[col];
+                    dst[col] = x;
+                }
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+}
+
+// 1 / (at[r] - lam[c] as[r]) for r < rows, c < N, row-major: the diagonal of
+// (M^- - K^-)^{-1} in the eigenbasis per cell, built once so that the split
+// GEMM's epilogue multiplies instead of dividing in FP64
+__global__ void k_oz_recip(int rows, int N, const double* __restrict__ at,
+                           const double* __restrict__ as, const double* __restrict__ lam,
+                           double* __restrict__ out) {
+    const size_t total = (size_t)rows * N;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / N), c = (int)(e % N);
+        out[e] = 1.0 / (at[r] - lam[c] * as[r]);
+    }
 }
 
 // One warp per row: exponent ex of the row maximum (|x| < 2^ex), then the
@@ -494,9 +567,9 @@ __global__ void k_oz_split(const double* __restrict__ X, int rows, int K, int S,
         for (int s = S - 1; s >= 1; --s) {
             const long long d = ((v + 64) & 127) - 64;
             v = (v - d) >> 7;
-            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn((float)d);
+            out[((size_t)s * rows + row) * K + k] = __float2bfloat16_rn((float)(int)d);
         }
-        out[(size_t)row * K + k] = __float2bfloat16_rn((float)v);
+        out[(size_t)row * K + k] = __float2bfloat16_rn((float)(int)v);
     }
 }
 
@@ -517,10 +590,22 @@ int ozaki_split(cudaStream_t s, const double* X, int rows, int K, int S, void* o
     return RTE_OK;
 }
 
+int ozaki_recip_table(cudaStream_t s, const double* at, const double* as, const double* lam,
+                      int rows, int N, double* out) {
+    if (rows <= 0 || N <= 0) return RTE_OK;
+    count_launches(1);
+    const size_t total = (size_t)rows * N;
+    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+    k_oz_recip<<<blocks, 256, 0, s>>>(rows, N, at, as, lam, out);
+    RTE_CUDA_TRY(cudaGetLastError());
+    return RTE_OK;
+}
+
 int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const void* Bslices,
-               const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
-               const double* as, const double* lam, int rows, int SB) {
+               const int* eb, int N, int K, int S, double* C, int ldc, int epi,
+               const double* rinv, int rows, int SB) {
     if (M <= 0 || N <= 0 || K <= 0) return RTE_OK;
+    if (epi == 1 && (!rinv || rows <= 0)) return fail(RTE_ERR_ARG, "epilogue 1 needs its table");
     if (S < 1 || S > 9 || S * (S + 1) / 2 > kOzMaxPairs) return fail(RTE_ERR_ARG, "bad slice count");
     if (SB == 0) SB = S;
     if (SB < S) return fail(RTE_ERR_ARG, "second operand has fewer slices than used");
@@ -554,8 +639,8 @@ int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const 
                                       (int)sm));
     dim3 grid((N + kOzBN - 1) / kOzBN, (M + kOzBM - 1) / kOzBM);
     count_launches(1);
-    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, pairs, ea, eb, C, ldc, epi, at, as,
-                                         lam, rows);
+    k_ozaki<<<grid, kOzThreads, sm, s>>>(ma, mb, M, N, K, pairs, ea, eb, C, ldc, epi, rinv,
+                                         rows);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
 }

@@ -33,13 +33,16 @@ int tc_set_wait_cycles(long long cycles);
 size_t ozaki_slice_bytes(int rows, int K, int S);
 int ozaki_split(cudaStream_t s, const double* X, int rows, int K, int S, void* out, int** e);
 // C (M x N, FP64) = A B^T from the slices of A (M x K) and of Bt (N x K);
-// epi 1 divides by (at[r % rows] - lam[c] as[r % rows]).  K <= any; exact
-// accumulation within chunks of 1024.  S digit slices are used; Bslices
-// holds SB >= S (its slices s < S are the leading digits of the same
-// expansion, so the first S of them are an S-digit truncation); SB = 0
-// means SB = S.
+// epi 1 multiplies entry (r, c) by rinv[(r % rows) N + c] (ozaki_recip_table).
+// K <= any; exact accumulation within chunks of 512.  S digit slices are
+// used; Bslices holds SB >= S (its slices s < S are the leading digits of
+// the same expansion, so the first S of them are an S-digit truncation);
+// SB = 0 means SB = S.
 int ozaki_gemm(cudaStream_t s, const void* Aslices, const int* ea, int M, const void* Bslices,
-               const int* eb, int N, int K, int S, double* C, int ldc, int epi, const double* at,
-               const double* as, const double* lam, int rows, int SB = 0);
+               const int* eb, int N, int K, int S, double* C, int ldc, int epi,
+               const double* rinv, int rows, int SB = 0);
+// out[r N + c] = 1 / (at[r] - lam[c] as[r]) for r < rows, c < N (rows x N FP64)
+int ozaki_recip_table(cudaStream_t s, const double* at, const double* as, const double* lam,
+                      int rows, int N, double* out);
 
 }  // namespace rte

@@ -114,6 +114,35 @@ def test_mixed_coarse_inverse(prec, route):
             assert np.linalg.norm(res) / np.linalg.norm(qc[r]) <= 2 * tol
 
 
+@pytest.mark.parametrize('prec', [1, 2], ids=['fp32', 'bf16'])
+def test_mixed_coarse_inverse_at_the_default_tolerance(prec):
+    # at the mixed modes' coarse tolerance 0.3 the coarse CG's own E_c
+    # products run in FP32 on the multigrid's level 0: the result meets the
+    # tolerance in the oracle's E_c, and it agrees with the FP64 handle's
+    # (the same FP32 V-cycle, FP64 products) to far below the tolerance
+    import paper_2102_09038_gb300 as rte
+    p = problem(17, 2, 2)
+    disc, ops = oracle_ops(p)
+    outs, qc, W = {}, None, None
+    for pr in (0, prec):
+        s = rte.Solver(p, n_plus=2, n_minus=3, precision=pr, max_rhs=2, coarse_tol=0.3,
+                       coarse_route=2)
+        d = s.d_plus
+        W = s.export('WpN').reshape(disc.nSp, d)
+        if qc is None:
+            qc = np.random.default_rng(5).standard_normal((2, disc.nRp, d))
+        out = torch.zeros((2, disc.nRp, d), dtype=torch.float64, device='cuda')
+        s.operator('EC_INV', torch.tensor(qc, dtype=torch.float64, device='cuda'), out)
+        outs[pr] = out.cpu().numpy()
+        s.close()
+    co = Coarse(ops, 2, W=W)
+    for r in range(2):
+        res = co.Ec @ outs[prec][r].ravel() - qc[r].ravel()
+        assert np.linalg.norm(res) / np.linalg.norm(qc[r]) <= 0.3 * 1.01
+        diff = np.linalg.norm(outs[prec][r] - outs[0][r]) / np.linalg.norm(outs[0][r])
+        assert diff <= 1e-4, diff
+
+
 # element-wise bounds on max|got - ref| / max|ref| of one mixed apply: six
 # unit roundoffs of the GEMM operand type (TF32 u = 2^-11, BF16 u = 2^-9),
 # the operand roundings of the two eigenbasis contractions and of U S^+
