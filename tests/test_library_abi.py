@@ -207,6 +207,13 @@ def test_memory_estimate_grows_with_the_problem(lib_path):
     assert e(small, precision=rte.MIXED_BF16) == pcg          # the mixed default
     assert e(small, precision=rte.FP64) == e(small, precision=rte.FP64,
                                              p1_route=rte.P1_RICHARDSON)
+    # the split GEMM's reciprocal table 1 / (at - lam as) of the eigenbasis
+    # route: n_R^- x n_S^- FP64 values, independent of the right-hand sides
+    table = 2 * 16 * 16 * 3 * 64 * 8
+    split = e(small, precision=rte.FP64, dgemm=rte.DGEMM_SPLIT)
+    assert split - e(small, precision=rte.FP64) == table
+    assert e(small, precision=rte.FP64, dgemm=rte.DGEMM_SPLIT, mk_route=rte.MK_PCG) == \
+        e(small, precision=rte.FP64, mk_route=rte.MK_PCG)
 
 
 @pytest.mark.parametrize('field, value, words', [
