@@ -147,7 +147,10 @@ typedef struct {
                                0: 1e-12 (FP64) or 0.3 (mixed modes)          */
     int e0_maxit;
     double coarse_tol;      /* relative residual of the E_c CG;
-                               0: 1e-12 (FP64) or 0.3 (mixed modes)          */
+                               0: 1e-12 (FP64) or 0.3 (mixed modes); from
+                               1e-2 on, mixed modes run the CG's own E_c
+                               products in FP32 (multigrid route), the CG
+                               recurrences staying FP64                     */
     int coarse_maxit;
     int max_iter;           /* outer Richardson iterations                   */
     int max_rhs;            /* workspace is sized for this many RHS          */

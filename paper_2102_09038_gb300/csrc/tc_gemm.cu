@@ -595,7 +595,8 @@ int ozaki_recip_table(cudaStream_t s, const double* at, const double* as, const 
     if (rows <= 0 || N <= 0) return RTE_OK;
     count_launches(1);
     const size_t total = (size_t)rows * N;
-    const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, 152 * 16);
+    const unsigned blocks =
+        (unsigned)std::min<size_t>((total + 255) / 256, (size_t)device_sm_count() * 8);
     k_oz_recip<<<blocks, 256, 0, s>>>(rows, N, at, as, lam, out);
     RTE_CUDA_TRY(cudaGetLastError());
     return RTE_OK;
