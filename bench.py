@@ -322,6 +322,18 @@ def roofline_of(name, total_ms, launches, d, nrhs, info, peaks, src, fp64_peak, 
     return roof
 
 
+def scope_rooflines(tim, d, nrhs, info, peaks, src, fp64_peak, tol, count=4):
+    """The roofline of the largest timing scope and those of the `count`
+    largest ({scope: (total ms, launches)} as the library's timing reports
+    it), each against its own bound."""
+    ranked = sorted(tim.items(), key=lambda kv: -kv[1][0])
+    top = ranked[0]
+    roof = roofline_of(top[0], top[1][0], top[1][1], d, nrhs, info, peaks, src, fp64_peak, tol)
+    rooflines = [roofline_of(k, v[0], v[1], d, nrhs, info, peaks, src, fp64_peak, tol)
+                 for k, v in ranked[:count]]
+    return roof, rooflines
+
+
 def kernel_impl_bytes(name, d, nrhs, info):
     """The bytes the E_0 kernels move by their own design, per launch (kept
     beside the algorithmic count): per V-cycle and active (node, column) the
@@ -453,12 +465,8 @@ def run_ours(args):
             fp64_rate.append(fp64_peak_tflops(torch))
         return fp64_rate[0]
 
-    roof = roofline_of(top[0], top[1][0], top[1][1], d, p.nrhs, last_info, peaks, src,
-                       fp64_peak, p.tol)
+    roof, rooflines = scope_rooflines(tim, d, p.nrhs, last_info, peaks, src, fp64_peak, p.tol)
     roof.update(traffic=traffic, traffic_source=traffic_note)
-    # the four largest timing scopes, each against its own bound
-    rooflines = [roofline_of(k, v[0], v[1], d, p.nrhs, last_info, peaks, src, fp64_peak, p.tol)
-                 for k, v in ranked[:4]]
     share = {k: round(v[0] / sum(x[0] for x in tim.values()), 4)
              for k, v in tim.items()}
 

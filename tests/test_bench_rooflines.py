@@ -63,3 +63,19 @@ def test_fp64_scopes_use_the_measured_fp64_rate_and_unknown_scopes_stay_empty():
     empty = _roof('axpy', 3.0, 100)
     assert empty['frac'] is None and empty['avg_ms'] == pytest.approx(0.03)
     assert not math.isnan(empty['avg_ms'])
+
+
+def test_scope_rooflines_rank_the_timing_scopes():
+    import bench
+    # total ms and launches of one benchmark solve as the library's timing
+    # scopes report them
+    tim = {'coarse_cg': (38.8, 16), 'e0_direct': (34.4, 32), 'dgemm_split_mk1': (18.0, 17),
+           'dgemm_split_mk2': (15.1, 17), 'apply_even': (11.0, 17), 'axpy': (5.1, 113),
+           'tc_gemm_mk1': (7.5, 48)}
+    roof, rows = bench.scope_rooflines(tim, D, 1, INFO, PEAKS, 'measured', lambda: 1.10, 1e-6)
+    assert roof['kernel'] == 'coarse_cg' and roof['bound'] == 'hbm'
+    assert [r['kernel'] for r in rows] == ['coarse_cg', 'e0_direct', 'dgemm_split_mk1',
+                                           'dgemm_split_mk2']
+    assert [r['bound'] for r in rows] == ['hbm', 'hbm', 'tensor', 'tensor']
+    assert all(0 < r['frac'] < 1 for r in rows)
+    assert rows[0] == roof
